@@ -1,0 +1,312 @@
+"""Seeded synthetic inputs for the free-surface LBM step.
+
+This module only builds *inputs*: cell flags, densities, velocities, fill
+levels, seeded noise and wall link fractions, from the geometry of each
+workload.  It holds none of the method's arithmetic (no equilibrium, no
+collision, no closure): both the CUDA library and the CPU oracle turn these
+arrays into populations themselves.
+
+Layout conventions (shared with the C interface):
+  * cell index ``i = x + nx*(y + ny*z)`` (x fastest),
+  * per-link arrays are ``[19][N]`` in the library's population order,
+  * cell flags: LIQUID=1, INTERFACE=2, GAS=4, WALL=8,
+  * node (x, y, z) sits at the physical point (x+1/2, y+1/2, z+1/2); a
+    non-periodic face is a half-way wall on the domain boundary.
+
+Workloads follow the paper's test cases (Sec. 4.3 film flows, Sec. 4.4 dam
+break) and the standing wave; sizes are parameters.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+LIQUID, INTERFACE, GAS, WALL = 1, 2, 4, 8
+
+# D3Q19 link directions in the public population order (an interface
+# convention of the C ABI: rest, 6 axis links, 12 diagonals, each followed by
+# its opposite).  Used here only to place wall link fractions.
+LINKS = np.array(
+    [[0, 0, 0],
+     [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+     [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0],
+     [1, 0, 1], [-1, 0, -1], [1, 0, -1], [-1, 0, 1],
+     [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]], dtype=np.int64)
+
+SEED = 1409
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Counter-based SplitMix64 (Steele, Lea, Flood 2014): output k is the
+    finaliser applied to ``seed + (offset + k + 1) * golden``."""
+    k = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, count: int, amp: float, offset: int = 0) -> np.ndarray:
+    """Uniform numbers in [-amp, amp) from the top 53 bits of SplitMix64."""
+    u = (splitmix64(seed, count, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return amp * (2.0 * u - 1.0)
+
+
+def default_params(**kw) -> dict:
+    p = dict(tau=0.8, magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), rho_G=1.0, sigma=0.0,
+             rule=1, compressible=0, linear_eq=0, eps=1e-3,
+             periodic=(0, 0, 0), zshift=0, freeze=0, delta_min=0.0)
+    p.update(kw)
+    return p
+
+
+class Case(dict):
+    """dict with keys dims, params, flags, rho, u, phi, noise, wall_delta."""
+
+    @property
+    def N(self) -> int:
+        nx, ny, nz = self["dims"]
+        return nx * ny * nz
+
+
+def _neighbour_index(dims, periodic, zshift, i, c):
+    """Index of cell i + c (arrays), -1 beyond a non-periodic face."""
+    nx, ny, nz = dims
+    x = i % nx
+    y = (i // nx) % ny
+    z = i // (nx * ny)
+    X, Y, Z = x + c[0], y + c[1], z + c[2]
+    ok = np.ones_like(i, dtype=bool)
+    if periodic[0]:
+        lo, hi = X < 0, X >= nx
+        Z = Z + np.where(lo, zshift, 0) - np.where(hi, zshift, 0)
+        X = np.where(lo, X + nx, np.where(hi, X - nx, X))
+    else:
+        ok &= (X >= 0) & (X < nx)
+    if periodic[1]:
+        Y = np.mod(Y, ny)
+    else:
+        ok &= (Y >= 0) & (Y < ny)
+    if periodic[2]:
+        Z = np.mod(Z, nz)
+    ok &= (X >= 0) & (X < nx) & (Y >= 0) & (Y < ny) & (Z >= 0) & (Z < nz)
+    out = X + nx * (Y + ny * Z)
+    return np.where(ok, out, -1)
+
+
+def classify(dims, periodic, zshift, phi, solid=None, sharp=False) -> np.ndarray:
+    """Flags from fill levels: phi == 0 -> GAS, a cell with phi > 0 that has a
+    gas cell along one of the 18 links -> INTERFACE, else LIQUID; solid cells
+    -> WALL.  ``sharp=True`` (frozen-interface test geometries) takes a cell as
+    liquid only when its node lies inside the liquid, i.e. phi >= 1/2 for a
+    planar cut, so that every boundary node has its surface ahead of it."""
+    N = int(np.prod(dims))
+    thresh = (phi >= 0.5) if sharp else (phi > 0.0)
+    flags = np.where(thresh, LIQUID, GAS).astype(np.uint8)
+    if solid is not None:
+        flags[solid] = WALL
+    i = np.arange(N, dtype=np.int64)
+    gas = flags == GAS
+    near_gas = np.zeros(N, dtype=bool)
+    for q in range(1, 19):
+        j = _neighbour_index(dims, periodic, zshift, i, LINKS[q])
+        near_gas |= (j >= 0) & gas[np.maximum(j, 0)]
+    flags[(flags == LIQUID) & near_gas] = INTERFACE
+    return flags
+
+
+def _clamped_linear_mean(z0, z1):
+    """Exact mean over t in [0,1] of clamp(z0 + (z1-z0) t, 0, 1) (vectorised)."""
+    z0 = np.asarray(z0, dtype=np.float64)
+    z1 = np.asarray(z1, dtype=np.float64)
+    lo = np.minimum(z0, z1)
+    hi = np.maximum(z0, z1)
+    span = hi - lo
+    out = np.empty(np.broadcast(lo, hi).shape)
+    flat = span <= 1e-300
+    # integral of clamp(s,0,1) ds over [lo,hi] divided by the span
+    def G(s):  # antiderivative of clamp(s, 0, 1)
+        return np.where(s <= 0.0, 0.0, np.where(s >= 1.0, s - 0.5, 0.5 * s * s))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        out = (G(hi) - G(lo)) / np.where(flat, 1.0, span)
+    return np.where(flat, np.clip(lo, 0.0, 1.0), out)
+
+
+def film(nx=4, ny=4, nz=32, h=20.0, tau=0.8, gx=1e-6, rule=1, noise_amp=1e-8,
+         magic=3.0 / 16.0, seed=SEED, **kw) -> Case:
+    """Gravity-driven film on a half-way bounce-back wall at z=0 (Sec. 4.3):
+    x, y periodic, liquid depth h (fill 1 below the surface plane z = h, the
+    exact cut fraction in the cut cell, 0 above), rho = rho_G = 1, u = 0,
+    populations at equilibrium plus seeded uniform noise."""
+    dims = (nx, ny, nz)
+    N = nx * ny * nz
+    z = np.arange(N) // (nx * ny)
+    phi = np.clip(h - z, 0.0, 1.0).astype(np.float64)
+    params = default_params(tau=tau, magic=magic, g=(gx, 0.0, 0.0), rule=rule,
+                            periodic=(1, 1, 0))
+    params.update(kw)
+    sharp = bool(params["freeze"])
+    flags = classify(dims, params["periodic"], 0, phi, sharp=sharp)
+    noise = uniform(seed, 19 * N, noise_amp) if noise_amp else None
+    keep = (flags == INTERFACE) | ((flags == GAS) & sharp)
+    return Case(dims=dims, params=params, flags=flags, rho=np.ones(N),
+                u=np.zeros((N, 3)), phi=np.where(keep, phi, 0.0),
+                noise=noise, wall_delta=None, h=h)
+
+
+def film_profile(z, h, g, nu):
+    """Steady half-Poiseuille film u(z) = g/(2 nu) (2 h z - z^2)."""
+    return g / (2.0 * nu) * (2.0 * h * z - z * z)
+
+
+def film_transient(z, t, h, g, nu, terms=200):
+    """Film started from rest: u(z,t) = u_s(z) - sum_n b_n sin(l_n z) exp(-nu l_n^2 t),
+    l_n = (2n+1) pi / (2h), b_n = 2 g / (nu h l_n^3) (separation of variables for
+    u_t = nu u_zz + g, u(0) = 0, u_z(h) = 0, u(z, 0) = 0)."""
+    z = np.asarray(z, dtype=np.float64)
+    out = film_profile(z, h, g, nu)
+    for n in range(terms):
+        ln = (2 * n + 1) * math.pi / (2.0 * h)
+        bn = 2.0 * g / (nu * h * ln ** 3)
+        out = out - bn * np.sin(ln * z) * math.exp(-nu * ln * ln * t)
+    return out
+
+
+def inclined_film(h=8, tau=0.8, rule=1, magic=0.25, wall_offset=0.1, peak=None,
+                  headroom=4, init_exact=True, **kw) -> Case:
+    """Film on an inclined wall, slope 1/2 (Sec. 4.3, rotated film): ny = 1,
+    period nx = 2h with a z-shift of h on the x wrap, wall plane
+    z = x/2 + wall_offset (explicit WALL cells below it, link fractions from the
+    exact plane), free surface h cells higher (vertical depth h), exact cut
+    fill levels, gravity along the slope with g = 2 nu peak / H^2
+    (H = 2h/sqrt5 the normal depth), frozen interface.
+
+    ``peak=None`` keeps the Reynolds number fixed across depths as the paper's
+    refinement does (g ~ dx^-3 at fixed tau): peak velocity 0.05 at h = 8,
+    scaled as 8/h."""
+    if peak is None:
+        peak = 0.05 * 8.0 / h
+    nx, ny, nz = 2 * h, 1, 2 * h + headroom
+    dims = (nx, ny, nz)
+    N = nx * ny * nz
+    i = np.arange(N)
+    x = (i % nx) + 0.5
+    z = (i // (nx * ny)) + 0.5
+    zw = x / 2.0 + wall_offset
+    solid = z < zw
+    # fill: mean over the cell's x-extent of clamp(z_s(x) - k, 0, 1)
+    k = z - 0.5
+    xl = x - 0.5
+    zs0 = xl / 2.0 + wall_offset + h - k
+    zs1 = zs0 + 0.5
+    phi = _clamped_linear_mean(zs0, zs1)
+    phi = np.where(solid, 0.0, phi)
+    params = default_params(tau=tau, magic=magic, rule=rule, periodic=(1, 1, 0),
+                            zshift=h, freeze=1)
+    params.update(kw)
+    nu = (params["tau"] - 0.5) / 3.0
+    H = 2.0 * h / math.sqrt(5.0)
+    g = 2.0 * nu * peak / (H * H)
+    t_hat = np.array([2.0, 0.0, 1.0]) / math.sqrt(5.0)
+    params["g"] = tuple(g * t_hat)
+    flags = classify(dims, params["periodic"], params["zshift"], phi, solid=solid,
+                     sharp=bool(params["freeze"]))
+    # wall link fractions: x_b + s c_q crosses the plane z - x/2 - off = 0
+    wd = np.full((19, N), -1.0)
+    fluid = (flags == LIQUID) | (flags == INTERFACE)
+    for q in range(1, 19):
+        c = LINKS[q]
+        j = _neighbour_index(dims, params["periodic"], params["zshift"], i, c)
+        hit = fluid & ((j < 0) | (flags[np.maximum(j, 0)] == WALL))
+        denom = c[0] / 2.0 - c[2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = (z - x / 2.0 - wall_offset) / denom
+        good = hit & (denom > 0)
+        wd[q, good] = s[good]
+    ncoord = (z - zw) * (2.0 / math.sqrt(5.0))
+    ut = np.where(fluid, g / (2 * nu) * (2 * H * np.minimum(ncoord, H) - np.minimum(ncoord, H) ** 2), 0.0)
+    u = np.zeros((N, 3))
+    if init_exact:
+        u = ut[:, None] * t_hat[None, :]
+    keep = (flags == INTERFACE) | ((flags == GAS) & bool(params["freeze"]))
+    return Case(dims=dims, params=params, flags=flags, rho=np.ones(N), u=u,
+                phi=np.where(keep, phi, 0.0), noise=None,
+                wall_delta=wd.reshape(-1), h=h, H=H, nu=nu, gmag=g,
+                ncoord=ncoord, t_hat=t_hat)
+
+
+def standing_wave(n=128, depth=64.0, amp=2.0, tau=0.55, g=2e-5, sigma=1e-4,
+                  phi_noise=1e-4, seed=SEED, quad=8, rule=1, **kw) -> Case:
+    """Standing gravity-capillary wave in an n^3 box with walls on all faces:
+    surface z = depth + amp cos(2 pi x / n) cos(2 pi y / n); fill levels from
+    the exact cut volume (quad x quad Gauss quadrature of clamp(s - k, 0, 1)
+    over the cell's x-y square), seeded fill noise on interface cells,
+    hydrostatic density."""
+    dims = (n, n, n)
+    N = n ** 3
+    gx, gw = np.polynomial.legendre.leggauss(quad)
+    gx = 0.5 * (gx + 1.0)
+    gw = 0.5 * gw
+    xs = np.arange(n)
+    # surface heights at quadrature points, per column
+    X = xs[:, None] + gx[None, :]  # (n, quad)
+    cx = np.cos(2 * math.pi * X / n)
+    phi = np.empty((n, n, n))
+    for k in range(n):
+        s = depth + amp * cx[None, :, None, :] * cx[:, None, :, None] - k  # (y, x, qy, qx)
+        v = np.clip(s, 0.0, 1.0)
+        phi[k] = np.einsum("yxab,a,b->yx", v, gw, gw)
+    phi = phi.reshape(-1)
+    phi[np.abs(phi) < 1e-15] = 0.0
+    phi[np.abs(phi - 1.0) < 1e-15] = 1.0
+    params = default_params(tau=tau, g=(0.0, 0.0, -g), sigma=sigma, rule=rule)
+    params.update(kw)
+    flags = classify(dims, params["periodic"], 0, phi)
+    i = np.arange(N)
+    x = (i % n) + 0.5
+    y = ((i // n) % n) + 0.5
+    z = (i // (n * n)) + 0.5
+    surf = depth + amp * np.cos(2 * math.pi * x / n) * np.cos(2 * math.pi * y / n)
+    rho = params["rho_G"] + 3.0 * g * np.maximum(surf - z, 0.0)
+    ifc = flags == INTERFACE
+    phi = np.where(ifc, phi, 0.0)
+    phi[ifc] += uniform(seed, int(ifc.sum()), phi_noise, offset=19 * N)
+    return Case(dims=dims, params=params, flags=flags, rho=rho, u=np.zeros((N, 3)),
+                phi=phi, noise=None, wall_delta=None, depth=depth, amp=amp)
+
+
+def dam_break(nx=512, ny=256, nz=256, col_x=128, col_z=192, tau=0.51, g=1e-5,
+              phi_noise=1e-3, seed=SEED, rule=1, **kw) -> Case:
+    """Dam break (Sec. 4.4) at throughput scale: walls on all faces, liquid
+    column x < col_x, z < col_z at rest with hydrostatic density from the
+    surface, rest gas; seeded fill perturbation on the interface layer."""
+    dims = (nx, ny, nz)
+    N = nx * ny * nz
+    i = np.arange(N, dtype=np.int64)
+    x = i % nx
+    z = i // (nx * ny)
+    inside = (x < col_x) & (z < col_z)
+    phi = inside.astype(np.float64)
+    params = default_params(tau=tau, g=(0.0, 0.0, -g), rule=rule)
+    params.update(kw)
+    flags = classify(dims, params["periodic"], 0, phi)
+    rho = np.where(inside, params["rho_G"] + 3.0 * g * (col_z - (z + 0.5)), params["rho_G"])
+    ifc = flags == INTERFACE
+    phi = np.where(ifc, 1.0, 0.0)
+    phi[ifc] += uniform(seed, int(ifc.sum()), phi_noise, offset=19 * N)
+    return Case(dims=dims, params=params, flags=flags, rho=rho, u=np.zeros((N, 3)),
+                phi=phi, noise=None, wall_delta=None)
+
+
+def adjoint_film(**kw) -> Case:
+    """Film of the differentiation workload: 8 x 4 x 64, depth 40."""
+    args = dict(nx=8, ny=4, nz=64, h=40.0)
+    args.update(kw)
+    return film(**args)
