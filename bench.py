@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the free-surface LBM step on GB300.
+
+Workload: 3D dam break 512 x 256 x 256 (33.5 M cells), walls on all faces,
+liquid column x < 128, z < 192 at rest with hydrostatic density, tau = 0.51,
+Lambda = 3/16, g = 1e-5 along -z, FSL rule, seeded fill perturbation 1e-3 on
+the interface layer.  The headline form is FP32 populations with FP64
+interface mass and mass balance; FP64 and FP16-storage forms are measured in
+the same run.  A "step" is one full time step: stream-collide, free-surface
+reconstruction, mass exchange, mass balance and cell conversions.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FSLBM MLUPS at 1 GB300 (FP32/FP16-store vs FP64 plain), % HBM roofline, adjoint/fwd"
+WORKLOAD = "dam_break_512x256x256_fsl"
+DIMS = (512, 256, 256)
+COL = (128, 192)
+KERNELS_PER_STEP = 11  # k_bulk, k_iface, 2 x k_reduce, 7 conversion kernels
+STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="f32,f64,f16", help="precision forms; the first is the headline")
+    ap.add_argument("--form-steps", type=int, default=2000, help="timed steps of the non-headline forms")
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="development size (128 x 64 x 64)")
+    return ap.parse_args()
+
+
+def dims_for(args):
+    return (128, 64, 64) if args.small else DIMS
+
+
+def col_for(args):
+    return (32, 48) if args.small else COL
+
+
+def make_case(args):
+    from paper_1409_5645_gb300 import cases
+    nx, ny, nz = dims_for(args)
+    cx, cz = col_for(args)
+    return cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=cx, col_z=cz)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (independent replicas: one lattice per GPU)
+# ---------------------------------------------------------------------------
+def dist_setup(backend):
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# measured peaks and the committed ncu traffic figure
+# ---------------------------------------------------------------------------
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("fslbm_step.cu", "fslbm_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(form):
+    """Per-launch DRAM bytes of k_bulk from the committed ncu summary, scaled
+    to the full lattice; None if absent or taken on other kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_bulk_dam_break_{form}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    val = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not sha or not val or sha.group(1) != kernel_source_sha():
+        return None
+    return float(val.group(1))
+
+
+# ---------------------------------------------------------------------------
+# one precision form
+# ---------------------------------------------------------------------------
+def count_kinds(lat):
+    import numpy as np
+    from paper_1409_5645_gb300 import fslbm
+    fl = lat.get(fslbm.FIELD_FLAGS)["flags"]
+    return int(np.count_nonzero(fl == 1)), int(np.count_nonzero(fl == 2))
+
+
+def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False):
+    import torch
+    from paper_1409_5645_gb300 import fslbm
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    lat = fslbm.Lattice(case["dims"], case["params"], precision=form, stream=stream.cuda_stream)
+    t = {k: torch.from_numpy(case[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
+    lat.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
+    del t
+    lat.step(warmup)
+    lat.sync()
+    M0, _ = lat.total_mass()
+    nliq0, nifc0 = count_kinds(lat)
+    lat.timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    ck = Clocks(local_rank) if clocks else None
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = ck.stop() if ck else None
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    groups, nt = lat.timing_read()
+    lat.timing(False)
+    lat.sync()
+    M1, lost = lat.total_mass()
+    nliq1, nifc1 = count_kinds(lat)
+    out = dict(ms=ms, steps=steps, groups_ms=groups, timed_steps=nt, mass0=M0, mass1=M1, lost=lost,
+               n_liquid=(nliq0 + nliq1) / 2, n_interface=(nifc0 + nifc1) / 2, clocks=clk,
+               device_bytes=lat.device_bytes, t_end=lat.time)
+    lat.close()
+    torch.cuda.synchronize(dev)
+    return out
+
+
+def e2e_run(case, form, steps, local_rank):
+    """The user's call sequence with host buffers: state from pinned host
+    memory, then every step fslbm_step + a device->host read of that step's
+    mass balance."""
+    import torch
+    from paper_1409_5645_gb300 import fslbm
+    dev = torch.device("cuda", local_rank)
+    pinned = {k: torch.from_numpy(case[k]).pin_memory() for k in ("flags", "rho", "u", "phi")}
+    host = {k: v.numpy() for k, v in pinned.items()}
+    h2d = sum(v.nbytes for v in host.values())
+    lat = fslbm.Lattice(case["dims"], case["params"], precision=form)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    lat.init_equilibrium(host["flags"], host["rho"], host["u"], host["phi"])
+    for _ in range(steps):
+        lat.step(1)
+        lat.step_mass()
+    t1 = time.perf_counter()
+    lat.close()
+    N = int(case["flags"].size)
+    return dict(value=N * steps / (t1 - t0) / 1e6, seconds=t1 - t0, h2d_bytes=h2d,
+                d2h_bytes_per_step=8 + 4)
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_rate(dims, col, budget_s, max_steps=None, warmup=0):
+    from oracle.oracle import Oracle
+    from paper_1409_5645_gb300 import cases
+    c = cases.dam_break(nx=dims[0], ny=dims[1], nz=dims[2], col_x=col[0], col_z=col[1])
+    o = Oracle.from_case(c)
+    if warmup:
+        o.step(warmup)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            break
+    return c.N * steps / el / 1e6, steps, el
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, ws = dist_setup("nccl")
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    case = make_case(args)
+    N = int(case["flags"].size)
+
+    head = run_form(case, forms[0], args.steps, args.warmup, ws, rank, local_rank, clocks=True)
+    ms_max = max_over_ranks(head["ms"], ws, torch.device("cuda", local_rank))
+    value = ws * N * args.steps / (ms_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (k_bulk): algorithmic bytes per launch =
+    # liquid cells x 2*19*s (pull + store) + every cell's flag byte
+    s = STORE_BYTES[forms[0]]
+    peak, peak_kind = hbm_peak()
+    bulk_ms = head["groups_ms"][0]
+    alg_bulk = head["n_liquid"] * 2 * 19 * s + N * 1.0
+    achieved = alg_bulk / (bulk_ms / 1e3) / 1e9
+    # whole step: + interface cells (populations, m, phi) and their lists
+    alg_step = (head["n_liquid"] + head["n_interface"]) * 2 * 19 * s + N * 1.0 + head["n_interface"] * (16 + 8)
+    step_gbs = alg_step / (head["ms"] / args.steps / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(head["ms"] / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": forms[0], "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.small else "dam_break_128x64x64_fsl",
+                   "dims": list(dims_for(args)), "rule": "FSL", "tau": 0.51, "g": 1e-5,
+                   "precision": forms[0], "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (populations %.1f GB)" % (N * 2 * 19 * s / 1e9)},
+        "mflups_active": round(ws * (head["n_liquid"] + head["n_interface"]) * args.steps
+                               / (ms_max / 1e3) / 1e6, 2),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(forms[0]),
+                     "kernel": "k_bulk", "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bulk, "launch_ms": round(bulk_ms, 5)},
+        "step_roofline": {"achieved": round(step_gbs, 1), "frac": round(step_gbs / peak, 4),
+                          "alg_bytes_per_step": alg_step},
+        "kernel_ms_per_step": {"bulk": round(head["groups_ms"][0], 5), "iface": round(head["groups_ms"][1], 5),
+                               "reduce": round(head["groups_ms"][2], 5), "conversions": round(head["groups_ms"][3], 5)},
+        "cells": {"total": N, "liquid_avg": head["n_liquid"], "interface_avg": head["n_interface"]},
+        "mass_drift_rel": (head["mass1"] - head["mass0"]) / head["mass0"],
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": head["clocks"],
+    }
+    # the other precision forms on the same workload
+    other = {}
+    for f in forms[1:]:
+        r = run_form(case, f, args.form_steps, args.warmup, ws, rank, local_rank)
+        msx = max_over_ranks(r["ms"], ws, torch.device("cuda", local_rank))
+        sb = STORE_BYTES[f]
+        bulk = r["n_liquid"] * 2 * 19 * sb + N
+        other[f] = {"value": round(ws * N * args.form_steps / (msx / 1e3) / 1e6, 2), "steps": args.form_steps,
+                    "ms_per_step": round(r["ms"] / args.form_steps, 5),
+                    "bulk_gbs": round(bulk / (r["groups_ms"][0] / 1e3) / 1e9, 1),
+                    "bulk_frac": round(bulk / (r["groups_ms"][0] / 1e3) / 1e9 / peak, 4),
+                    "kernel_ms_per_step": [round(x, 5) for x in r["groups_ms"]]}
+    line["forms"] = other
+    # end to end through the C interface with host buffers
+    e2e = e2e_run(case, forms[0], args.e2e_steps, local_rank)
+    e2e_v = max_over_ranks(-e2e["value"], ws, torch.device("cuda", local_rank))
+    line["e2e"] = {"value": round(-e2e_v * ws, 2), "unit": "MLUPS",
+                   "h2d_bytes_per_step": e2e["h2d_bytes"] // args.e2e_steps,
+                   "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "steps": args.e2e_steps,
+                   "includes": "state upload from pinned host memory, per-step mass read"}
+    # the oracle on the host cores (rank 0, N = 1)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, st, el = oracle_rate((128, 64, 64), (32, 48), budget_s=12.0)
+        line["cpu_baseline"] = {"value": round(rate, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle, dam break 128x64x64 (same setup scaled by 1/4), "
+                                          f"{st} steps in {el:.1f} s, single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ncores = os.cpu_count()
+    total = args.steps + args.warmup
+    # sample sized so that warm-up + timed steps take about two minutes
+    budget = 120.0
+    per_step = budget / max(total, 1)
+    # oracle cost ~ 0.4 us per cell and step on one core
+    cells = min(max(int(per_step / 4e-7), 16 * 8 * 12), 2_000_000)
+    scale = (cells / (DIMS[0] * DIMS[1] * DIMS[2])) ** (1 / 3)
+    nx = max(16, int(DIMS[0] * scale) // 4 * 4)
+    ny = max(8, int(DIMS[1] * scale) // 4 * 4)
+    nz = max(12, int(DIMS[2] * scale) // 4 * 4)
+    col = (max(4, nx // 4), max(6, nz * 3 // 4))
+    from oracle.oracle import Oracle
+    from paper_1409_5645_gb300 import cases
+    c = cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=col[0], col_z=col[1])
+    o = Oracle.from_case(c)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = c.N * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 4),
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_dims": [nx, ny, nz], "rule": "FSL", "tau": 0.51, "g": 1e-5},
+            "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 oracle, dam break {nx}x{ny}x{nz} (same setup scaled), "
+                                       f"{args.steps} timed steps, single thread of {ncores}"},
+            "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * fslbm.h -- C interface of the GB300 free-surface lattice Boltzmann step.
+ *
+ * One time step of the free-surface lattice Boltzmann method (FSLBM) on a
+ * D3Q19 lattice, after Bogner, Ammer, Ruede, "Boundary Conditions for Free
+ * Interfaces with the Lattice Boltzmann Method" (arXiv:1409.5645):
+ *   - TRT stream-collide with a body force on liquid and interface cells
+ *     (Sec. 2.1, Eq. lbe1 / lbe2, forcing through u^eq = U - F/lambda_-),
+ *   - half-way bounce-back or CLI walls (Sec. 4.2, 4.3),
+ *   - reconstruction of the populations streaming in from gas cells by the
+ *     FSK rule (Eq. koerner) or the FSL rule (Eq. closure with Table 1, D = 0),
+ *     with the link fraction delta taken from the fill levels and the interface
+ *     normal (Sec. 2.2, Sec. 5),
+ *   - interface mass exchange and fill update, and cell conversion with
+ *     excess-mass redistribution (Sec. 2.3 / 4.4; the paper takes these from
+ *     Koerner et al. and Thuerey).
+ *
+ * Conventions shared by every entry point
+ *   cells       N = nx*ny*nz, cell index i = x + nx*(y + ny*z) (x fastest).
+ *   links       q = 0..18 in this order: rest; (+-1,0,0), (0,+-1,0), (0,0,+-1);
+ *               (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0); (1,0,1),(-1,0,-1),(1,0,-1),
+ *               (-1,0,1); (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1).  Each link is
+ *               followed by its opposite.  Per-link arrays are [19][N].
+ *   flags       uint8 per cell: FSLBM_LIQUID, FSLBM_INTERFACE, FSLBM_GAS,
+ *               FSLBM_WALL.  A face of a non-periodic axis is a half-way wall.
+ *   f           populations in FP64 at the interface, whatever the internal
+ *               precision.  fslbm_set_state takes pre-collision f(x,t);
+ *               fslbm_get_fields returns post-collision f~(x,t) (what the
+ *               library stores); fslbm_set_state_post takes that back.
+ *   where       FSLBM_HOST: plain host pointers (copied synchronously);
+ *               FSLBM_DEVICE: device pointers on the handle's GPU (copied on
+ *               the handle's stream).
+ *   ownership   the library owns its device state; buffers passed in or out
+ *               belong to the caller, are copied, and are never retained.
+ *   errors      every int-returning call returns an fslbm_status.  Device-side
+ *               faults of the method (instability, a liquid cell next to gas)
+ *               are recorded in a sticky device error word, reported by the
+ *               next synchronising call (fslbm_sync, fslbm_get_fields,
+ *               fslbm_total_mass) and cleared by fslbm_set_state.  No call
+ *               exits or aborts the process.
+ *   threading   one handle per host thread at a time; calls on one handle are
+ *               ordered on its CUDA stream.
+ */
+#ifndef FSLBM_H
+#define FSLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fslbm fslbm_t;
+
+enum fslbm_rule { FSLBM_FSK = 0, FSLBM_FSL = 1 };
+
+/* Precision forms: FP64 throughout; FP32 populations with FP64 interface
+ * mass and mass balance; FP16 storage of f_q - w_q (rho_0 = 1) with FP32
+ * arithmetic and FP64 interface mass and mass balance. */
+enum fslbm_precision { FSLBM_F64 = 0, FSLBM_F32 = 1, FSLBM_F16 = 2 };
+
+enum fslbm_status {
+  FSLBM_OK = 0,
+  FSLBM_ERR_ARG = -1,      /* bad argument or parameter */
+  FSLBM_ERR_OOM = -2,      /* device allocation failed */
+  FSLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
+  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density */
+  FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
+  FSLBM_ERR_TIMEOUT = -7   /* reserved for bounded waits */
+};
+
+enum fslbm_cell { FSLBM_LIQUID = 1, FSLBM_INTERFACE = 2, FSLBM_GAS = 4, FSLBM_WALL = 8 };
+
+enum fslbm_where { FSLBM_HOST = 0, FSLBM_DEVICE = 1 };
+
+/* Field bits of fslbm_get_fields; out[] holds one pointer per set bit, in
+ * increasing bit order. */
+enum fslbm_field {
+  FSLBM_FIELD_FLAGS = 1, /* uint8 [N] */
+  FSLBM_FIELD_F = 2,     /* double [19][N], post-collision f~(t); 0 off fluid cells */
+  FSLBM_FIELD_MASS = 4,  /* double [N]: interface m, liquid rho, else 0 */
+  FSLBM_FIELD_PHI = 8,   /* double [N]: liquid 1, interface m/rho, gas its stored fill */
+  FSLBM_FIELD_RHO = 16,  /* double [N]: rho = sum_q f_q on fluid cells */
+  FSLBM_FIELD_U = 32     /* double [N][3]: u = U + F/(2 rho_0) (Eq. momentum) */
+};
+
+/* Parameters of a lattice (fslbm_default_params fills the defaults). */
+typedef struct {
+  int dims[3];        /* nx, ny, nz > 0 */
+  double tau;         /* > 1/2; lambda_+ = -1/tau, nu = (tau - 1/2)/3 (Sec. 2.1) */
+  double magic;       /* Lambda = Lambda_+ Lambda_- (Sec. 3.1) fixing lambda_-; <= 0: SRT
+                         (lambda_- = lambda_+); default 3/16 */
+  double g[3];        /* body force per unit mass and step; F = rho_0 g */
+  double rho_G;       /* gas density: boundary pressure P_b = rho_G/3 (Eq. koerner) */
+  double sigma;       /* surface tension: rho_b = rho_G + 3 sigma kappa (Sec. 2.3) */
+  int rule;           /* FSLBM_FSK or FSLBM_FSL */
+  int compressible;   /* 1: rho_0 = rho (Qian); 0: rho_0 = 1 (He-Luo), default */
+  int linear_eq;      /* 1: drop the non-linear part N_q of e^+ (Stokes flow) */
+  double eps;         /* conversion threshold: fill if m > (1+eps) rho, empty if m < -eps rho */
+  int periodic[3];    /* 1 = periodic axis, 0 = half-way wall at both faces */
+  int zshift;         /* z offset added on a periodic x wrap (inclined films) */
+  int freeze;         /* 1 = frozen interface: no mass exchange, no conversions */
+  double delta_min;   /* lower clamp of the free-surface link fraction, default 0 */
+  int precision;      /* fslbm_precision */
+  void *stream;       /* cudaStream_t for all work of the handle; NULL = legacy default */
+} fslbm_params;
+
+/* Defaults: tau 0.8, magic 3/16, g 0, rho_G 1, sigma 0, FSL, rho_0 = 1,
+ * non-linear e^+, eps 1e-3, all axes walls, zshift 0, dynamic interface,
+ * delta_min 0, FP64, default stream.  dims are set to 0. */
+void fslbm_default_params(fslbm_params *p);
+
+/* Create a lattice with the paper's problem data (Eq. freeboundary:
+ * viscosity through tau, P_b through rho_G, sigma, gravity g) and the given
+ * rule; other parameters at their defaults.  *out receives the handle.
+ * Returns FSLBM_ERR_ARG for dims <= 0 or tau <= 1/2, FSLBM_ERR_OOM when the
+ * device state does not fit.  The state is all-gas until set. */
+int fslbm_create(const int dims[3], double tau, const double g[3], double rho_G, double sigma,
+                 int rule, fslbm_t **out);
+
+/* As fslbm_create with every parameter given.  FSL with |1 - tau| < 1e-3 is
+ * rejected (FSLBM_ERR_ARG): the library stores post-collision populations
+ * and recovers n^+ from them by dividing by 1 + lambda_+. */
+int fslbm_create_ex(const fslbm_params *p, fslbm_t **out);
+
+/* Set the state from cell flags, pre-collision populations f[19][N] (FP64),
+ * fill levels phi[N] (read on interface cells, and on gas cells of a frozen
+ * interface; m = phi * rho), and optional wall link fractions
+ * wall_delta[19][N] (the fraction delta_w in [0,1] of link q from fluid cell
+ * i to the wall it crosses, CLI rule; a negative entry or NULL = half-way
+ * bounce-back).  Synchronises.  Returns FSLBM_ERR_STATE when a liquid cell
+ * touches a gas cell or a flag is not one of the four cell kinds. */
+int fslbm_set_state(fslbm_t *h, const uint8_t *flags, const double *f, const double *phi,
+                    const double *wall_delta, int where);
+
+/* As fslbm_set_state, but the populations are built by the library:
+ * f = f^eq(rho, u) + noise (Eq. eqEven / eqOdd with u^eq = u), from rho[N],
+ * u[N][3] and an optional noise[19][N] (NULL = none). */
+int fslbm_init_equilibrium(fslbm_t *h, const uint8_t *flags, const double *rho, const double *u,
+                           const double *phi, const double *noise, const double *wall_delta,
+                           int where);
+
+/* Restore a state saved with fslbm_get_fields: flags, post-collision
+ * f~[19][N], mass m[N] (interface m; ignored elsewhere), phi[N], optional
+ * wall_delta.  Round-trips every precision bit-exactly. */
+int fslbm_set_state_post(fslbm_t *h, const uint8_t *flags, const double *f_post, const double *m,
+                         const double *phi, const double *wall_delta, int where);
+
+/* Advance n >= 0 time steps.  Asynchronous on the handle's stream: returns
+ * launch errors only; method faults appear at the next synchronising call. */
+int fslbm_step(fslbm_t *h, int n);
+
+/* Wait for the handle's stream; return the sticky device error, if any. */
+int fslbm_sync(fslbm_t *h);
+
+/* Copy the fields selected by mask (fslbm_field bits) into out[], one buffer
+ * per set bit in increasing bit order, host or device per `where`.
+ * Synchronises. */
+int fslbm_get_fields(fslbm_t *h, unsigned mask, void *const *out, int where);
+
+/* Total mass M = sum_liquid rho + sum_interface m + lost, and the lost
+ * ledger (excess mass that found no interface neighbour), in FP64 with a
+ * fixed reduction order.  Synchronises. */
+int fslbm_total_mass(fslbm_t *h, double *mass, double *lost);
+
+/* Mass balance of the last step, reduced inside the step kernels before the
+ * conversions (which conserve it): M(t) as above.  Synchronises. */
+int fslbm_step_mass(fslbm_t *h, double *mass);
+
+/* Conversions of the last step: out[0] filled (interface -> liquid),
+ * out[1] emptied (interface -> gas), out[2] new interface from gas, out[3]
+ * new interface from liquid; out[4] interface cells at the start of the
+ * step.  Synchronises. */
+int fslbm_counters(fslbm_t *h, long long out[5]);
+
+/* Per-kernel timing.  While on, fslbm_step records CUDA events on the
+ * handle's stream between the kernel groups of every step (a few
+ * microseconds of overhead per step).  Switching it on clears the totals. */
+int fslbm_timing(fslbm_t *h, int on);
+
+/* Average device time per step, in milliseconds, of each kernel group over
+ * the steps taken with timing on: ms[0] bulk stream-collide (k_bulk),
+ * ms[1] interface cells (k_iface), ms[2] mass-balance reduction, ms[3] the
+ * conversion kernels; *steps receives the number of timed steps.
+ * Synchronises. */
+int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
+
+/* Steps taken since the last set_state. */
+long long fslbm_time(const fslbm_t *h);
+
+/* Bytes of device memory held by the handle. */
+size_t fslbm_device_bytes(const fslbm_t *h);
+
+/* Text of the last error on this handle (static storage, never NULL). */
+const char *fslbm_last_error(const fslbm_t *h);
+
+/* Release the handle and its device memory.  NULL is a no-op. */
+void fslbm_destroy(fslbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSLBM_H */

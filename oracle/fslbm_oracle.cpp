@@ -69,6 +69,9 @@ inline double tan_of(const Dual& x) { return x.d; }
 using std::sqrt;
 
 template <class T> inline T absT(const T& x) { return val(x) < 0.0 ? T(-x) : x; }
+template <class T> inline T with_tangent(double v, double d);
+template <> inline double with_tangent<double>(double v, double) { return v; }
+template <> inline Dual with_tangent<Dual>(double v, double d) { return Dual(v, d); }
 template <class T> inline T clampT(const T& x, double lo, double hi) {
   if (val(x) < lo) return T(lo);
   if (val(x) > hi) return T(hi);
@@ -337,14 +340,18 @@ struct Sim {
 
   // Plane offset d (from the cell centre, along the unit normal n pointing
   // from liquid to gas) such that the liquid side {n.(x - x_c) <= d} fills the
-  // fraction ph of the unit cell.  Bisection on the value, then one Newton
-  // step in T so that a tangent (if any) gets the implicit derivative.
+  // fraction ph of the unit cell.  The inverse volume has a cube-root
+  // singularity at an empty or full corner (alpha ~ (6 m1 m2 m3 ph)^(1/3)), so
+  // the fill is first kept in [PH_REG, 1 - PH_REG]; the plane constant is the
+  // bisection result, and a tangent (if any) gets the implicit derivative
+  // d alpha = -(dV|_m - d ph) / V'(alpha).
+  static constexpr double PH_REG = 1e-9;
   static T plic_offset(const T n[3], T ph) {
     T ms[3] = {absT(n[0]), absT(n[1]), absT(n[2])};
     T L1 = ms[0] + ms[1] + ms[2];
     for (int a = 0; a < 3; ++a) ms[a] = ms[a] / L1;
     std::sort(ms, ms + 3, [](const T& a, const T& b) { return val(a) < val(b); });
-    ph = clampT(ph, 0.0, 1.0);
+    ph = clampT(ph, PH_REG, 1.0 - PH_REG);
     double lo = 0.0, hi = 1.0;
     for (int it = 0; it < 200; ++it) {
       double mid = 0.5 * (lo + hi);
@@ -354,10 +361,11 @@ struct Sim {
     double a0 = 0.5 * (lo + hi);
     T alpha = T(a0);
     T area = cube_area(alpha, ms);
-    if (val(area) > 0.0) alpha = alpha - (cube_volume(alpha, ms) - ph) / area + T(0.0);
-    // keep the value part exactly on the bisection result
-    T out = L1 * (alpha - T(0.5));
-    return out;
+    if (val(area) > 0.0) {
+      T corr = (cube_volume(alpha, ms) - ph) / area;
+      alpha = with_tangent<T>(a0, -tan_of(corr));
+    }
+    return L1 * (alpha - T(0.5));
   }
 
   // Parker-Youngs gradient: 3x3x3 stencil, weights (2-|o_b|)(2-|o_c|) for the
@@ -835,7 +843,8 @@ extern "C" int orc_step(void* hv, int n) {
   return st;
 }
 
-// Fields: 0 f (pre-collision, 19N), 1 f~ (post-collision, 19N), 2 m (N),
+// Fields: 0 f (pre-collision, 19N), 1 f~ (post-collision, 19N), 2 mass (N:
+// interface m, liquid rho),
 // 3 phi (N), 4 rho (N), 5 u (3N, cell-major u[3*i+a]).  Values of non-fluid
 // cells are 0.  tangent=1 returns the tangent part (dual handles only).
 template <class T>
@@ -856,13 +865,13 @@ static int get_impl(Sim<T>* s, int field, int tangent, double* out) {
   for (long i = 0; i < N; ++i) {
     bool fl = Sim<T>::fluid(s->flag[i]);
     T fq[Q], rho = T(0), U[3], u[3] = {T(0), T(0), T(0)};
-    if (fl && (field == 4 || field == 5)) {
+    if (fl && (field == 2 || field == 4 || field == 5)) {
       for (int q = 0; q < Q; ++q) fq[q] = s->f[(size_t)q * N + i];
       s->moments(fq, rho, U, u);
     }
     switch (field) {
-      case 2: put(i, fl ? s->m[i] : T(0)); break;
-      case 3: put(i, s->flag[i] == LIQ ? T(1.0) : (s->flag[i] == IFC ? s->phi[i] : T(0))); break;
+      case 2: put(i, s->flag[i] == IFC ? s->m[i] : (s->flag[i] == LIQ ? rho : T(0))); break;
+      case 3: put(i, s->flag[i] == LIQ ? T(1.0) : ((s->flag[i] == IFC || s->flag[i] == GAS) ? s->phi[i] : T(0))); break;
       case 4: put(i, rho); break;
       case 5: for (int a = 0; a < 3; ++a) put((size_t)3 * i + a, u[a]); break;
       default: return ERR_ARG;

@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 
@@ -25,11 +26,19 @@ F_PRE, F_POST, MASS, PHI, RHO, VEL = 0, 1, 2, 3, 4, 5
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    stamp = os.path.join(_BUILD, "STAMP")
+    try:
+        same_machine = open(stamp).read().strip() == platform.machine()
+    except OSError:
+        same_machine = False
+    if (force or not same_machine or not os.path.exists(_LIB_PATH)
+            or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC",
                                _SRC, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     return _LIB_PATH
 
 

@@ -296,7 +296,12 @@ def dam_break(nx=512, ny=256, nz=256, col_x=128, col_z=192, tau=0.51, g=1e-5,
     phi = inside.astype(np.float64)
     params = default_params(tau=tau, g=(0.0, 0.0, -g), rule=rule)
     params.update(kw)
-    flags = classify(dims, params["periodic"], 0, phi)
+    if any(params["periodic"]) or col_x >= nx or col_z >= nz:
+        flags = classify(dims, params["periodic"], 0, phi)
+    else:
+        # walled box: the column's cells on its two open faces touch gas
+        flags = np.where(inside, LIQUID, GAS).astype(np.uint8)
+        flags[inside & ((x == col_x - 1) | (z == col_z - 1))] = INTERFACE
     rho = np.where(inside, params["rho_G"] + 3.0 * g * (col_z - (z + 0.5)), params["rho_G"])
     ifc = flags == INTERFACE
     phi = np.where(ifc, 1.0, 0.0)

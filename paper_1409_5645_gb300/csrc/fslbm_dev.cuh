@@ -1,0 +1,326 @@
+// fslbm_dev.cuh -- device-side building blocks of the FSLBM step (sm_103a).
+//
+// Layout in HBM (one handle):
+//   flags  u8  [N]        cell kind (bits 0-3) + NEAR_BOUNDARY bit (static walls)
+//   mark   u8  [N]        conversion marks of the current step (zero between steps)
+//   fA, fB S   [19][N]    post-collision populations f~(t) / f~(t+1), SoA, x fastest
+//   m      f64 [N]        interface mass
+//   phiA/B R   [N]        fill level phi(t) / phi(t+1)
+//   wd     f64 [19][N]    wall link fractions (only when given)
+// S = double / float / half (f - w_q stored), R = double (FP64 form) or float.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fsl {
+
+// ---------------------------------------------------------------------------
+// D3Q19 (Sec. 4), public population order.  Tables as constexpr functions so
+// that fully unrolled loops fold them into immediates.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int q) {
+  return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+       : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int q) {
+  return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+       : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int q) {
+  return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+       : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+// each link is followed by its opposite
+__host__ __device__ constexpr int inv(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+template <class R>
+__host__ __device__ constexpr R wq(int q) {
+  return q == 0 ? R(1) / R(3) : (q <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+
+enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16 };
+enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16 };
+enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4 };
+
+// ---------------------------------------------------------------------------
+// Precision forms
+// ---------------------------------------------------------------------------
+enum { P64 = 0, P32 = 1, P16 = 2 };
+template <int P> struct Form;
+template <> struct Form<P64> { using S = double; using R = double; };
+template <> struct Form<P32> { using S = float; using R = float; };
+template <> struct Form<P16> { using S = __half; using R = float; };
+
+template <int P, int q>
+__device__ __forceinline__ typename Form<P>::R ld(const typename Form<P>::S* __restrict__ p, size_t k) {
+  if constexpr (P == P16) return __half2float(__ldg(p + k)) + wq<float>(q);
+  else return __ldg(p + k);
+}
+template <int P>
+__device__ __forceinline__ typename Form<P>::R ldq(const typename Form<P>::S* __restrict__ p, size_t k, int q) {
+  if constexpr (P == P16) return __half2float(p[k]) + wq<float>(q);
+  else return p[k];
+}
+template <int P, int q>
+__device__ __forceinline__ void st(typename Form<P>::S* __restrict__ p, size_t k, typename Form<P>::R v) {
+  if constexpr (P == P16) p[k] = __float2half_rn(v - wq<float>(q));
+  else p[k] = v;
+}
+template <int P>
+__device__ __forceinline__ void stq(typename Form<P>::S* __restrict__ p, size_t k, int q, typename Form<P>::R v) {
+  if constexpr (P == P16) p[k] = __float2half_rn(v - wq<float>(q));
+  else p[k] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Parameters passed by value to every kernel
+// ---------------------------------------------------------------------------
+struct Par {
+  int nx, ny, nz;
+  long long N;
+  int px, py, pz, zshift;
+  double lam_p, lam_m;     // TRT rates
+  double inv_1plp;         // 1/(1 + lambda_+), recovers n^+ from f~
+  double g[3];
+  double rho_G, sigma, eps, delta_min;
+  int rule, compressible, linear_eq, freeze;
+  int has_wd;
+};
+
+template <int P>
+struct View {
+  using S = typename Form<P>::S;
+  using R = typename Form<P>::R;
+  uint8_t* flags;
+  uint8_t* mark;
+  const S* fin;
+  S* fout;
+  double* m;
+  const R* phin;
+  R* phout;
+  const double* wd;  // wall link fractions (FP64 in every form)
+  // lists and counters
+  int* ilist;   // interface cells of this step
+  int* flist;   // fill
+  int* elist;   // empty
+  int* nglist;  // new from gas
+  int* nllist;  // new from liquid
+  int* rlist;   // excess receivers
+  int* cnt;     // [0] ilist [1] flist [2] elist [3] ng [4] nl [5] rl [6] filled [7] emptied
+  int cap;
+  double* share;
+  double* partials;  // block partial sums of the mass balance
+  double* lost;
+  int* err;
+};
+
+// ---------------------------------------------------------------------------
+// Neighbours: cell (x,y,z) + d with periodic wrap (x wrap shifts z), -1 past a
+// non-periodic face (half-way wall there).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long nbr(const Par& p, int x, int y, int z, int dx, int dy, int dz) {
+  int X = x + dx, Y = y + dy, Z = z + dz;
+  if ((unsigned)X >= (unsigned)p.nx) {
+    if (!p.px) return -1;
+    if (X < 0) { X += p.nx; Z += p.zshift; } else { X -= p.nx; Z -= p.zshift; }
+  }
+  if ((unsigned)Y >= (unsigned)p.ny) {
+    if (!p.py) return -1;
+    Y += (Y < 0) ? p.ny : -p.ny;
+  }
+  if ((unsigned)Z >= (unsigned)p.nz) {
+    if (!p.pz) return -1;
+    Z += (Z < 0) ? p.nz : -p.nz;
+  }
+  if ((unsigned)X >= (unsigned)p.nx || (unsigned)Y >= (unsigned)p.ny || (unsigned)Z >= (unsigned)p.nz) return -1;
+  return (long long)X + (long long)p.nx * ((long long)Y + (long long)p.ny * Z);
+}
+__device__ __forceinline__ void coords(const Par& p, long long i, int& x, int& y, int& z) {
+  long long s = (long long)p.nx * p.ny;
+  z = (int)(i / s);
+  long long r = i - (long long)z * s;
+  y = (int)(r / p.nx);
+  x = (int)(r - (long long)y * p.nx);
+}
+__device__ __forceinline__ uint8_t kind_at(const uint8_t* flags, long long j) {
+  return j < 0 ? (uint8_t)WALL : (uint8_t)(flags[j] & KIND);
+}
+__device__ __forceinline__ bool is_fluid(uint8_t k) { return k == LIQ || k == IFC; }
+
+// ---------------------------------------------------------------------------
+// Equilibria (Eq. eqEven / eqOdd), c_s^2 = 1/3:
+//   e_q^+ = w_q (rho + 3 N_q),  3 N_q = 3/2 rho_0 (3 (c.u)^2 - u.u)
+//   e_q^- = 3 w_q rho_0 (c.u^eq)
+// ---------------------------------------------------------------------------
+template <class R, int q>
+__device__ __forceinline__ R eplus(const Par& p, R rho, R r0, R ux, R uy, R uz, R usq) {
+  R e = wq<R>(q) * rho;
+  if (!p.linear_eq) {
+    R cu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
+    e += wq<R>(q) * R(1.5) * r0 * (R(3) * cu * cu - usq);
+  }
+  return e;
+}
+template <class R>
+__device__ __forceinline__ R eplus_q(const Par& p, int q, R rho, R r0, R ux, R uy, R uz, R usq) {
+  R w = q == 0 ? R(1) / R(3) : (q <= 6 ? R(1) / R(18) : R(1) / R(36));
+  R e = w * rho;
+  if (!p.linear_eq) {
+    R cu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
+    e += w * R(1.5) * r0 * (R(3) * cu * cu - usq);
+  }
+  return e;
+}
+template <class R, int q>
+__device__ __forceinline__ R eminus(R r0, R vx, R vy, R vz) {
+  R cu = R(cx(q)) * vx + R(cy(q)) * vy + R(cz(q)) * vz;
+  return R(3) * wq<R>(q) * r0 * cu;
+}
+
+// TRT collision of one cell (Eq. lbe2) in place: f <- f + l+ n^+ + l- n^-,
+// with u = U + g/2 in e^+ and u^eq = U - g/lambda_- in e^- (Sec. 2.1).
+// On return rho holds sum f and (ux,uy,uz) the velocity u of the
+// pre-collision state.
+template <class R>
+__device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux, R& uy, R& uz) {
+  R r = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    r += f[q];
+    if (cx(q)) jx += R(cx(q)) * f[q];
+    if (cy(q)) jy += R(cy(q)) * f[q];
+    if (cz(q)) jz += R(cz(q)) * f[q];
+  }
+  R r0 = p.compressible ? r : R(1);
+  R ir0 = R(1) / r0;
+  R Ux = jx * ir0, Uy = jy * ir0, Uz = jz * ir0;
+  R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
+  ux = Ux + R(0.5) * gx; uy = Uy + R(0.5) * gy; uz = Uz + R(0.5) * gz;
+  R ilm = R(1) / R(p.lam_m);
+  R vx = Ux - gx * ilm, vy = Uy - gy * ilm, vz = Uz - gz * ilm;
+  R usq = ux * ux + uy * uy + uz * uz;
+  R lp = R(p.lam_p), lm = R(p.lam_m);
+  R out[19];
+  {
+    R ep = eplus<R, 0>(p, r, r0, ux, uy, uz, usq);
+    out[0] = f[0] + lp * (f[0] - ep);
+  }
+#define FSL_PAIR(q)                                                       \
+  {                                                                       \
+    constexpr int qb = inv(q);                                            \
+    R ep = eplus<R, q>(p, r, r0, ux, uy, uz, usq);                        \
+    R em = eminus<R, q>(r0, vx, vy, vz);                                  \
+    R np = R(0.5) * (f[q] + f[qb]) - ep;                                  \
+    R nm = R(0.5) * (f[q] - f[qb]) - em;                                  \
+    out[q] = f[q] + lp * np + lm * nm;                                    \
+    out[qb] = f[qb] + lp * np - lm * nm;                                  \
+  }
+  FSL_PAIR(1) FSL_PAIR(3) FSL_PAIR(5) FSL_PAIR(7) FSL_PAIR(9)
+  FSL_PAIR(11) FSL_PAIR(13) FSL_PAIR(15) FSL_PAIR(17)
+#undef FSL_PAIR
+#pragma unroll
+  for (int q = 0; q < 19; ++q) f[q] = out[q];
+  rho = r;
+}
+
+// Moments of the pre-collision state recovered from post-collision f~:
+// sum f~ = rho and sum c f~ = rho_0 U + F, so u = U + g/2 = (sum c f~)/rho_0 - g/2.
+template <class R>
+__device__ __forceinline__ void moments_post(const Par& p, const R (&f)[19], R& rho, R& ux, R& uy, R& uz) {
+  R r = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    r += f[q];
+    if (cx(q)) jx += R(cx(q)) * f[q];
+    if (cy(q)) jy += R(cy(q)) * f[q];
+    if (cz(q)) jz += R(cz(q)) * f[q];
+  }
+  R ir0 = p.compressible ? R(1) / r : R(1);
+  ux = jx * ir0 - R(0.5) * R(p.g[0]);
+  uy = jy * ir0 - R(0.5) * R(p.g[1]);
+  uz = jz * ir0 - R(0.5) * R(p.g[2]);
+  rho = r;
+}
+
+// ---------------------------------------------------------------------------
+// Plane / unit-cube volume (piecewise cubic in the plane constant alpha for a
+// normal with sorted components m1 <= m2 <= m3, m1+m2+m3 = 1) and its slope.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R cube_vol_half(R a, R m1, R m2, R m3) {
+  // valid for 0 <= a <= 1/2
+  if (a <= R(0)) return R(0);
+  if (a <= m1) return a * a * a / (R(6) * m1 * m2 * m3);
+  R base = R(3) * a * a - R(3) * a * m1 + m1 * m1;
+  R den = R(6) * m2 * m3;
+  if (a <= m2) return base / den;
+  R s = a - m2;
+  R m12 = m1 + m2;
+  if (m3 >= m12) {
+    if (a <= m12) return (base - s * s * s / m1) / den;
+    return (a - R(0.5) * m12) / m3;
+  }
+  if (a <= m3) return (base - s * s * s / m1) / den;
+  R r = a - m3;
+  return (base - s * s * s / m1 - r * r * r / m1) / den;
+}
+template <class R>
+__device__ __forceinline__ R cube_vol(R a, R m1, R m2, R m3) {
+  if (a >= R(1)) return R(1);
+  if (a > R(0.5)) return R(1) - cube_vol_half(R(1) - a, m1, m2, m3);
+  return cube_vol_half(a, m1, m2, m3);
+}
+template <class R>
+__device__ __forceinline__ R cube_area_half(R a, R m1, R m2, R m3) {
+  if (a <= R(0)) return R(0);
+  if (a <= m1) return a * a / (R(2) * m1 * m2 * m3);
+  R base = R(6) * a - R(3) * m1;
+  R den = R(6) * m2 * m3;
+  if (a <= m2) return base / den;
+  R s = a - m2;
+  R m12 = m1 + m2;
+  if (m3 >= m12) {
+    if (a <= m12) return (base - R(3) * s * s / m1) / den;
+    return R(1) / m3;
+  }
+  if (a <= m3) return (base - R(3) * s * s / m1) / den;
+  R r = a - m3;
+  return (base - R(3) * s * s / m1 - R(3) * r * r / m1) / den;
+}
+template <class R>
+__device__ __forceinline__ R cube_area(R a, R m1, R m2, R m3) {
+  if (a >= R(1)) return R(0);
+  if (a > R(0.5)) return cube_area_half(R(1) - a, m1, m2, m3);
+  return cube_area_half(a, m1, m2, m3);
+}
+
+// Signed offset d (from the cell centre along the unit normal n, liquid on
+// the side n.(x - x_c) <= d) of the plane cutting volume fraction ph.  The
+// fill is kept in [1e-9, 1 - 1e-9] first: at an empty or full corner the
+// inverse volume grows like a cube root and would turn rounding of ph into
+// visible plane shifts.  Bisection on the plane constant.
+template <class R>
+__device__ R plic_offset(R nx_, R ny_, R nz_, R ph) {
+  R a0 = fabs(nx_), a1 = fabs(ny_), a2 = fabs(nz_);
+  R L1 = a0 + a1 + a2;
+  a0 /= L1; a1 /= L1; a2 /= L1;
+  // sort ascending
+  R t;
+  if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
+  if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
+  if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
+  const R lo_ph = R(1e-9), hi_ph = R(1) - R(1e-9);
+  ph = ph < lo_ph ? lo_ph : (ph > hi_ph ? hi_ph : ph);
+  R lo = R(0), hi = R(1);
+  constexpr int iters = sizeof(R) == 8 ? 96 : 48;
+#pragma unroll 1
+  for (int it = 0; it < iters; ++it) {
+    R mid = R(0.5) * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (cube_vol(mid, a0, a1, a2) < ph) lo = mid; else hi = mid;
+  }
+  return L1 * (R(0.5) * (lo + hi) - R(0.5));
+}
+
+}  // namespace fsl

@@ -1,0 +1,36 @@
+// fslbm_kernels.h -- launchers shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fslbm_dev.cuh"
+
+namespace fsl {
+
+template <int P>
+int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int iface_blocks, void* timing_handle);
+
+// records the handle's between-kernel timing event (host side, fslbm_api.cu)
+int fslbm_mark_between(void* handle);
+
+template <int P>
+int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks);
+
+int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, const double* add, double* out,
+                  cudaStream_t st);
+
+// state set-up and read-back (fslbm_state.cu)
+template <int P>
+int launch_init_pre(const Par& p, const View<P>& v, const double* f, const double* phi, const double* rho_in,
+                    const double* u_in, const double* noise, cudaStream_t st);
+template <int P>
+int launch_init_post(const Par& p, const View<P>& v, const double* f, const double* m, const double* phi,
+                     cudaStream_t st);
+int launch_prepare_flags(const Par& p, uint8_t* flags, int* err, cudaStream_t st);
+template <int P>
+int launch_fields(const Par& p, const View<P>& v, unsigned mask, void* const* out, cudaStream_t st);
+template <int P>
+int launch_total_mass(const Par& p, const View<P>& v, double* partials, long long nparts, double* tmp,
+                      int tmp_blocks, double* out, cudaStream_t st);
+
+}  // namespace fsl

@@ -1,0 +1,258 @@
+"""Python binding of the C interface in ``include/fslbm.h`` (argument
+marshalling only; every step of the method runs in the CUDA library).
+
+Arrays may be host NumPy arrays or CUDA ``torch.Tensor`` objects; device
+tensors are passed to the library as device pointers on the tensor's GPU,
+so no host round trip is made.  There is no fallback: if the CUDA library is
+not built or cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfslbm.so")
+
+FSK, FSL = 0, 1
+F64, F32, F16 = 0, 1, 2
+HOST, DEVICE = 0, 1
+FIELD_FLAGS, FIELD_F, FIELD_MASS, FIELD_PHI, FIELD_RHO, FIELD_U = 1, 2, 4, 8, 16, 32
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE", -5: "ERR_UNSTABLE",
+          -6: "ERR_OVERFLOW", -7: "ERR_TIMEOUT"}
+
+
+class FslbmError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("dims", C.c_int * 3), ("tau", C.c_double), ("magic", C.c_double), ("g", C.c_double * 3),
+                ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int), ("compressible", C.c_int),
+                ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
+                ("freeze", C.c_int), ("delta_min", C.c_double), ("precision", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libfslbm.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+            L = C.CDLL(LIB_PATH)
+            vp, ip, dp, u8p = C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p
+            L.fslbm_default_params.argtypes = [C.POINTER(Params)]
+            L.fslbm_default_params.restype = None
+            L.fslbm_create.argtypes = [C.POINTER(C.c_int), C.c_double, dp, C.c_double, C.c_double, ip,
+                                       C.POINTER(vp)]
+            L.fslbm_create_ex.argtypes = [C.POINTER(Params), C.POINTER(vp)]
+            L.fslbm_set_state.argtypes = [vp, u8p, vp, vp, vp, ip]
+            L.fslbm_init_equilibrium.argtypes = [vp, u8p, vp, vp, vp, vp, vp, ip]
+            L.fslbm_set_state_post.argtypes = [vp, u8p, vp, vp, vp, vp, ip]
+            L.fslbm_step.argtypes = [vp, ip]
+            L.fslbm_sync.argtypes = [vp]
+            L.fslbm_get_fields.argtypes = [vp, C.c_uint, C.POINTER(vp), ip]
+            L.fslbm_total_mass.argtypes = [vp, dp, dp]
+            L.fslbm_step_mass.argtypes = [vp, dp]
+            L.fslbm_counters.argtypes = [vp, C.POINTER(C.c_longlong)]
+            L.fslbm_timing.argtypes = [vp, ip]
+            L.fslbm_timing_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
+            L.fslbm_time.argtypes = [vp]
+            L.fslbm_time.restype = C.c_longlong
+            L.fslbm_device_bytes.argtypes = [vp]
+            L.fslbm_device_bytes.restype = C.c_size_t
+            L.fslbm_last_error.argtypes = [vp]
+            L.fslbm_last_error.restype = C.c_char_p
+            L.fslbm_destroy.argtypes = [vp]
+            L.fslbm_destroy.restype = None
+            _lib = L
+    return _lib
+
+
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+class _Arg:
+    """Keeps the buffers alive and yields (pointer, where)."""
+
+    def __init__(self):
+        self.keep = []
+        self.where = None
+
+    def __call__(self, a, dtype):
+        if a is None:
+            return None
+        if _is_torch_cuda(a):
+            import torch
+            tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+            t = a.contiguous()
+            if t.dtype != tdt:
+                raise TypeError(f"expected {tdt}, got {t.dtype}")
+            self._where(DEVICE)
+            self.keep.append(t)
+            return C.c_void_p(t.data_ptr())
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        self._where(HOST)
+        self.keep.append(arr)
+        return C.c_void_p(arr.ctypes.data)
+
+    def _where(self, w):
+        if self.where is None:
+            self.where = w
+        elif self.where != w:
+            raise ValueError("mixing host arrays and device tensors in one call")
+
+
+def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
+    P = Params()
+    lib().fslbm_default_params(C.byref(P))
+    for a in range(3):
+        P.dims[a] = int(dims[a])
+    P.tau = params.get("tau", P.tau)
+    P.magic = params.get("magic", P.magic)
+    g = params.get("g", (0.0, 0.0, 0.0))
+    per = params.get("periodic", (0, 0, 0))
+    for a in range(3):
+        P.g[a] = g[a]
+        P.periodic[a] = int(per[a])
+    P.rho_G = params.get("rho_G", P.rho_G)
+    P.sigma = params.get("sigma", P.sigma)
+    P.rule = int(params.get("rule", P.rule))
+    P.compressible = int(params.get("compressible", 0))
+    P.linear_eq = int(params.get("linear_eq", 0))
+    P.eps = params.get("eps", P.eps)
+    P.zshift = int(params.get("zshift", 0))
+    P.freeze = int(params.get("freeze", 0))
+    P.delta_min = params.get("delta_min", P.delta_min)
+    P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    P.stream = stream
+    return P
+
+
+class Lattice:
+    """One lattice on the current CUDA device (a handle of the C library)."""
+
+    def __init__(self, dims, params: dict, precision="f64", stream=None):
+        self.L = lib()
+        self.dims = tuple(int(d) for d in dims)
+        self.N = int(np.prod(self.dims))
+        self.params = dict(params)
+        self.precision = precision
+        self._P = params_struct(self.dims, self.params, precision, stream)
+        h = C.c_void_p()
+        rc = self.L.fslbm_create_ex(C.byref(self._P), C.byref(h))
+        if rc != 0:
+            raise FslbmError(rc, "fslbm_create_ex")
+        self.h = h
+
+    @classmethod
+    def from_case(cls, case, precision="f64", stream=None, **override):
+        p = dict(case["params"])
+        p.update(override)
+        lat = cls(case["dims"], p, precision, stream)
+        lat.init_equilibrium(case["flags"], case["rho"], case["u"], case["phi"], case.get("noise"),
+                             case.get("wall_delta"))
+        return lat
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise FslbmError(rc, f"{what}: {self.L.fslbm_last_error(self.h).decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.fslbm_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def init_equilibrium(self, flags, rho, u, phi, noise=None, wall_delta=None):
+        A = _Arg()
+        args = (A(flags, np.uint8), A(rho, np.float64), A(u, np.float64), A(phi, np.float64),
+                A(noise, np.float64), A(wall_delta, np.float64))
+        self._check(self.L.fslbm_init_equilibrium(self.h, *args, A.where), "init_equilibrium")
+
+    def set_state(self, flags, f, phi, wall_delta=None):
+        A = _Arg()
+        args = (A(flags, np.uint8), A(f, np.float64), A(phi, np.float64), A(wall_delta, np.float64))
+        self._check(self.L.fslbm_set_state(self.h, *args, A.where), "set_state")
+
+    def set_state_post(self, flags, f_post, m, phi, wall_delta=None):
+        A = _Arg()
+        args = (A(flags, np.uint8), A(f_post, np.float64), A(m, np.float64), A(phi, np.float64),
+                A(wall_delta, np.float64))
+        self._check(self.L.fslbm_set_state_post(self.h, *args, A.where), "set_state_post")
+
+    def step(self, n: int = 1):
+        self._check(self.L.fslbm_step(self.h, int(n)), "step")
+
+    def sync(self):
+        self._check(self.L.fslbm_sync(self.h), "sync")
+
+    def get(self, mask: int = 63, device=None) -> dict:
+        """Fields as NumPy arrays (or CUDA tensors when ``device`` is given)."""
+        N = self.N
+        spec = [(FIELD_FLAGS, "flags", (N,), np.uint8), (FIELD_F, "f", (19, N), np.float64),
+                (FIELD_MASS, "m", (N,), np.float64), (FIELD_PHI, "phi", (N,), np.float64),
+                (FIELD_RHO, "rho", (N,), np.float64), (FIELD_U, "u", (N, 3), np.float64)]
+        out, ptrs = {}, []
+        for bit, name, shape, dt in spec:
+            if not mask & bit:
+                continue
+            if device is not None:
+                import torch
+                t = torch.empty(shape, dtype=torch.uint8 if dt == np.uint8 else torch.float64, device=device)
+                out[name] = t
+                ptrs.append(t.data_ptr())
+            else:
+                a = np.empty(shape, dtype=dt)
+                out[name] = a
+                ptrs.append(a.ctypes.data)
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        self._check(self.L.fslbm_get_fields(self.h, mask, arr, DEVICE if device is not None else HOST), "get_fields")
+        return out
+
+    def total_mass(self):
+        M, L = C.c_double(), C.c_double()
+        self._check(self.L.fslbm_total_mass(self.h, C.byref(M), C.byref(L)), "total_mass")
+        return M.value, L.value
+
+    def step_mass(self) -> float:
+        M = C.c_double()
+        self._check(self.L.fslbm_step_mass(self.h, C.byref(M)), "step_mass")
+        return M.value
+
+    def counters(self):
+        c = (C.c_longlong * 5)()
+        self._check(self.L.fslbm_counters(self.h, c), "counters")
+        return list(c)
+
+    def timing(self, on: bool = True):
+        self._check(self.L.fslbm_timing(self.h, 1 if on else 0), "timing")
+
+    def timing_read(self):
+        """Average ms per step of (bulk, interface, reduction, conversions)."""
+        ms = (C.c_double * 4)()
+        n = C.c_longlong()
+        self._check(self.L.fslbm_timing_read(self.h, ms, C.byref(n)), "timing_read")
+        return list(ms), n.value
+
+    @property
+    def time(self) -> int:
+        return int(self.L.fslbm_time(self.h))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.L.fslbm_device_bytes(self.h))

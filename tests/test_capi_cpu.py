@@ -1,0 +1,77 @@
+"""The C interface without a GPU: the header's declarations, the built
+library's exported symbols, and the binding's refusal to run without it."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fslbm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fslbm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_1409_5645_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_step_api():
+    names = declared_functions()
+    for required in ("fslbm_create", "fslbm_create_ex", "fslbm_set_state", "fslbm_init_equilibrium",
+                     "fslbm_step", "fslbm_get_fields", "fslbm_total_mass", "fslbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    lib = ctypes.CDLL(built_lib)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fslbm_[a-z_0-9]+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_build_targets_sm103a_only():
+    from paper_1409_5645_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_default_params_and_argument_checks(built_lib):
+    from paper_1409_5645_gb300 import fslbm
+    L = fslbm.lib()
+    P = fslbm.Params()
+    L.fslbm_default_params(ctypes.byref(P))
+    assert P.tau == 0.8 and P.magic == pytest.approx(3 / 16) and P.rule == fslbm.FSL
+    assert P.eps == 1e-3 and P.delta_min == 0.0 and P.precision == fslbm.F64
+    h = ctypes.c_void_p()
+    bad = fslbm.Params()
+    L.fslbm_default_params(ctypes.byref(bad))
+    bad.dims[0], bad.dims[1], bad.dims[2] = 4, 4, 0          # empty lattice
+    assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.dims[2] = 4
+    bad.tau = 0.5                                            # tau must exceed 1/2
+    assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.tau = 1.0                                            # FSL cannot recover n^+ at tau = 1
+    assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.tau, bad.precision = 0.8, 7
+    assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
+    assert L.fslbm_step(None, 1) == -1
+    L.fslbm_last_error.restype = ctypes.c_char_p
+    assert L.fslbm_last_error(None) == b"NULL handle"
+    L.fslbm_destroy(None)
+
+
+def test_binding_refuses_without_library(monkeypatch, tmp_path):
+    from paper_1409_5645_gb300 import fslbm
+    monkeypatch.setattr(fslbm, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(fslbm, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        fslbm.lib()

@@ -1,0 +1,141 @@
+"""Parity of the FP64 CUDA path with the FP64 oracle, through the C interface.
+
+Bar: cell flags (and so every conversion) bit-exact; post-collision
+populations, interface mass and fill levels within 1e-12 relative to the
+field's largest magnitude, after every compared step.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1409_5645_gb300 import cases, fslbm
+from tests.gpu_util import compare, run_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_film_every_step(rule):
+    """Gravity-driven film 4x4x32, h=20, tau=0.8, g=1e-6 along x, seeded noise
+    1e-8: every step for 100 steps, then every 250 steps to 5000."""
+    c = cases.film(rule=rule)
+    o = Oracle.from_case(c)
+    g = fslbm.Lattice.from_case(c)
+    compare(o, g, where="t=0")
+    for s in range(1, 5001):
+        o.step(1)
+        g.step(1)
+        if s <= 100 or s % 250 == 0:
+            compare(o, g, where=f"t={s}")
+    Mo, _ = o.total_mass()
+    Mg, _ = g.total_mass()
+    assert abs(Mg - Mo) <= 1e-12 * Mo
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_inclined_film_cli_wall_and_shifted_wrap(rule):
+    """Inclined film (slope 1/2, x wrap with z-shift, CLI wall link fractions,
+    frozen interface with partial fills in gas cells)."""
+    c = cases.inclined_film(h=8, rule=rule)
+    run_parity(c, 400, every=20, check_mass=False)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_dam_break_conversions_every_step(rule):
+    """Dam-break miniature 24x8x16 with fills, empties and new cells."""
+    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=rule)
+    _, _, conv = run_parity(c, 300, every=1)
+    assert conv[0] > 0 and conv[2] > 0
+
+
+def test_dam_break_ragged_sizes():
+    """Lattice sizes that fill no block evenly (37 x 13 x 21), FSL."""
+    c = cases.dam_break(nx=37, ny=13, nz=21, col_x=11, col_z=15, tau=0.56, g=3e-4, rule=1)
+    _, _, conv = run_parity(c, 200, every=1)
+    assert conv[0] > 0
+
+
+@pytest.mark.parametrize("variant", [dict(compressible=1), dict(linear_eq=1), dict(magic=-1.0)])
+def test_equilibrium_and_collision_variants(variant):
+    """rho_0 = rho, linear equilibrium, and SRT (lambda_- = lambda_+)."""
+    c = cases.dam_break(nx=20, ny=6, nz=14, col_x=7, col_z=10, tau=0.7, g=2e-4, rule=1, **variant)
+    run_parity(c, 150, every=5)
+
+
+def test_periodic_blob_uniform_flow():
+    """Periodic box, liquid blob advected by a uniform flow: wrap on every
+    axis, curvature-free closures, conversions on all sides."""
+    n = 16
+    dims = (n, n, n)
+    N = n ** 3
+    i = np.arange(N)
+    x, y, z = i % n + 0.5, (i // n) % n + 0.5, i // (n * n) + 0.5
+    r = np.sqrt((x - 8.2) ** 2 + (y - 7.7) ** 2 + ((z - 8.1) / 0.8) ** 2)
+    phi = np.clip(5.3 - r + 0.5, 0.0, 1.0)
+    params = cases.default_params(tau=0.7, rule=1, periodic=(1, 1, 1), g=(1e-4, 0.0, -5e-5))
+    flags = cases.classify(dims, params["periodic"], 0, phi)
+    u = np.tile(np.array([0.02, -0.015, 0.01]), (N, 1))
+    c = cases.Case(dims=dims, params=params, flags=flags, rho=np.ones(N), u=u,
+                   phi=np.where(flags == 2, phi, 0.0), noise=cases.uniform(7, 19 * N, 1e-4), wall_delta=None)
+    _, _, conv = run_parity(c, 150, every=1)
+    assert conv[0] + conv[1] > 0
+
+
+def test_standing_wave_with_surface_tension():
+    """Small standing capillary-gravity wave: curvature from heights enters
+    rho_b = rho_G + 3 sigma kappa."""
+    c = cases.standing_wave(n=24, depth=12.0, amp=1.5, tau=0.6, g=1e-4, sigma=5e-3, phi_noise=1e-4)
+    run_parity(c, 150, every=5)
+
+
+def test_checkpoint_roundtrip_bit_exact():
+    """get_fields -> set_state_post into a new handle -> continue: identical."""
+    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1)
+    for prec in ("f64", "f32", "f16"):
+        a = fslbm.Lattice.from_case(c, precision=prec)
+        a.step(50)
+        st = a.get(fslbm.FIELD_FLAGS | fslbm.FIELD_F | fslbm.FIELD_MASS | fslbm.FIELD_PHI)
+        b = fslbm.Lattice(c["dims"], c["params"], precision=prec)
+        b.set_state_post(st["flags"], st["f"], st["m"], st["phi"])
+        a.step(40)
+        b.step(40)
+        ga, gb = a.get(), b.get()
+        for k in ga:
+            assert np.array_equal(ga[k], gb[k]), (prec, k)
+
+
+def test_device_pointer_path_matches_host_path():
+    import torch
+    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1)
+    a = fslbm.Lattice.from_case(c)
+    dev = torch.device("cuda:0")
+    b = fslbm.Lattice(c["dims"], c["params"])
+    b.init_equilibrium(torch.from_numpy(c["flags"]).to(dev), torch.from_numpy(c["rho"]).to(dev),
+                       torch.from_numpy(c["u"]).to(dev), torch.from_numpy(c["phi"]).to(dev))
+    a.step(30)
+    b.step(30)
+    ga = a.get()
+    gb = b.get(device=dev)
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k].cpu().numpy()), k
+
+
+def test_invariant_violation_and_instability_are_reported():
+    c = cases.dam_break(nx=12, ny=6, nz=10, col_x=5, col_z=6, tau=0.6, g=1e-4)
+    flags = c["flags"].copy()
+    # a liquid cell touching gas
+    i = np.where(flags == cases.INTERFACE)[0][0]
+    flags[i] = cases.LIQUID
+    g = fslbm.Lattice(c["dims"], c["params"])
+    with pytest.raises(fslbm.FslbmError) as e:
+        g.init_equilibrium(flags, c["rho"], c["u"], c["phi"])
+    assert e.value.code == -4
+    # a NaN population: the next synchronising call reports instability
+    g2 = fslbm.Lattice(c["dims"], c["params"])
+    rho = c["rho"].copy()
+    rho[np.where(c["flags"] == cases.LIQUID)[0][3]] = np.nan
+    g2.init_equilibrium(c["flags"], rho, c["u"], c["phi"])
+    g2.step(2)
+    with pytest.raises(fslbm.FslbmError) as e:
+        g2.sync()
+    assert e.value.code == -5

@@ -304,11 +304,14 @@ def test_plic_roundtrip_and_aligned_case():
         if rng.random() < 0.3:
             n[rng.integers(3)] = 0.0
         n /= np.linalg.norm(n)
-        phi = rng.random()
+        phi = 1e-6 + (1 - 2e-6) * rng.random()
         d = plic_offset(n, phi)
         assert cube_volume(n, d) == pytest.approx(phi, abs=1e-13)
     for phi in (0.0, 0.25, 0.5, 0.9, 1.0):
-        assert plic_offset(np.array([0.0, 0.0, 1.0]), phi) == pytest.approx(phi - 0.5, abs=1e-14)
+        # the fill is kept 1e-9 away from an empty / full cell
+        assert plic_offset(np.array([0.0, 0.0, 1.0]), phi) == pytest.approx(phi - 0.5, abs=1.1e-9)
+    for phi in (0.25, 0.5, 0.9):
+        assert plic_offset(np.array([0.0, 0.0, 1.0]), phi) == pytest.approx(phi - 0.5, abs=1e-15)
 
 
 def test_height_function_normal_exact_for_planes():
@@ -378,3 +381,12 @@ def test_splitmix64_reference_value():
     """SplitMix64 seeded with 0: first output 0xE220A8397B1DCDAF (published
     reference sequence)."""
     assert int(cases.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+
+
+def test_dam_break_fast_flags_match_generic_classifier():
+    c = cases.dam_break(nx=20, ny=6, nz=14, col_x=7, col_z=9)
+    phi = np.zeros(c.N)
+    x = np.arange(c.N) % 20
+    z = np.arange(c.N) // (20 * 6)
+    phi[(x < 7) & (z < 9)] = 1.0
+    assert np.array_equal(c["flags"], cases.classify(c["dims"], (0, 0, 0), 0, phi))
