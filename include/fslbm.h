@@ -102,6 +102,9 @@ typedef struct {
   int periodic[3];    /* 1 = periodic axis, 0 = half-way wall at both faces */
   int zshift;         /* z offset added on a periodic x wrap (inclined films) */
   int freeze;         /* 1 = frozen interface: no mass exchange, no conversions */
+  int cleanup;        /* isolated-cell rules (Thuerey): bit 1 fills an interface cell with no gas
+                         neighbour, bit 2 empties an interface cell with no liquid/interface
+                         neighbour (its mass goes to the lost ledger if no receiver); default 3 */
   double delta_min;   /* lower clamp of the free-surface link fraction, default 0 */
   int precision;      /* fslbm_precision */
   void *stream;       /* cudaStream_t for all work of the handle; NULL = legacy default */
@@ -109,7 +112,7 @@ typedef struct {
 
 /* Defaults: tau 0.8, magic 3/16, g 0, rho_G 1, sigma 0, FSL, rho_0 = 1,
  * non-linear e^+, eps 1e-3, all axes walls, zshift 0, dynamic interface,
- * delta_min 0, FP64, default stream.  dims are set to 0. */
+ * cleanup 3, delta_min 0, FP64, default stream.  dims are set to 0. */
 void fslbm_default_params(fslbm_params *p);
 
 /* Create a lattice with the paper's problem data (Eq. freeboundary:
@@ -186,6 +189,39 @@ int fslbm_timing(fslbm_t *h, int on);
  * conversion kernels; *steps receives the number of timed steps.
  * Synchronises. */
 int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
+
+/* ---- Differentiation: hand-written adjoint -------------------------------
+ * The differentiated map runs from the initial populations of the current
+ * state (as set by fslbm_init_equilibrium / fslbm_set_state, whose collision
+ * is included) through nsteps time steps to an objective J, at fixed cell
+ * flags: every discrete decision of the forward pass (flags, the height-
+ * function or plane-fit branch, the dominant axis, clamps of delta) is held.
+ * Supported: rho_0 = 1, sigma = 0, and no cell conversion inside the window
+ * (FSLBM_ERR_STATE otherwise).  Parameters: nu = (tau - 1/2)/3 with the magic
+ * parameter Lambda held fixed, g, and the initial fill levels phi0 of
+ * interface cells (m0 = phi0 rho0). */
+enum fslbm_objective {
+  FSLBM_OBJ_SURFACE_UX = 0, /* mean u_x over interface cells at the end */
+  FSLBM_OBJ_FLUX_X = 1      /* sum over liquid and interface cells of phi u_x, divided by nx */
+};
+
+/* Forward pass: run nsteps >= 1 steps from the current state with a full
+ * checkpoint (f~, m, phi) every K >= 1 steps, and return J.  Holds
+ * ceil(nsteps/K) checkpoints on the device until the handle's state is set
+ * again or the handle is destroyed. */
+int fslbm_adjoint_forward(fslbm_t *h, int nsteps, int K, int objective, double *J);
+
+/* Reverse pass (once per forward pass): recompute each K-step segment from
+ * its checkpoint, storing its states, and run the adjoint step kernels
+ * backwards.  Returns dJ/dnu, dJ/dg[3], and dJ/dphi0[N] (zero off interface
+ * cells; host or device per `where`; NULL to skip).  Afterwards the handle
+ * holds the state of step min(K, nsteps). */
+int fslbm_adjoint_backward(fslbm_t *h, double *dJ_dnu, double dJ_dg[3], double *dJ_dphi0, int where);
+
+/* Costs of the last differentiation: device milliseconds per forward step
+ * and per adjoint step (segment recomputation excluded), and the device bytes
+ * held (lattice + checkpoints + adjoint buffers). */
+int fslbm_adjoint_stats(fslbm_t *h, double *fwd_ms_per_step, double *adj_ms_per_step, size_t *peak_bytes);
 
 /* Steps taken since the last set_state. */
 long long fslbm_time(const fslbm_t *h);

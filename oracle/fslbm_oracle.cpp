@@ -122,6 +122,7 @@ struct Params {
   int periodic[3];   // 1 = periodic axis, 0 = half-way wall at the face
   int zshift;        // z offset applied on a periodic x wrap
   int freeze;        // 1 = fixed flags and fill levels (no mass exchange, no conversion)
+  int cleanup;       // bit 1: no gas neighbour -> fill; bit 2: no fluid neighbour -> empty
   double delta_min;  // lower clamp of the free-surface link fraction (0: FSL needs delta >= 0)
 };
 
@@ -612,7 +613,8 @@ struct Sim {
 
   // Cell conversions after the mass update (reading of Koerner et al. /
   // Thuerey as cited in Sec. 4.4; the paper gives no details):
-  //  F = {interface : m > (1+eps) rho}, E = {interface : m < -eps rho}
+  //  F = {interface : m > (1+eps) rho, or no gas neighbour (cleanup bit 1)},
+  //  E = {interface : m < -eps rho, or no liquid/interface neighbour (bit 2)}
   //  1. drop from E every cell next to a cell of F;
   //  2. gas neighbours of F become interface, f = f^eq(mean rho, mean u) over
   //     their liquid/interface neighbours (q order), m = 0;
@@ -625,8 +627,15 @@ struct Sim {
     std::vector<uint8_t> isF(NN, 0), isE(NN, 0), isNG(NN, 0), isNL(NN, 0);
     for (long i = 0; i < NN; ++i) {
       if (flag[i] != IFC) continue;
-      if (val(m[i]) > (1.0 + p.eps) * val(rho1[i])) isF[i] = 1;
-      else if (val(m[i]) < -p.eps * val(rho1[i])) isE[i] = 1;
+      bool any_gas = false, any_fluid = false;
+      for (int q = 1; q < Q; ++q) {
+        uint8_t tj = type(nbq(i, q, 1));
+        any_gas |= tj == GAS;
+        any_fluid |= fluid(tj);
+      }
+      // thresholds, plus Thuerey's isolated-cell rules (cleanup bits)
+      if (val(m[i]) > (1.0 + p.eps) * val(rho1[i]) || ((p.cleanup & 1) && !any_gas)) isF[i] = 1;
+      else if (val(m[i]) < -p.eps * val(rho1[i]) || ((p.cleanup & 2) && !any_fluid)) isE[i] = 1;
     }
     // 1.
     for (long i = 0; i < NN; ++i) {

@@ -1,0 +1,811 @@
+// fslbm_adjoint.cu -- hand-written adjoint of the FSLBM step and the
+// checkpointed reverse sweep behind fslbm_adjoint_forward / _backward.
+//
+// The forward step maps the stored state (f~(t), m(t), phi(t)) to
+// (f~(t+1), m(t+1), phi(t+1)) for fixed cell flags.  Its adjoint is taken in
+// two kernels per step:
+//   k_adj_local   per fluid cell x: recompute the cell's forward step (pull,
+//                 wall and free-surface closures, mass exchange, collision),
+//                 then reverse it.  Writes the adjoint of the populations the
+//                 cell read from itself ("own", O) and of the populations it
+//                 pulled from its neighbours (P), the adjoint of m(t), and
+//                 adds adjoints of phi(t) of itself and of the neighbours it
+//                 read (mass-exchange weights, height functions) with atomics.
+//   k_adj_gather  reverse of the pull: abar_q(y) = O_q(y) + P_q(y + c_q).
+// Parameters: lambda_+, lambda_- (-> nu with Lambda fixed) and g, reduced per
+// block.  Interface decisions (flags, the height-function/PLIC branch, the
+// dominant axis, clamps of delta) are held fixed: a clamped delta or a cell
+// whose plane came from the PLIC fallback passes no derivative to phi.
+// Supported: rho_0 = 1, sigma = 0, no conversions inside the window.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "fslbm.h"
+#include "fslbm_dev.cuh"
+#include "fslbm_handle.h"
+#include "fslbm_kernels.h"
+
+using namespace fsl;
+
+struct AdjointState {
+  int nsteps = 0, K = 1, objective = 0, nck = 0;
+  size_t fbytes = 0, rbytes = 0;
+  void* ck_f = nullptr;
+  double* ck_m = nullptr;
+  void* ck_phi = nullptr;
+  void* seg_f = nullptr;
+  double* seg_m = nullptr;
+  void* seg_phi = nullptr;
+  double* abar[2] = {nullptr, nullptr};
+  double* P = nullptr;
+  double* mbar[2] = {nullptr, nullptr};
+  double* phibar[2] = {nullptr, nullptr};
+  double* theta = nullptr;  // [0] lambda_+ [1] lambda_- [2..4] g
+  double* red = nullptr;    // objective reductions
+  double* dphi0 = nullptr;
+  int conv0 = 0;
+  double J = 0.0, gseed = 0.0;
+  double fwd_ms = 0.0, adj_ms = 0.0;
+  size_t bytes = 0;
+  bool ready = false;
+};
+
+namespace fsl {
+
+template <int P>
+struct AdjView {
+  using S = typename Form<P>::S;
+  using R = typename Form<P>::R;
+  const uint8_t* flags;
+  const S* f;
+  const double* m;
+  const R* phi;
+  const double* wd;
+  const double* abar_in;
+  const double* mbar_in;
+  const double* phibar_in;
+  double* abar_out;
+  double* Pb;
+  double* mbar_out;
+  double* phibar_out;
+  double* theta;
+};
+
+// d e_q^+ / d u for rho_0 = 1: w_q (9 (c.u) c - 3 u); zero for the linear equilibrium
+__device__ __forceinline__ void deplus_du(const Par& p, int q, double ux, double uy, double uz, double g,
+                                          double (&ub)[3]) {
+  if (p.linear_eq) return;
+  double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  double cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+  ub[0] += g * w * (9.0 * cu * cx(q) - 3.0 * ux);
+  ub[1] += g * w * (9.0 * cu * cy(q) - 3.0 * uy);
+  ub[2] += g * w * (9.0 * cu * cz(q) - 3.0 * uz);
+}
+
+__device__ __forceinline__ double eplus_d(const Par& p, int q, double rho, double ux, double uy, double uz) {
+  double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  double e = w * rho;
+  if (!p.linear_eq) {
+    double cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+    e += w * 1.5 * (3.0 * cu * cu - (ux * ux + uy * uy + uz * uz));
+  }
+  return e;
+}
+
+// Reverse of the TRT collision (Eq. lbe2, rho_0 = 1) at pre-collision f with
+// output adjoint ab: adds to fb and to th (lambda_+, lambda_-, g).
+__device__ void collide_rev(const Par& p, const double (&f)[19], const double (&ab)[19], double (&fb)[19],
+                            double (&th)[5]) {
+  const double lp = p.lam_p, lm = p.lam_m;
+  const double g0 = p.g[0], g1 = p.g[1], g2 = p.g[2];
+  double r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    r += f[q];
+    jx += cx(q) * f[q];
+    jy += cy(q) * f[q];
+    jz += cz(q) * f[q];
+  }
+  const double ux = jx + 0.5 * g0, uy = jy + 0.5 * g1, uz = jz + 0.5 * g2;
+  const double vx = jx - g0 / lm, vy = jy - g1 / lm, vz = jz - g2 / lm;
+  double rb = 0, ub[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 19; ++q) fb[q] += ab[q];
+  {  // rest population: out0 = f0 + l+ (f0 - e0+)
+    double e0 = eplus_d(p, 0, r, ux, uy, uz);
+    double np = f[0] - e0;
+    double npb = lp * ab[0];
+    th[0] += np * ab[0];
+    fb[0] += npb;
+    rb += (1.0 / 3.0) * (-npb);
+    deplus_du(p, 0, ux, uy, uz, -npb, ub);
+  }
+#pragma unroll
+  for (int q = 1; q < 19; q += 2) {
+    const int qb = q + 1;
+    double w = q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0;
+    double ep = eplus_d(p, q, r, ux, uy, uz);
+    double em = 3.0 * w * (cx(q) * vx + cy(q) * vy + cz(q) * vz);
+    double np = 0.5 * (f[q] + f[qb]) - ep;
+    double nm = 0.5 * (f[q] - f[qb]) - em;
+    double npb = lp * (ab[q] + ab[qb]);
+    double nmb = lm * (ab[q] - ab[qb]);
+    th[0] += np * (ab[q] + ab[qb]);
+    th[1] += nm * (ab[q] - ab[qb]);
+    fb[q] += 0.5 * npb + 0.5 * nmb;
+    fb[qb] += 0.5 * npb - 0.5 * nmb;
+    // e^+: -npb;  e^-: -nmb
+    rb += w * (-npb);
+    deplus_du(p, q, ux, uy, uz, -npb, ub);
+    vb[0] += 3.0 * w * cx(q) * (-nmb);
+    vb[1] += 3.0 * w * cy(q) * (-nmb);
+    vb[2] += 3.0 * w * cz(q) * (-nmb);
+  }
+  // u = U + g/2, v = U - g/lambda_-, U = j
+  double Ub[3] = {ub[0] + vb[0], ub[1] + vb[1], ub[2] + vb[2]};
+  th[2] += 0.5 * ub[0] - vb[0] / lm;
+  th[3] += 0.5 * ub[1] - vb[1] / lm;
+  th[4] += 0.5 * ub[2] - vb[2] / lm;
+  th[1] += (g0 * vb[0] + g1 * vb[1] + g2 * vb[2]) / (lm * lm);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) fb[q] += rb + cx(q) * Ub[0] + cy(q) * Ub[1] + cz(q) * Ub[2];
+}
+
+__device__ __forceinline__ void block_add(double (&th)[5], double* out) {
+  __shared__ double red[4][5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double v = th[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    double s = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+    if (s != 0.0) atomicAdd(out + threadIdx.x, s);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
+  using R = typename Form<P>::R;
+  const size_t N = (size_t)p.N;
+  double th[5] = {0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t kc = a.flags[i] & KIND;
+    if (!is_fluid(kc)) {
+#pragma unroll
+      for (int q = 0; q < 19; ++q) { a.abar_out[q * N + i] = 0.0; a.Pb[q * N + i] = 0.0; }
+      a.mbar_out[i] = 0.0;
+      continue;
+    }
+    int x, y, z;
+    coords(p, i, x, y, z);
+    double own[19], F[19], f[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) own[q] = (double)ldq<P>(a.f, q * N + i, q);
+    unsigned wallm = 0u, gasm = 0u;
+    long long src[19];
+    F[0] = own[0];
+    src[0] = i;
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      long long s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
+      src[q] = s;
+      uint8_t ks = kind_at(a.flags, s);
+      if (is_fluid(ks)) F[q] = (double)ldq<P>(a.f, q * N + s, q);
+      else if (ks == WALL) { wallm |= 1u << q; F[q] = 0.0; }
+      else { gasm |= 1u << q; F[q] = 0.0; }
+    }
+#pragma unroll
+    for (int q = 0; q < 19; ++q) f[q] = F[q];
+    // own moments at t (rho_0 = 1): rho_t = sum f~, u_t = sum c f~ - g/2
+    double rt = 0, tx = 0, ty = 0, tz = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      rt += own[q];
+      tx += cx(q) * own[q];
+      ty += cy(q) * own[q];
+      tz += cz(q) * own[q];
+    }
+    const double utx = tx - 0.5 * p.g[0], uty = ty - 0.5 * p.g[1], utz = tz - 0.5 * p.g[2];
+    const bool ifc = kc == IFC;
+    const double phic = ifc ? (double)a.phi[i] : 1.0;
+    const bool dyn = ifc && !p.freeze;
+    // mass exchange
+    double dm = 0.0;
+    if (dyn) {
+#pragma unroll
+      for (int q = 1; q < 19; ++q) {
+        if ((wallm | gasm) & (1u << q)) continue;
+        uint8_t ks = a.flags[src[q]] & KIND;
+        double sw = (ks == LIQ) ? 1.0 : 0.5 * (phic + (double)a.phi[src[q]]);
+        dm += sw * (F[q] - own[inv(q)]);
+      }
+    }
+    // wall closures
+    double kw[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) kw[q] = 0.0;
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      if (!(wallm & (1u << q))) continue;
+      const int pq = inv(q);
+      double val = own[pq];
+      if (p.has_wd) {
+        double dw = a.wd[(size_t)pq * N + i];
+        bool upf = !((wallm | gasm) & (1u << pq));
+        if (dw >= 0.0 && upf) {
+          kw[q] = (1.0 - 2.0 * dw) / (1.0 + 2.0 * dw);
+          val += kw[q] * (F[pq] - own[q]);
+        }
+      }
+      f[q] = val;
+    }
+    // free-surface closures (forward, keeping what the reverse needs)
+    Geo<R> G;
+    double dl[19], npl[19], et[19];
+    bool fsl[19];
+    const double lp = p.lam_p, inv1 = p.inv_1plp;
+    if (gasm) {
+      geometry<R>(p, a.flags, a.phi, x, y, z, (R)phic, G);
+#pragma unroll
+      for (int q = 1; q < 19; ++q) {
+        fsl[q] = false;
+        if (!(gasm & (1u << q))) continue;
+        const int pq = inv(q);
+        double eb = eplus_d(p, pq, p.rho_G, utx, uty, utz);
+        bool upf = !((wallm | gasm) & (1u << pq));
+        if (p.rule == 0 || !upf) {
+          f[q] = -own[pq] + 2.0 * eb;
+        } else {
+          double d_ = 0.5;
+          if (G.ok) {
+            double cn = cx(pq) * (double)G.n[0] + cy(pq) * (double)G.n[1] + cz(pq) * (double)G.n[2];
+            if (cn > 0.0) {
+              d_ = (double)G.d / cn;
+              d_ = d_ < p.delta_min ? p.delta_min : (d_ > 1.0 ? 1.0 : d_);
+            }
+          }
+          dl[q] = d_;
+          et[q] = eplus_d(p, pq, rt, utx, uty, utz);
+          npl[q] = (0.5 * (own[pq] + own[q]) - et[q]) * inv1;
+          double C = lp * (0.5 + d_) - 2.0 * lp;
+          f[q] = (0.5 - d_) * own[pq] + 0.5 * own[q] + (d_ - 1.0) * F[pq] + C * npl[q] + eb;
+          fsl[q] = true;
+        }
+      }
+    }
+    double rho1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) rho1 += f[q];
+
+    // ---------------- reverse ----------------
+    double ab[19], fb[19], ob[19], Fb[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      ab[q] = a.abar_in[q * N + i];
+      fb[q] = 0.0; ob[q] = 0.0; Fb[q] = 0.0;
+    }
+    double phib_self = 0.0, mb1 = 0.0, rho1b = 0.0;
+    if (dyn) {
+      const double m1 = a.m[i] + dm;
+      const double pb = a.phibar_in[i];
+      mb1 = a.mbar_in[i] + pb / rho1;
+      rho1b = -pb * m1 / (rho1 * rho1);
+    } else if (ifc) {
+      phib_self += a.phibar_in[i];  // frozen interface: phi(t+1) = phi(t)
+    }
+    collide_rev(p, f, ab, fb, th);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) fb[q] += rho1b;
+    a.mbar_out[i] = dyn ? mb1 : 0.0;
+    if (dyn) {
+      const double dmb = mb1;
+#pragma unroll
+      for (int q = 1; q < 19; ++q) {
+        if ((wallm | gasm) & (1u << q)) continue;
+        uint8_t ks = a.flags[src[q]] & KIND;
+        double sw = (ks == LIQ) ? 1.0 : 0.5 * (phic + (double)a.phi[src[q]]);
+        Fb[q] += sw * dmb;
+        ob[inv(q)] -= sw * dmb;
+        if (ks == IFC) {
+          double c = 0.5 * dmb * (F[q] - own[inv(q)]);
+          phib_self += c;
+          atomicAdd(a.phibar_out + src[q], c);
+        }
+      }
+    }
+    // wall closures
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      if (!(wallm & (1u << q))) continue;
+      const int pq = inv(q);
+      ob[pq] += fb[q];
+      if (kw[q] != 0.0) {
+        Fb[pq] += kw[q] * fb[q];
+        ob[q] -= kw[q] * fb[q];
+      }
+    }
+    // free-surface closures
+    double utb[3] = {0, 0, 0}, rtb = 0.0;
+    double Hbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool geo_used = false;
+    if (gasm) {
+#pragma unroll
+      for (int q = 1; q < 19; ++q) {
+        if (!(gasm & (1u << q))) continue;
+        const int pq = inv(q);
+        const double fbq = fb[q];
+        if (!fsl[q]) {  // FSK: f_q = -f~_p + 2 e_p^+(rho_b, u_t)
+          ob[pq] -= fbq;
+          deplus_du(p, pq, utx, uty, utz, 2.0 * fbq, utb);
+          continue;
+        }
+        const double d_ = dl[q];
+        ob[pq] += (0.5 - d_) * fbq;
+        ob[q] += 0.5 * fbq;
+        Fb[pq] += (d_ - 1.0) * fbq;
+        const double C = lp * (0.5 + d_) - 2.0 * lp;
+        th[0] += fbq * (d_ - 1.5) * npl[q];
+        deplus_du(p, pq, utx, uty, utz, fbq, utb);  // e_p^+(rho_b, u_t)
+        const double nb = C * fbq;
+        ob[pq] += 0.5 * nb * inv1;
+        ob[q] += 0.5 * nb * inv1;
+        const double etb = -nb * inv1;
+        rtb += (pq <= 6 ? 1.0 / 18.0 : 1.0 / 36.0) * etb;
+        deplus_du(p, pq, utx, uty, utz, etb, utb);
+        th[0] += -nb * (0.5 * (own[pq] + own[q]) - et[q]) * inv1 * inv1;
+        // delta -> heights (closed height columns, unclamped delta only)
+        const double db = fbq * (-own[pq] + F[pq] + lp * npl[q]);
+        if (G.ok && G.closed && db != 0.0) {
+          const int A = G.a, B = G.b, Cc = 3 - G.a - G.b;
+          const int ca = A == 0 ? cx(pq) : (A == 1 ? cy(pq) : cz(pq));
+          const int cb = B == 0 ? cx(pq) : (B == 1 ? cy(pq) : cz(pq));
+          const int cc = Cc == 0 ? cx(pq) : (Cc == 1 ? cy(pq) : cz(pq));
+          const double Hb = 0.5 * ((double)G.H[7] - (double)G.H[1]);
+          const double Hc = 0.5 * ((double)G.H[5] - (double)G.H[3]);
+          const double vc = G.s * ca - Hb * cb - Hc * cc;
+          if (vc > 0.0) {
+            const double raw = ((double)G.H[4] - 3.5) / vc;
+            if (raw > p.delta_min && raw < 1.0) {
+              const double hb_ = db * d_ * cb / vc, hc_ = db * d_ * cc / vc;
+              Hbar[4] += db / vc;
+              Hbar[7] += 0.5 * hb_;
+              Hbar[1] -= 0.5 * hb_;
+              Hbar[5] += 0.5 * hc_;
+              Hbar[3] -= 0.5 * hc_;
+              geo_used = true;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 1; q < 19; ++q)
+      if (!((wallm | gasm) & (1u << q))) Fb[q] += fb[q];
+    ob[0] += fb[0];
+    if (geo_used) {
+      const int A = G.a, B = G.b;
+      for (int ib = -1; ib <= 1; ++ib)
+        for (int ic = -1; ic <= 1; ++ic) {
+          const double hb = Hbar[(ib + 1) * 3 + (ic + 1)];
+          if (hb == 0.0) continue;
+          for (int k = -3; k <= 3; ++k) {
+            int o0 = (A == 0) ? k : ((B == 0) ? ib : ic);
+            int o1 = (A == 1) ? k : ((B == 1) ? ib : ic);
+            int o2 = (A == 2) ? k : ((B == 2) ? ib : ic);
+            long long j = nbr(p, x, y, z, o0, o1, o2);
+            uint8_t kj = kind_at(a.flags, j);
+            if (kj == IFC || (kj == GAS && p.freeze)) {
+              if (j == i) phib_self += hb;
+              else atomicAdd(a.phibar_out + j, hb);
+            }
+          }
+        }
+    }
+    // own moments: rho_t = sum f~, u_t = sum c f~ - g/2
+#pragma unroll
+    for (int q = 0; q < 19; ++q) ob[q] += rtb + cx(q) * utb[0] + cy(q) * utb[1] + cz(q) * utb[2];
+    th[2] -= 0.5 * utb[0];
+    th[3] -= 0.5 * utb[1];
+    th[4] -= 0.5 * utb[2];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      a.abar_out[q * N + i] = ob[q];
+      a.Pb[q * N + i] = Fb[q];
+    }
+    if (phib_self != 0.0) atomicAdd(a.phibar_out + i, phib_self);
+  }
+  block_add(th, a.theta);
+}
+
+// reverse of the pull: abar_q(y) += P_q(y + c_q) when y + c_q pulled from y
+template <int P>
+__global__ void k_adj_gather(Par p, const uint8_t* __restrict__ flags, const double* __restrict__ Pb,
+                             double* __restrict__ abar) {
+  const size_t N = (size_t)p.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (!is_fluid(flags[i] & KIND)) continue;
+    int x, y, z;
+    coords(p, i, x, y, z);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      long long zc = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      if (zc < 0 || !is_fluid(flags[zc] & KIND)) continue;
+      abar[q * N + i] += Pb[q * N + zc];
+    }
+  }
+}
+
+// Objective on the stored state: red[0] = sum of the objective's terms,
+// red[1] = count (interface cells) or sum of phi (flux).
+template <int P>
+__global__ void k_objective(Par p, const uint8_t* flags, const typename Form<P>::S* f,
+                            const typename Form<P>::R* phi, int objective, double* red) {
+  const size_t N = (size_t)p.N;
+  double s = 0.0, c = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint8_t k = flags[i] & KIND;
+    if (!is_fluid(k)) continue;
+    if (objective == 0 && k != IFC) continue;
+    double jx = 0.0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+      if (cx(q)) jx += cx(q) * (double)ldq<P>(f, q * N + i, q);
+    double ux = jx - 0.5 * p.g[0];
+    double w = objective == 0 ? 1.0 : (k == IFC ? (double)phi[i] : 1.0);
+    s += w * ux;
+    c += w;
+  }
+  atomicAdd(red, s);
+  atomicAdd(red + 1, c);
+}
+
+template <int P>
+__global__ void k_obj_seed(Par p, const uint8_t* flags, const typename Form<P>::S* f,
+                           const typename Form<P>::R* phi, int objective, double scale, double* abar,
+                           double* phibar, double* mbar) {
+  const size_t N = (size_t)p.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint8_t k = flags[i] & KIND;
+    double w = 0.0, pb = 0.0;
+    if (is_fluid(k)) {
+      if (objective == 0) {
+        w = (k == IFC) ? scale : 0.0;
+      } else {
+        w = (k == IFC ? (double)phi[i] : 1.0) * scale;
+        if (k == IFC) {
+          double jx = 0.0;
+#pragma unroll
+          for (int q = 0; q < 19; ++q)
+            if (cx(q)) jx += cx(q) * (double)ldq<P>(f, q * N + i, q);
+          pb = (jx - 0.5 * p.g[0]) * scale;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 19; ++q) abar[q * N + i] = w * cx(q);
+    phibar[i] = pb;
+    mbar[i] = 0.0;
+  }
+}
+
+// Reverse of the initial collision f~(0) = C(f(0)) for the parameter
+// adjoints (f(0) recovered by inverting the collision), and dJ/dphi0 =
+// mbar(0) rho(0) + phibar(0) on interface cells.
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_init(Par p, const uint8_t* flags, const typename Form<P>::S* f,
+                                                  const double* abar, const double* mbar, const double* phibar,
+                                                  double* theta, double* dphi0) {
+  const size_t N = (size_t)p.N;
+  double th[5] = {0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint8_t k = flags[i] & KIND;
+    dphi0[i] = 0.0;
+    if (!is_fluid(k)) continue;
+    double ft[19], f0[19], ab[19], fb[19];
+    double r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      ft[q] = (double)ldq<P>(f, q * N + i, q);
+      ab[q] = abar[q * N + i];
+      fb[q] = 0.0;
+      r += ft[q];
+      jx += cx(q) * ft[q];
+      jy += cy(q) * ft[q];
+      jz += cz(q) * ft[q];
+    }
+    // U = sum c f~ - g, u = U + g/2, v = U - g/lambda_-
+    const double Ux = jx - p.g[0], Uy = jy - p.g[1], Uz = jz - p.g[2];
+    const double ux = Ux + 0.5 * p.g[0], uy = Uy + 0.5 * p.g[1], uz = Uz + 0.5 * p.g[2];
+    const double vx = Ux - p.g[0] / p.lam_m, vy = Uy - p.g[1] / p.lam_m, vz = Uz - p.g[2] / p.lam_m;
+    f0[0] = eplus_d(p, 0, r, ux, uy, uz) + (ft[0] - eplus_d(p, 0, r, ux, uy, uz)) / (1.0 + p.lam_p);
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {
+      const int qb = q + 1;
+      double w = q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0;
+      double ep = eplus_d(p, q, r, ux, uy, uz);
+      double em = 3.0 * w * (cx(q) * vx + cy(q) * vy + cz(q) * vz);
+      double fp = ep + (0.5 * (ft[q] + ft[qb]) - ep) / (1.0 + p.lam_p);
+      double fm = em + (0.5 * (ft[q] - ft[qb]) - em) / (1.0 + p.lam_m);
+      f0[q] = fp + fm;
+      f0[qb] = fp - fm;
+    }
+    collide_rev(p, f0, ab, fb, th);
+    if (k == IFC) dphi0[i] = (p.freeze ? 0.0 : mbar[i] * r) + phibar[i];
+  }
+  block_add(th, theta);
+}
+
+template <int P>
+static void launch_local(const Par& p, const AdjView<P>& a, cudaStream_t st) {
+  int blocks = (int)((p.N + 127) / 128);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_adj_local<P><<<blocks, 128, 0, st>>>(p, a);
+  k_adj_gather<P><<<blocks, 128, 0, st>>>(p, a.flags, a.Pb, a.abar_out);
+}
+
+}  // namespace fsl
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static int adj_fail(fslbm* h, int code, const char* what) {
+  snprintf(h->msg, sizeof h->msg, "%s", what);
+  return code;
+}
+
+void fslbm_free_adjoint(fslbm* h) {
+  if (!h || !h->adj) return;
+  AdjointState* A = h->adj;
+  void* ptrs[] = {A->ck_f, A->ck_m, A->ck_phi, A->seg_f, A->seg_m, A->seg_phi, A->abar[0], A->abar[1], A->P,
+                  A->mbar[0], A->mbar[1], A->phibar[0], A->phibar[1], A->theta, A->red, A->dphi0};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete A;
+  h->adj = nullptr;
+}
+
+static bool amalloc(AdjointState* A, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    *p = nullptr;
+    return false;
+  }
+  A->bytes += bytes;
+  return true;
+}
+
+static void* cur_f(fslbm* h) { return h->cur ? h->fB : h->fA; }
+static void* cur_phi(fslbm* h) { return (h->par.freeze || !h->cur) ? h->phiA : h->phiB; }
+
+static int save_state(fslbm* h, void* f, double* m, void* phi) {
+  AdjointState* A = h->adj;
+  if (cudaMemcpyAsync(f, cur_f(h), A->fbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
+  if (cudaMemcpyAsync(m, h->m, (size_t)h->par.N * 8, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
+  if (cudaMemcpyAsync(phi, cur_phi(h), A->rbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
+  return 0;
+}
+
+static int restore_state(fslbm* h, const void* f, const double* m, const void* phi) {
+  AdjointState* A = h->adj;
+  h->cur = 0;
+  if (cudaMemcpyAsync(h->fA, f, A->fbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
+  if (cudaMemcpyAsync(h->m, m, (size_t)h->par.N * 8, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
+  if (cudaMemcpyAsync(h->phiA, phi, A->rbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
+  return 0;
+}
+
+template <int P>
+static int objective_t(fslbm* h, double* J, double* norm) {
+  AdjointState* A = h->adj;
+  if (cudaMemsetAsync(A->red, 0, 4 * 8, h->st) != cudaSuccess) return 1;
+  int blocks = (int)((h->par.N + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_objective<P><<<blocks, 256, 0, h->st>>>(h->par, h->flags, (const typename Form<P>::S*)cur_f(h),
+                                            (const typename Form<P>::R*)cur_phi(h), A->objective, A->red);
+  double r[2];
+  if (cudaMemcpyAsync(r, A->red, 16, cudaMemcpyDeviceToHost, h->st) != cudaSuccess) return 1;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return 1;
+  if (A->objective == 0) {
+    *norm = r[1] > 0 ? 1.0 / r[1] : 0.0;
+    *J = r[0] * *norm;
+  } else {
+    *norm = 1.0 / h->par.nx;
+    *J = r[0] * *norm;
+  }
+  A->gseed = A->objective == 0 ? -0.5 : -0.5 * r[1] * *norm;
+  return 0;
+}
+
+extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objective, double* J) {
+  if (!h || nsteps < 1 || K < 1 || (objective != 0 && objective != 1)) return FSLBM_ERR_ARG;
+  if (h->par.compressible) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs rho_0 = 1");
+  if (h->par.sigma != 0.0) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs sigma = 0");
+  fslbm_free_adjoint(h);
+  AdjointState* A = new AdjointState();
+  h->adj = A;
+  const size_t N = (size_t)h->par.N;
+  A->nsteps = nsteps;
+  A->K = K;
+  A->objective = objective;
+  A->nck = (nsteps + K - 1) / K;
+  const size_t sb = h->prec == FSLBM_F64 ? 8 : (h->prec == FSLBM_F32 ? 4 : 2);
+  A->fbytes = 19 * N * sb;
+  A->rbytes = N * (h->prec == FSLBM_F64 ? 8 : 4);
+  bool ok = amalloc(A, &A->ck_f, A->fbytes * A->nck) && amalloc(A, (void**)&A->ck_m, N * 8 * A->nck) &&
+            amalloc(A, &A->ck_phi, A->rbytes * A->nck) && amalloc(A, (void**)&A->red, 64);
+  if (!ok) {
+    fslbm_free_adjoint(h);
+    return adj_fail(h, FSLBM_ERR_OOM, "adjoint checkpoint allocation");
+  }
+  int c[16];
+  cudaMemcpy(c, h->cnt, sizeof c, cudaMemcpyDeviceToHost);
+  A->conv0 = c[8];
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, h->st);
+  for (int s = 0; s < A->nck; ++s) {
+    if (save_state(h, (char*)A->ck_f + s * A->fbytes, A->ck_m + s * N, (char*)A->ck_phi + s * A->rbytes))
+      return adj_fail(h, FSLBM_ERR_CUDA, "checkpoint copy");
+    int n = nsteps - s * K < K ? nsteps - s * K : K;
+    int rc = fslbm_step(h, n);
+    if (rc) return rc;
+  }
+  cudaEventRecord(e1, h->st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  A->fwd_ms = ms / nsteps;
+  int rc = fslbm_sync(h);
+  if (rc) return rc;
+  cudaMemcpy(c, h->cnt, sizeof c, cudaMemcpyDeviceToHost);
+  if (c[8] != A->conv0)
+    return adj_fail(h, FSLBM_ERR_STATE, "cell conversions inside the differentiated window are not supported");
+  double norm = 0.0;
+  int orc;
+  switch (h->prec) {
+    case FSLBM_F64: orc = objective_t<P64>(h, &A->J, &norm); break;
+    case FSLBM_F32: orc = objective_t<P32>(h, &A->J, &norm); break;
+    default: orc = objective_t<P16>(h, &A->J, &norm); break;
+  }
+  if (orc) return adj_fail(h, FSLBM_ERR_CUDA, "objective");
+  A->ready = true;
+  if (J) *J = A->J;
+  return FSLBM_OK;
+}
+
+template <int P>
+static int backward_t(fslbm* h) {
+  using S = typename Form<P>::S;
+  using R = typename Form<P>::R;
+  AdjointState* A = h->adj;
+  const size_t N = (size_t)h->par.N;
+  cudaStream_t st = h->st;
+  // seed from the objective at the final state
+  double J = 0.0, norm = 0.0;
+  if (objective_t<P>(h, &J, &norm)) return 1;
+  int blocks = (int)((N + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  cudaMemsetAsync(A->theta, 0, 8 * 8, st);
+  k_obj_seed<P><<<blocks, 256, 0, st>>>(h->par, h->flags, (const S*)cur_f(h), (const R*)cur_phi(h), A->objective,
+                                        norm, A->abar[0], A->phibar[0], A->mbar[0]);
+  int cur = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float adj_total = 0.f;
+  long long adj_steps = 0;
+  for (int s = A->nck - 1; s >= 0; --s) {
+    if (restore_state(h, (char*)A->ck_f + s * A->fbytes, A->ck_m + s * N, (char*)A->ck_phi + s * A->rbytes))
+      return 1;
+    int n = A->nsteps - s * A->K < A->K ? A->nsteps - s * A->K : A->K;
+    for (int k = 0; k < n; ++k) {
+      if (save_state(h, (char*)A->seg_f + k * A->fbytes, A->seg_m + k * N, (char*)A->seg_phi + k * A->rbytes))
+        return 1;
+      if (fslbm_step(h, 1)) return 1;
+    }
+    cudaEventRecord(e0, st);
+    for (int k = n - 1; k >= 0; --k) {
+      AdjView<P> a;
+      a.flags = h->flags;
+      a.f = (const S*)((char*)A->seg_f + k * A->fbytes);
+      a.m = A->seg_m + k * N;
+      a.phi = (const R*)((char*)A->seg_phi + k * A->rbytes);
+      a.wd = h->wd;
+      a.abar_in = A->abar[cur];
+      a.mbar_in = A->mbar[cur];
+      a.phibar_in = A->phibar[cur];
+      a.abar_out = A->abar[cur ^ 1];
+      a.Pb = A->P;
+      a.mbar_out = A->mbar[cur ^ 1];
+      a.phibar_out = A->phibar[cur ^ 1];
+      a.theta = A->theta;
+      cudaMemsetAsync(a.phibar_out, 0, N * 8, st);
+      launch_local<P>(h->par, a, st);
+      cur ^= 1;
+    }
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    adj_total += ms;
+    adj_steps += n;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  A->adj_ms = adj_total / (adj_steps ? adj_steps : 1);
+  // initial collision and phi0
+  k_adj_init<P><<<(int)((N + 127) / 128 < 152 * 16 ? (N + 127) / 128 : 152 * 16), 128, 0, st>>>(
+      h->par, h->flags, (const S*)A->ck_f, A->abar[cur], A->mbar[cur], A->phibar[cur], A->theta, A->dphi0);
+  return cudaGetLastError() != cudaSuccess;
+}
+
+extern "C" int fslbm_adjoint_backward(fslbm_t* h, double* dJ_dnu, double dJ_dg[3], double* dJ_dphi0, int where) {
+  if (!h) return FSLBM_ERR_ARG;
+  AdjointState* A = h->adj;
+  if (!A || !A->ready) return adj_fail(h, FSLBM_ERR_ARG, "fslbm_adjoint_forward has not run");
+  const size_t N = (size_t)h->par.N;
+  if (!A->abar[0]) {
+    bool ok = amalloc(A, (void**)&A->abar[0], 19 * N * 8) && amalloc(A, (void**)&A->abar[1], 19 * N * 8) &&
+              amalloc(A, (void**)&A->P, 19 * N * 8) && amalloc(A, (void**)&A->mbar[0], N * 8) &&
+              amalloc(A, (void**)&A->mbar[1], N * 8) && amalloc(A, (void**)&A->phibar[0], N * 8) &&
+              amalloc(A, (void**)&A->phibar[1], N * 8) && amalloc(A, (void**)&A->theta, 64) &&
+              amalloc(A, (void**)&A->dphi0, N * 8) && amalloc(A, &A->seg_f, A->fbytes * A->K) &&
+              amalloc(A, (void**)&A->seg_m, N * 8 * A->K) && amalloc(A, &A->seg_phi, A->rbytes * A->K);
+    if (!ok) return adj_fail(h, FSLBM_ERR_OOM, "adjoint buffer allocation");
+  }
+  int r;
+  switch (h->prec) {
+    case FSLBM_F64: r = backward_t<P64>(h); break;
+    case FSLBM_F32: r = backward_t<P32>(h); break;
+    default: r = backward_t<P16>(h); break;
+  }
+  if (r) return adj_fail(h, FSLBM_ERR_CUDA, "adjoint sweep");
+  double th[8];
+  if (cudaMemcpyAsync(th, A->theta, sizeof th, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+    return adj_fail(h, FSLBM_ERR_CUDA, "D2H theta");
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return adj_fail(h, FSLBM_ERR_CUDA, "sync");
+  // nu = (tau - 1/2)/3; lambda_+ = -1/tau; lambda_- from Lambda fixed
+  const double tau = h->prm.tau;
+  const double dlp_dtau = 1.0 / (tau * tau);
+  double dlm_dtau;
+  if (h->prm.magic <= 0.0) {
+    dlm_dtau = dlp_dtau;
+  } else {
+    const double Lp = tau - 0.5, Lm = h->prm.magic / Lp;
+    dlm_dtau = (1.0 / ((Lm + 0.5) * (Lm + 0.5))) * (-h->prm.magic / (Lp * Lp));
+  }
+  if (dJ_dnu) *dJ_dnu = 3.0 * (th[0] * dlp_dtau + th[1] * dlm_dtau);
+  if (dJ_dg) {
+    dJ_dg[0] = th[2] + A->gseed;
+    dJ_dg[1] = th[3];
+    dJ_dg[2] = th[4];
+  }
+  if (dJ_dphi0) {
+    cudaMemcpyKind kind = where == FSLBM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (cudaMemcpyAsync(dJ_dphi0, A->dphi0, N * 8, kind, h->st) != cudaSuccess)
+      return adj_fail(h, FSLBM_ERR_CUDA, "copy dJ/dphi0");
+  }
+  return fslbm_sync(h);
+}
+
+extern "C" int fslbm_adjoint_stats(fslbm_t* h, double* fwd_ms_per_step, double* adj_ms_per_step,
+                                   size_t* peak_bytes) {
+  if (!h || !h->adj) return FSLBM_ERR_ARG;
+  if (fwd_ms_per_step) *fwd_ms_per_step = h->adj->fwd_ms;
+  if (adj_ms_per_step) *adj_ms_per_step = h->adj->adj_ms;
+  if (peak_bytes) *peak_bytes = h->adj->bytes + h->bytes;
+  return FSLBM_OK;
+}

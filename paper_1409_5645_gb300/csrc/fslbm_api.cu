@@ -13,43 +13,10 @@
 
 #include "fslbm.h"
 #include "fslbm_dev.cuh"
+#include "fslbm_handle.h"
 #include "fslbm_kernels.h"
 
 using namespace fsl;
-
-struct fslbm {
-  fslbm_params prm;
-  Par par;
-  int prec;
-  cudaStream_t st;
-  uint8_t* flags;
-  uint8_t* mark;
-  void* fA;
-  void* fB;
-  double* m;
-  void* phiA;
-  void* phiB;
-  double* wd;
-  int* lists[6];
-  int* cnt;
-  double* share;
-  double* partials;
-  long long nparts;
-  int bulk_blocks, iface_blocks, list_blocks, red_blocks;
-  double* red;
-  double* lost;
-  int* err;
-  double* step_mass;
-  double* total_out;
-  int cur;
-  long long t;
-  int cap;
-  size_t bytes;
-  char msg[256];
-  int timing;
-  std::vector<cudaEvent_t>* events;  // 5 per timed step
-  long long timed_steps;
-};
 
 static const char* k_ok = "no error";
 
@@ -69,39 +36,6 @@ static int fail(fslbm* h, int code, const char* what, cudaError_t e = cudaSucces
 
 static size_t store_bytes(int prec) { return prec == FSLBM_F64 ? 8 : (prec == FSLBM_F32 ? 4 : 2); }
 static size_t real_bytes(int prec) { return prec == FSLBM_F64 ? 8 : 4; }
-
-template <int P>
-static View<P> make_view(fslbm* h) {
-  View<P> v;
-  using S = typename Form<P>::S;
-  using R = typename Form<P>::R;
-  v.flags = h->flags;
-  v.mark = h->mark;
-  v.fin = (const S*)(h->cur ? h->fB : h->fA);
-  v.fout = (S*)(h->cur ? h->fA : h->fB);
-  v.m = h->m;
-  if (h->par.freeze) {
-    v.phin = (const R*)h->phiA;
-    v.phout = (R*)h->phiA;
-  } else {
-    v.phin = (const R*)(h->cur ? h->phiB : h->phiA);
-    v.phout = (R*)(h->cur ? h->phiA : h->phiB);
-  }
-  v.wd = (const double*)h->wd;
-  v.ilist = h->lists[0];
-  v.flist = h->lists[1];
-  v.elist = h->lists[2];
-  v.nglist = h->lists[3];
-  v.nllist = h->lists[4];
-  v.rlist = h->lists[5];
-  v.cnt = h->cnt;
-  v.cap = h->cap;
-  v.share = h->share;
-  v.partials = h->partials;
-  v.lost = h->lost;
-  v.err = h->err;
-  return v;
-}
 
 static void drop_events(fslbm* h) {
   if (!h->events) return;
@@ -139,6 +73,7 @@ extern "C" void fslbm_default_params(fslbm_params* p) {
   p->rule = FSLBM_FSL;
   p->eps = 1e-3;
   p->delta_min = 0.0;
+  p->cleanup = 3;
   p->precision = FSLBM_F64;
 }
 
@@ -185,6 +120,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   p.compressible = q.compressible != 0;
   p.linear_eq = q.linear_eq != 0;
   p.freeze = q.freeze != 0;
+  p.cleanup = q.cleanup;
   p.has_wd = 0;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
@@ -248,6 +184,7 @@ extern "C" int fslbm_create(const int dims[3], double tau, const double g[3], do
 extern "C" void fslbm_destroy(fslbm_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  fslbm_free_adjoint(h);
   free_all(h);
   free(h);
 }
@@ -287,6 +224,7 @@ static int begin_state(fslbm* h, const uint8_t* flags, const double* wall_delta,
                        Staged& sw) {
   const size_t N = (size_t)h->par.N;
   if (!flags) return fail(h, FSLBM_ERR_ARG, "flags is NULL");
+  fslbm_free_adjoint(h);
   if (where != FSLBM_HOST && where != FSLBM_DEVICE) return fail(h, FSLBM_ERR_ARG, "bad `where`");
   CK(cudaMemcpyAsync(h->flags, flags, N, where == FSLBM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      h->st),

@@ -217,6 +217,8 @@ __global__ void k_final(Par p, View<P> v) {
   int ng = min(load_count(&v.cnt[3]), v.cap), nl = min(load_count(&v.cnt[4]), v.cap);
   int nr = min(load_count(&v.cnt[5]), v.cap);
   int total = nf + ne + ng + nl + nr;
+  // running total of conversions since the state was set (never reset per step)
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nf + ng + nl) atomicAdd(&v.cnt[8], nf + ng + nl);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     int kk = k;
     if (kk < nf) {
@@ -233,6 +235,7 @@ __global__ void k_final(Par p, View<P> v) {
         v.phout[i] = R(0);
         v.mark[i] = 0;
         atomicAdd(&v.cnt[7], 1);
+        atomicAdd(&v.cnt[8], 1);
       }
       continue;
     }

@@ -1,0 +1,84 @@
+// fslbm_handle.h -- the handle behind the opaque fslbm_t of the C interface
+// (shared by the host translation units of the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "fslbm.h"
+#include "fslbm_dev.cuh"
+
+struct AdjointState;
+struct fslbm;
+void fslbm_free_adjoint(fslbm* h);
+
+struct fslbm {
+  fslbm_params prm;
+  fsl::Par par;
+  int prec;
+  cudaStream_t st;
+  uint8_t* flags;
+  uint8_t* mark;
+  void* fA;
+  void* fB;
+  double* m;
+  void* phiA;
+  void* phiB;
+  double* wd;
+  int* lists[6];
+  int* cnt;
+  double* share;
+  double* partials;
+  long long nparts;
+  int bulk_blocks, iface_blocks, list_blocks, red_blocks;
+  double* red;
+  double* lost;
+  int* err;
+  double* step_mass;
+  double* total_out;
+  int cur;
+  long long t;
+  int cap;
+  size_t bytes;
+  char msg[256];
+  int timing;
+  std::vector<cudaEvent_t>* events;  // 5 per timed step
+  long long timed_steps;
+  AdjointState* adj;  // checkpoints and buffers of a differentiation, or NULL
+};
+
+
+template <int P>
+inline fsl::View<P> make_view(fslbm* h) {
+  using namespace fsl;
+
+  View<P> v;
+  using S = typename Form<P>::S;
+  using R = typename Form<P>::R;
+  v.flags = h->flags;
+  v.mark = h->mark;
+  v.fin = (const S*)(h->cur ? h->fB : h->fA);
+  v.fout = (S*)(h->cur ? h->fA : h->fB);
+  v.m = h->m;
+  if (h->par.freeze) {
+    v.phin = (const R*)h->phiA;
+    v.phout = (R*)h->phiA;
+  } else {
+    v.phin = (const R*)(h->cur ? h->phiB : h->phiA);
+    v.phout = (R*)(h->cur ? h->phiA : h->phiB);
+  }
+  v.wd = (const double*)h->wd;
+  v.ilist = h->lists[0];
+  v.flist = h->lists[1];
+  v.elist = h->lists[2];
+  v.nglist = h->lists[3];
+  v.nllist = h->lists[4];
+  v.rlist = h->lists[5];
+  v.cnt = h->cnt;
+  v.cap = h->cap;
+  v.share = h->share;
+  v.partials = h->partials;
+  v.lost = h->lost;
+  v.err = h->err;
+  return v;
+}
+

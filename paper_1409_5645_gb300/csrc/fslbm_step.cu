@@ -50,14 +50,6 @@ __device__ __forceinline__ double block_sum128(double v) {
   return s;
 }
 
-template <class R>
-__device__ __forceinline__ R phi_at(const Par& p, const R* __restrict__ phin, long long j, uint8_t kj) {
-  if (kj == LIQ) return R(1);
-  if (kj == IFC) return phin[j];
-  if (kj == GAS && p.freeze) return phin[j];
-  return R(0);
-}
-
 // ---------------------------------------------------------------------------
 // General pull for a cell next to a wall, a face or gas.  Fills f[q] from
 // fluid sources and returns masks of wall and gas sources.
@@ -164,95 +156,6 @@ __global__ void __launch_bounds__(128) k_bulk(Par p, View<P> v) {
 }
 
 // ---------------------------------------------------------------------------
-// Geometry of an interface cell from phi(t) (Sec. 2.2, Sec. 5): Parker-Youngs
-// gradient, then height functions over 3x3 columns of 7 cells along the
-// dominant axis; if every column is closed (liquid at its liquid end, gas at
-// its gas end, no wall) the normal, the plane offset
-// d = |n_a| (H(0,0) - 3.5) and the curvature come from the heights, else the
-// normalised Parker-Youngs normal and the plane cutting the cell's own fill.
-// ---------------------------------------------------------------------------
-template <class R>
-__device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const R* __restrict__ phin,
-                         int x, int y, int z, R phic, R (&n)[3], R& d, R& kap, bool& ok) {
-  R g0 = R(0), g1 = R(0), g2 = R(0);
-#pragma unroll 1
-  for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll 1
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (!dx && !dy && !dz) continue;
-        long long j = nbr(p, x, y, z, dx, dy, dz);
-        uint8_t kj = kind_at(flags, j);
-        R pj = (kj == WALL) ? phic : phi_at<R>(p, phin, j, kj);
-        int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
-        if (dx) g0 += R(dx * (2 - ay) * (2 - az)) * pj;
-        if (dy) g1 += R(dy * (2 - az) * (2 - ax)) * pj;
-        if (dz) g2 += R(dz * (2 - ax) * (2 - ay)) * pj;
-      }
-  n[0] = -g0; n[1] = -g1; n[2] = -g2;
-  kap = R(0);
-  R nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-  if (!(nn > R(1e-24))) {
-    ok = false;
-    d = R(0);
-    n[0] = R(0); n[1] = R(0); n[2] = R(1);
-    return;
-  }
-  ok = true;
-  int a = 0;
-  R na = fabs(n[0]);
-  if (fabs(n[1]) > na) { a = 1; na = fabs(n[1]); }
-  if (fabs(n[2]) > na) { a = 2; }
-  const int s = (a == 0 ? n[0] : (a == 1 ? n[1] : n[2])) > R(0) ? 1 : -1;
-  const int b = (a == 0) ? 1 : 0;  // the third axis is the remaining one
-  R H[9];
-  bool closed = true;
-#pragma unroll 1
-  for (int ib = -1; ib <= 1 && closed; ++ib)
-#pragma unroll 1
-    for (int ic = -1; ic <= 1 && closed; ++ic) {
-      R sum = R(0);
-#pragma unroll 1
-      for (int k = -3; k <= 3; ++k) {
-        int o0 = (a == 0) ? k : ((b == 0) ? ib : ic);
-        int o1 = (a == 1) ? k : ((b == 1) ? ib : ic);
-        int o2 = (a == 2) ? k : ((b == 2) ? ib : ic);
-        long long j = nbr(p, x, y, z, o0, o1, o2);
-        uint8_t kj = kind_at(flags, j);
-        if (kj == WALL) { closed = false; break; }
-        if (k == -3 * s && kj != LIQ) { closed = false; break; }
-        if (k == 3 * s && kj != GAS) { closed = false; break; }
-        sum += phi_at<R>(p, phin, j, kj);
-      }
-      H[(ib + 1) * 3 + (ic + 1)] = sum;
-    }
-  if (closed) {
-    R Hb = R(0.5) * (H[7] - H[1]);
-    R Hc = R(0.5) * (H[5] - H[3]);
-    R v0 = (a == 0) ? R(s) : ((b == 0) ? -Hb : -Hc);
-    R v1 = (a == 1) ? R(s) : ((b == 1) ? -Hb : -Hc);
-    R v2 = (a == 2) ? R(s) : ((b == 2) ? -Hb : -Hc);
-    R len = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-    n[0] = v0 / len; n[1] = v1 / len; n[2] = v2 / len;
-    R nabs = fabs(a == 0 ? n[0] : (a == 1 ? n[1] : n[2]));
-    d = nabs * (H[4] - R(3.5));
-    if (p.sigma != 0.0) {
-      R Hbb = H[7] - R(2) * H[4] + H[1];
-      R Hcc = H[5] - R(2) * H[4] + H[3];
-      R Hbc = R(0.25) * (H[8] - H[6] - H[2] + H[0]);
-      R q2 = R(1) + Hb * Hb + Hc * Hc;
-      R num = Hbb * (R(1) + Hc * Hc) + Hcc * (R(1) + Hb * Hb) - R(2) * Hb * Hc * Hbc;
-      kap = -num / (q2 * sqrt(q2));
-    }
-  } else {
-    R len = sqrt(nn);
-    n[0] /= len; n[1] /= len; n[2] /= len;
-    d = plic_offset<R>(n[0], n[1], n[2], phic);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // k_iface
 // ---------------------------------------------------------------------------
 template <int P>
@@ -296,9 +199,11 @@ __global__ void __launch_bounds__(128) k_iface(Par p, View<P> v, int bulk_blocks
       }
       if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
       if (gasm) {
-        R n[3], d, kap;
-        bool ok;
-        geometry<R>(p, v.flags, v.phin, x, y, z, phic, n, d, kap, ok);
+        Geo<R> G;
+        geometry<R>(p, v.flags, v.phin, x, y, z, phic, G);
+        const R* n = G.n;
+        const R d = G.d, kap = G.kap;
+        const bool ok = G.ok;
         R rb = R(p.rho_G);
         if (p.sigma != 0.0) rb = rb + R(3.0 * p.sigma) * kap;
         const R r0b = p.compressible ? rb : R(1);
@@ -339,8 +244,10 @@ __global__ void __launch_bounds__(128) k_iface(Par p, View<P> v, int bulk_blocks
         mm = mm + dm;
         v.m[i] = mm;
         v.phout[i] = (R)(mm / (double)rho);
-        fill = mm > (1.0 + p.eps) * (double)rho;
-        empty = !fill && (mm < -p.eps * (double)rho);
+        // thresholds, plus the isolated-cell rules: no gas neighbour -> fill,
+        // no liquid/interface neighbour -> empty
+        fill = mm > (1.0 + p.eps) * (double)rho || ((p.cleanup & 1) && gasm == 0u);
+        empty = !fill && (mm < -p.eps * (double)rho || ((p.cleanup & 2) && (wallm | gasm) == 0x7fffeu));
       }
       msum += mm;
     }

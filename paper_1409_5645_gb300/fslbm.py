@@ -36,7 +36,7 @@ class Params(C.Structure):
     _fields_ = [("dims", C.c_int * 3), ("tau", C.c_double), ("magic", C.c_double), ("g", C.c_double * 3),
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int), ("compressible", C.c_int),
                 ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
-                ("freeze", C.c_int), ("delta_min", C.c_double), ("precision", C.c_int),
+                ("freeze", C.c_int), ("cleanup", C.c_int), ("delta_min", C.c_double), ("precision", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -69,6 +69,9 @@ def lib():
             L.fslbm_counters.argtypes = [vp, C.POINTER(C.c_longlong)]
             L.fslbm_timing.argtypes = [vp, ip]
             L.fslbm_timing_read.argtypes = [vp, dp, C.POINTER(C.c_longlong)]
+            L.fslbm_adjoint_forward.argtypes = [vp, ip, ip, ip, dp]
+            L.fslbm_adjoint_backward.argtypes = [vp, dp, dp, C.c_void_p, ip]
+            L.fslbm_adjoint_stats.argtypes = [vp, dp, dp, C.POINTER(C.c_size_t)]
             L.fslbm_time.argtypes = [vp]
             L.fslbm_time.restype = C.c_longlong
             L.fslbm_device_bytes.argtypes = [vp]
@@ -136,6 +139,7 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.eps = params.get("eps", P.eps)
     P.zshift = int(params.get("zshift", 0))
     P.freeze = int(params.get("freeze", 0))
+    P.cleanup = int(params.get("cleanup", P.cleanup))
     P.delta_min = params.get("delta_min", P.delta_min)
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream
@@ -248,6 +252,32 @@ class Lattice:
         n = C.c_longlong()
         self._check(self.L.fslbm_timing_read(self.h, ms, C.byref(n)), "timing_read")
         return list(ms), n.value
+
+    # -- differentiation ------------------------------------------------------
+    def adjoint_forward(self, nsteps: int, K: int = 200, objective: int = 0) -> float:
+        J = C.c_double()
+        self._check(self.L.fslbm_adjoint_forward(self.h, int(nsteps), int(K), int(objective), C.byref(J)),
+                    "adjoint_forward")
+        return J.value
+
+    def adjoint_backward(self, device=None):
+        """(dJ/dnu, dJ/dg[3], dJ/dphi0[N]) as NumPy (or a CUDA tensor for phi0)."""
+        dnu = C.c_double()
+        dg = (C.c_double * 3)()
+        if device is not None:
+            import torch
+            dphi = torch.empty(self.N, dtype=torch.float64, device=device)
+            ptr, where = C.c_void_p(dphi.data_ptr()), DEVICE
+        else:
+            dphi = np.empty(self.N, dtype=np.float64)
+            ptr, where = C.c_void_p(dphi.ctypes.data), HOST
+        self._check(self.L.fslbm_adjoint_backward(self.h, C.byref(dnu), dg, ptr, where), "adjoint_backward")
+        return dnu.value, np.array(list(dg)), dphi
+
+    def adjoint_stats(self):
+        f, a, b = C.c_double(), C.c_double(), C.c_size_t()
+        self._check(self.L.fslbm_adjoint_stats(self.h, C.byref(f), C.byref(a), C.byref(b)), "adjoint_stats")
+        return f.value, a.value, b.value
 
     @property
     def time(self) -> int:

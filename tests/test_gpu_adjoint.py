@@ -1,0 +1,146 @@
+"""The hand-written adjoint against the oracle's tangent-linear model,
+central finite differences of the CUDA forward path, the film series, and
+through torch.autograd."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import VEL, Oracle
+from paper_1409_5645_gb300 import cases, fslbm
+
+pytestmark = pytest.mark.gpu
+
+
+def _J_gpu(case, steps, precision="f64", **override):
+    c = cases.Case(case)
+    p = dict(case["params"])
+    p.update(override)
+    c["params"] = p
+    g = fslbm.Lattice.from_case(c, precision=precision)
+    return g.adjoint_forward(steps, K=max(1, steps // 4))
+
+
+def _grad_gpu(case, steps, K, precision="f64"):
+    g = fslbm.Lattice.from_case(case, precision=precision)
+    J = g.adjoint_forward(steps, K)
+    dnu, dg, dphi = g.adjoint_backward()
+    stats = g.adjoint_stats()
+    return J, dnu, dg, dphi, stats
+
+
+def _tlm(case, steps, dtau=0.0, dg=None, dphi=None):
+    o = Oracle.from_case(case, dual=True)
+    o.seed(dtau=dtau, dg=dg, dphi=dphi)
+    o.step(steps)
+    fl = o.flags()
+    return o.get(VEL, tangent=True)[fl == 2, 0].mean()
+
+
+def test_adjoint_matches_oracle_tangent_linear():
+    """FP64 adjoint (several checkpoint segments) = FP64 tangent-linear model
+    of the oracle, in nu, g_x and the interface fill levels."""
+    c = cases.adjoint_film(nz=48, h=30.0)
+    steps = 300
+    J, dnu, dg, dphi, _ = _grad_gpu(c, steps, K=70)
+    o = Oracle.from_case(c)
+    o.step(steps)
+    fl = o.flags()
+    assert J == pytest.approx(o.get(VEL)[fl == 2, 0].mean(), rel=1e-11)
+    t_tau = _tlm(c, steps, dtau=1.0)
+    assert dnu == pytest.approx(3.0 * t_tau, rel=1e-7)  # tau = 3 nu + 1/2
+    t_g = _tlm(c, steps, dg=[1.0, 0.0, 0.0])
+    assert dg[0] == pytest.approx(t_g, rel=1e-7)
+    ifc = np.where(c["flags"] == cases.INTERFACE)[0]
+    scale = np.abs(dphi[ifc]).max()
+    for k in ifc[[0, 5, 13, 31]]:
+        e = np.zeros(c.N)
+        e[k] = 1.0
+        assert dphi[k] == pytest.approx(_tlm(c, steps, dphi=e), abs=1e-6 * scale)
+    assert np.all(dphi[c["flags"] != cases.INTERFACE] == 0.0)
+
+
+def test_adjoint_matches_central_differences_film_4000_steps():
+    """Film 8x4x64, depth 40, 4000 steps, checkpoints every 200: the adjoint
+    gradient against central differences of the CUDA forward path."""
+    c = cases.adjoint_film()
+    steps = 4000
+    J, dnu, dg, dphi, stats = _grad_gpu(c, steps, K=200)
+    nu = (c["params"]["tau"] - 0.5) / 3
+    h = 1e-6 * nu
+    fd = (_J_gpu(c, steps, tau=0.5 + 3 * (nu + h)) - _J_gpu(c, steps, tau=0.5 + 3 * (nu - h))) / (2 * h)
+    assert dnu == pytest.approx(fd, rel=1e-4)
+    gx = c["params"]["g"][0]
+    h = 1e-6 * gx
+    fd = (_J_gpu(c, steps, g=(gx + h, 0.0, 0.0)) - _J_gpu(c, steps, g=(gx - h, 0.0, 0.0))) / (2 * h)
+    assert dg[0] == pytest.approx(fd, rel=1e-4)
+    ifc = np.where(c["flags"] == cases.INTERFACE)[0]
+    k = ifc[9]
+    hp = 1e-4
+    cp, cm = cases.Case(c), cases.Case(c)
+    cp["phi"] = c["phi"].copy()
+    cm["phi"] = c["phi"].copy()
+    cp["phi"][k] += hp
+    cm["phi"][k] -= hp
+    fd = (_J_gpu(cp, steps) - _J_gpu(cm, steps)) / (2 * hp)
+    assert dphi[k] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(dphi[ifc]).max())
+    fwd_ms, adj_ms, peak = stats
+    assert fwd_ms > 0 and adj_ms > 0 and peak > 0
+
+
+def test_adjoint_nu_derivative_against_film_series():
+    """dJ/dnu against the nu-derivative of the transient film series at the
+    interface nodes (z = h - 1/2) after 4000 steps (the closed-form steady
+    limit is -u_s/nu)."""
+    c = cases.adjoint_film()
+    steps = 4000
+    J, dnu, _, _, _ = _grad_gpu(c, steps, K=200)
+    nu = (c["params"]["tau"] - 0.5) / 3
+    z = 40.0 - 0.5
+    series = lambda v: cases.film_transient(np.array([z]), steps, 40.0, 1e-6, v, terms=400)[0]
+    assert J == pytest.approx(series(nu), rel=2e-3)
+    h = 1e-6
+    dser = (series(nu + h) - series(nu - h)) / (2 * h)
+    assert dnu == pytest.approx(dser, rel=5e-3)
+    us = cases.film_profile(np.array([z]), 40.0, 1e-6, nu)[0]
+    # steady limit of the same derivative: d u_s / d nu = -u_s / nu
+    assert dser > -us / nu
+
+
+def test_adjoint_fp32_close_to_fp64():
+    c = cases.adjoint_film(nz=48, h=30.0)
+    _, d64, g64, p64, _ = _grad_gpu(c, 300, K=100, precision="f64")
+    _, d32, g32, p32, _ = _grad_gpu(c, 300, K=100, precision="f32")
+    assert d32 == pytest.approx(d64, rel=1e-3)
+    assert g32[0] == pytest.approx(g64[0], rel=1e-3)
+    ifc = c["flags"] == cases.INTERFACE
+    assert np.abs(p32[ifc] - p64[ifc]).max() <= 2e-2 * np.abs(p64[ifc]).max()
+
+
+def test_autograd_function_matches_c_interface():
+    import torch
+    from paper_1409_5645_gb300.autograd import run
+    c = cases.adjoint_film(nz=48, h=30.0)
+    dev = torch.device("cuda:0")
+    nu = torch.tensor((c["params"]["tau"] - 0.5) / 3, dtype=torch.float64, requires_grad=True)
+    g = torch.tensor(c["params"]["g"], dtype=torch.float64, requires_grad=True)
+    phi0 = torch.tensor(c["phi"], dtype=torch.float64, device=dev, requires_grad=True)
+    J = run(nu, g, phi0, c, 200, K=50)
+    J.backward()
+    _, dnu, dg, dphi, _ = _grad_gpu(c, 200, K=50)
+    assert float(nu.grad) == pytest.approx(dnu, rel=1e-12)
+    assert np.allclose(g.grad.cpu().numpy(), dg, rtol=1e-12)
+    assert np.allclose(phi0.grad.cpu().numpy(), dphi, rtol=1e-12, atol=0)
+
+
+def test_adjoint_refuses_conversions_and_unsupported_settings():
+    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4)
+    g = fslbm.Lattice.from_case(c)
+    with pytest.raises(fslbm.FslbmError) as e:
+        g.adjoint_forward(200, 50)
+    assert e.value.code == -4
+    c2 = cases.adjoint_film(nz=48, h=30.0, compressible=1)
+    g2 = fslbm.Lattice.from_case(c2)
+    with pytest.raises(fslbm.FslbmError) as e:
+        g2.adjoint_forward(10, 5)
+    assert e.value.code == -1
