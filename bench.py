@@ -32,7 +32,7 @@ METRIC = "FSLBM MLUPS at 1 GB300 (FP32/FP16-store vs FP64 plain), % HBM roofline
 WORKLOAD = "dam_break_512x256x256_fsl"
 DIMS = (512, 256, 256)
 COL = (128, 192)
-KERNELS_PER_STEP = 11  # k_bulk, k_iface, 2 x k_reduce, 7 conversion kernels
+KERNELS_PER_STEP = 12  # k_segments, k_bulk, k_iface, 2 x k_reduce, 7 conversion kernels
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 

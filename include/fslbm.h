@@ -105,6 +105,10 @@ typedef struct {
   int cleanup;        /* isolated-cell rules (Thuerey): bit 1 fills an interface cell with no gas
                          neighbour, bit 2 empties an interface cell with no liquid/interface
                          neighbour (its mass goes to the lost ledger if no receiver); default 3 */
+  int keep_f0;        /* 1: keep the pre-collision initial populations in FP64 (152 B per cell) so
+                         that fslbm_adjoint_backward reverses the initial collision from them; 0:
+                         it recovers them by inverting the collision from the stored populations
+                         (exact in FP64, limited by the storage precision in FP32/FP16) */
   double delta_min;   /* lower clamp of the free-surface link fraction, default 0 */
   int precision;      /* fslbm_precision */
   void *stream;       /* cudaStream_t for all work of the handle; NULL = legacy default */

@@ -25,6 +25,7 @@ class FslbmRun(torch.autograd.Function):
         params = dict(case["params"])
         params["tau"] = 3.0 * float(nu) + 0.5
         params["g"] = tuple(float(v) for v in g.detach().cpu())
+        params["keep_f0"] = 1
         dev = phi0.device if phi0.is_cuda else torch.device("cuda", torch.cuda.current_device())
         lat = fslbm.Lattice(case["dims"], params, precision=precision)
         t = {k: torch.as_tensor(case[k]).to(dev) for k in ("flags", "rho", "u")}
@@ -33,6 +34,7 @@ class FslbmRun(torch.autograd.Function):
         J = lat.adjoint_forward(nsteps, K, objective)
         ctx.lat = lat
         ctx.dev = dev
+        ctx.devices = (nu.device, g.device, phi0.device)
         return torch.tensor(J, dtype=torch.float64, device=dev)
 
     @staticmethod
@@ -40,8 +42,9 @@ class FslbmRun(torch.autograd.Function):
         dnu, dg, dphi = ctx.lat.adjoint_backward(device=ctx.dev)
         ctx.lat.close()
         gJ = gJ.to(torch.float64)
-        return (gJ * dnu, gJ * torch.as_tensor(dg, dtype=torch.float64, device=ctx.dev), gJ * dphi,
-                None, None, None, None, None)
+        d_nu, d_g, d_phi = ctx.devices
+        return ((gJ * dnu).to(d_nu), (gJ * torch.as_tensor(dg, dtype=torch.float64, device=ctx.dev)).to(d_g),
+                (gJ * dphi).to(d_phi), None, None, None, None, None)
 
 
 def run(nu, g, phi0, case, nsteps, K=200, objective=0, precision="f64"):

@@ -503,8 +503,8 @@ __global__ void k_obj_seed(Par p, const uint8_t* flags, const typename Form<P>::
 // mbar(0) rho(0) + phibar(0) on interface cells.
 template <int P>
 __global__ void __launch_bounds__(128) k_adj_init(Par p, const uint8_t* flags, const typename Form<P>::S* f,
-                                                  const double* abar, const double* mbar, const double* phibar,
-                                                  double* theta, double* dphi0) {
+                                                  const double* f0keep, const double* abar, const double* mbar,
+                                                  const double* phibar, double* theta, double* dphi0) {
   const size_t N = (size_t)p.N;
   double th[5] = {0, 0, 0, 0, 0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
@@ -539,6 +539,14 @@ __global__ void __launch_bounds__(128) k_adj_init(Par p, const uint8_t* flags, c
       double fm = em + (0.5 * (ft[q] - ft[qb]) - em) / (1.0 + p.lam_m);
       f0[q] = fp + fm;
       f0[qb] = fp - fm;
+    }
+    if (f0keep) {  // the initial populations as set, in FP64
+      r = 0.0;
+#pragma unroll
+      for (int q = 0; q < 19; ++q) {
+        f0[q] = f0keep[(size_t)q * N + i];
+        r += f0[q];
+      }
     }
     collide_rev(p, f0, ab, fb, th);
     if (k == IFC) dphi0[i] = (p.freeze ? 0.0 : mbar[i] * r) + phibar[i];
@@ -748,7 +756,8 @@ static int backward_t(fslbm* h) {
   A->adj_ms = adj_total / (adj_steps ? adj_steps : 1);
   // initial collision and phi0
   k_adj_init<P><<<(int)((N + 127) / 128 < 152 * 16 ? (N + 127) / 128 : 152 * 16), 128, 0, st>>>(
-      h->par, h->flags, (const S*)A->ck_f, A->abar[cur], A->mbar[cur], A->phibar[cur], A->theta, A->dphi0);
+      h->par, h->flags, (const S*)A->ck_f, h->f0_valid ? h->f0 : nullptr, A->abar[cur], A->mbar[cur],
+      A->phibar[cur], A->theta, A->dphi0);
   return cudaGetLastError() != cudaSuccess;
 }
 

@@ -47,7 +47,7 @@ static void drop_events(fslbm* h) {
 static void free_all(fslbm* h) {
   drop_events(h);
   void* ptrs[] = {h->flags, h->mark, h->fA, h->fB, h->m, h->phiA, h->phiB, h->wd, h->cnt, h->share,
-                  h->partials, h->red, h->lost, h->err, h->step_mass, h->total_out};
+                  h->partials, h->red, h->lost, h->err, h->step_mass, h->total_out, h->f0, h->seglist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int k = 0; k < 6; ++k)
@@ -74,6 +74,7 @@ extern "C" void fslbm_default_params(fslbm_params* p) {
   p->eps = 1e-3;
   p->delta_min = 0.0;
   p->cleanup = 3;
+  p->keep_f0 = 0;
   p->precision = FSLBM_F64;
 }
 
@@ -125,7 +126,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;
-  h->bulk_blocks = (int)(((p.nx + 127) / 128) * (long long)p.ny * p.nz);
+  const long long nseg = ((p.nx + 127) / 128) * (long long)p.ny * p.nz;
+  h->bulk_blocks = (int)(nseg < 152 * 12 ? nseg : 152 * 12);
   h->iface_blocks = 152 * 8;
   h->list_blocks = 152 * 2;
   h->red_blocks = 152;
@@ -140,6 +142,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
             dalloc(h, &h->red, (size_t)(h->red_blocks + 2) * 8) && dalloc(h, &h->lost, 8) &&
             dalloc(h, &h->err, 8) && dalloc(h, &h->step_mass, 8) && dalloc(h, &h->total_out, 8);
   for (int k = 0; k < 6 && ok; ++k) ok = dalloc(h, &h->lists[k], Nn * sizeof(int));
+  if (ok && q.keep_f0) ok = dalloc(h, &h->f0, 19 * Nn * 8);
+  if (ok) ok = dalloc(h, &h->seglist, (size_t)nseg * sizeof(int));
   if (!ok) {
     free_all(h);
     free(h);
@@ -256,11 +260,13 @@ template <int P>
 static int init_pre_t(fslbm* h, const double* f, const double* phi, const double* rho, const double* u,
                       const double* noise) {
   View<P> v = make_view<P>(h);
-  return launch_init_pre<P>(h->par, v, f, phi, rho, u, noise, h->st);
+  h->f0_valid = h->f0 != nullptr;
+  return launch_init_pre<P>(h->par, v, f, phi, rho, u, noise, h->f0, h->st);
 }
 template <int P>
 static int init_post_t(fslbm* h, const double* f, const double* m, const double* phi) {
   View<P> v = make_view<P>(h);
+  h->f0_valid = 0;
   return launch_init_post<P>(h->par, v, f, m, phi, h->st);
 }
 
@@ -341,8 +347,11 @@ template <int P>
 static int step_t(fslbm* h) {
   View<P> v = make_view<P>(h);
   if (cudaMemsetAsync(h->cnt, 0, 8 * sizeof(int), h->st) != cudaSuccess) return 1;
+  if (cudaMemsetAsync(h->cnt + 9, 0, sizeof(int), h->st) != cudaSuccess) return 1;
   if (mark_event(h, 0)) return 1;
-  if (launch_step_kernels<P>(h->par, v, h->st, h->iface_blocks, h->timing ? h : nullptr)) return 1;
+  if (launch_step_kernels<P>(h->par, v, h->st, h->bulk_blocks, h->iface_blocks, h->seglist, h->cnt + 9,
+                             h->timing ? h : nullptr))
+    return 1;
   if (mark_event(h, 2)) return 1;
   if (launch_reduce(h->partials, (long long)h->bulk_blocks + h->iface_blocks, h->red, h->red_blocks, h->lost,
                     h->step_mass, h->st))

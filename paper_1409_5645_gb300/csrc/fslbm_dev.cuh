@@ -107,7 +107,7 @@ struct View {
   int* nglist;  // new from gas
   int* nllist;  // new from liquid
   int* rlist;   // excess receivers
-  int* cnt;     // [0] ilist [1] flist [2] elist [3] ng [4] nl [5] rl [7] emptied; [8] all conversions since set
+  int* cnt;     // [0] ilist [1] flist [2] elist [3] ng [4] nl [5] rl [7] emptied; [8] all conversions since set; [9] fluid segments
   int cap;
   double* share;
   double* partials;  // block partial sums of the mass balance

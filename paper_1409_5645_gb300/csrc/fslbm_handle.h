@@ -25,6 +25,7 @@ struct fslbm {
   void* phiB;
   double* wd;
   int* lists[6];
+  int* seglist;  // 128-cell x segments holding fluid (rebuilt every step)
   int* cnt;
   double* share;
   double* partials;
@@ -44,6 +45,8 @@ struct fslbm {
   std::vector<cudaEvent_t>* events;  // 5 per timed step
   long long timed_steps;
   AdjointState* adj;  // checkpoints and buffers of a differentiation, or NULL
+  double* f0;         // FP64 pre-collision initial populations (keep_f0), or NULL
+  int f0_valid;       // f0 holds the populations of the current initial state
 };
 
 

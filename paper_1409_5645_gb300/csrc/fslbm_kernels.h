@@ -8,7 +8,8 @@
 namespace fsl {
 
 template <int P>
-int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int iface_blocks, void* timing_handle);
+int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
+                        int* seglist, int* segcount, void* timing_handle);
 
 // records the handle's between-kernel timing event (host side, fslbm_api.cu)
 int fslbm_mark_between(void* handle);
@@ -22,7 +23,7 @@ int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, co
 // state set-up and read-back (fslbm_state.cu)
 template <int P>
 int launch_init_pre(const Par& p, const View<P>& v, const double* f, const double* phi, const double* rho_in,
-                    const double* u_in, const double* noise, cudaStream_t st);
+                    const double* u_in, const double* noise, double* keep_f0, cudaStream_t st);
 template <int P>
 int launch_init_post(const Par& p, const View<P>& v, const double* f, const double* m, const double* phi,
                      cudaStream_t st);

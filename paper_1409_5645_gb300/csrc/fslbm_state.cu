@@ -9,7 +9,7 @@ namespace fsl {
 template <int P>
 __global__ void k_init_pre(Par p, View<P> v, const double* __restrict__ fin, const double* __restrict__ phi,
                            const double* __restrict__ rho_in, const double* __restrict__ u_in,
-                           const double* __restrict__ noise) {
+                           const double* __restrict__ noise, double* __restrict__ keep_f0) {
   using R = typename Form<P>::R;
   const size_t N = (size_t)p.N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
@@ -43,6 +43,10 @@ __global__ void k_init_pre(Par p, View<P> v, const double* __restrict__ fin, con
     double rs = 0.0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) rs += fd[q];
+    if (keep_f0) {
+#pragma unroll
+      for (int q = 0; q < 19; ++q) keep_f0[(size_t)q * N + i] = fd[q];
+    }
     if (k == IFC) {
       double mm = (phi ? phi[i] : 1.0) * rs;
       v.m[i] = mm;
@@ -173,8 +177,8 @@ static int grid_for(long long n, int block) {
 
 template <int P>
 int launch_init_pre(const Par& p, const View<P>& v, const double* f, const double* phi, const double* rho_in,
-                    const double* u_in, const double* noise, cudaStream_t st) {
-  k_init_pre<P><<<grid_for(p.N, 128), 128, 0, st>>>(p, v, f, phi, rho_in, u_in, noise);
+                    const double* u_in, const double* noise, double* keep_f0, cudaStream_t st) {
+  k_init_pre<P><<<grid_for(p.N, 128), 128, 0, st>>>(p, v, f, phi, rho_in, u_in, noise, keep_f0);
   return (int)cudaGetLastError();
 }
 template <int P>
@@ -209,7 +213,7 @@ int launch_total_mass(const Par& p, const View<P>& v, double* partials, long lon
 
 #define FSL_INST(P)                                                                                          \
   template int launch_init_pre<P>(const Par&, const View<P>&, const double*, const double*, const double*,  \
-                                  const double*, const double*, cudaStream_t);                              \
+                                  const double*, const double*, double*, cudaStream_t);                     \
   template int launch_init_post<P>(const Par&, const View<P>&, const double*, const double*, const double*, \
                                    cudaStream_t);                                                           \
   template int launch_fields<P>(const Par&, const View<P>&, unsigned, void* const*, cudaStream_t);          \

@@ -1,10 +1,12 @@
 // fslbm_step.cu -- the stream-collide kernels of one FSLBM time step.
 //
-// k_bulk   one thread per cell over the whole lattice.  Liquid cells pull their
-//          19 populations (Eq. lbe1), apply half-way bounce-back / CLI at walls,
-//          collide (Eq. lbe2) and store; interface cells are compacted into a
-//          list by warp ballot; gas cells read one flag byte and stop.  The
-//          liquid density is reduced per block for the mass balance.
+// k_segments  compact list of the 128-cell x segments holding fluid (so that
+//          gas-only stretches of the lattice cost one flag scan, not a block).
+// k_bulk   persistent blocks over that list, one thread per cell.  Liquid
+//          cells pull their 19 populations (Eq. lbe1), apply half-way
+//          bounce-back / CLI at walls, collide (Eq. lbe2) and store; interface
+//          cells are compacted into a list by warp ballot.  The liquid density
+//          is reduced per block for the mass balance.
 // k_iface  one thread per interface cell (grid-stride over the list): pulls,
 //          rebuilds the populations arriving from gas cells by the FSK rule
 //          (Eq. koerner) or the FSL rule (Eq. closure, Table 1, D = 0) with the
@@ -99,21 +101,65 @@ __device__ __forceinline__ void wall_links(const Par& p, const View<P>& v, long 
 }
 
 // ---------------------------------------------------------------------------
-// k_bulk
+// k_segments: compact list of the 128-cell x segments that hold a liquid or
+// interface cell (one thread per segment, one atomic per warp).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restrict__ flags, int* __restrict__ seglist,
+                                                  int* __restrict__ count) {
+  const int nsx = (p.nx + 127) >> 7;
+  const long long nseg = (long long)nsx * p.ny * p.nz;
+  const long long sgi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool act = false;
+  if (sgi < nseg) {
+    const long long row = sgi / nsx;
+    const int x0 = (int)(sgi - row * nsx) << 7;
+    const int len = min(128, p.nx - x0);
+    const uint8_t* base = flags + row * p.nx + x0;
+    unsigned acc = 0u;
+    if (len == 128 && ((p.nx & 15) == 0)) {
+      const uint4* v4 = reinterpret_cast<const uint4*>(base);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        uint4 w = __ldg(v4 + k);
+        acc |= w.x | w.y | w.z | w.w;
+      }
+      // any byte with a liquid or interface bit
+      act = (acc & 0x03030303u) != 0u;
+    } else {
+      for (int k = 0; k < len; ++k) acc |= base[k];
+      act = (acc & 0x03u) != 0u;
+    }
+  }
+  unsigned bal = __ballot_sync(0xffffffffu, act);
+  if (bal) {
+    int lane = threadIdx.x & 31, leader = __ffs(bal) - 1, b = 0;
+    if (lane == leader) b = atomicAdd(count, __popc(bal));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (act) seglist[b + __popc(bal & ((1u << lane) - 1u))] = (int)sgi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_bulk: persistent blocks over the segment list, one thread per cell
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(128) k_bulk(Par p, View<P> v) {
+__global__ void __launch_bounds__(128) k_bulk(Par p, View<P> v, const int* __restrict__ seglist,
+                                              const int* __restrict__ segcount) {
   using R = typename Form<P>::R;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const bool in = x < p.nx;
-  const long long i = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
-  const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
-  const uint8_t k = fl & KIND;
-  warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
-
+  const int nsx = (p.nx + 127) >> 7;
+  const int nseg = *((volatile const int*)segcount);
   double msum = 0.0;
-  if (k == LIQ) {
+  for (int si = blockIdx.x; si < nseg; si += gridDim.x) {
+    const int sg = seglist[si];
+    const int row = sg / nsx;
+    const int x = ((sg - row * nsx) << 7) + threadIdx.x;
+    const int y = row % p.ny, z = row / p.ny;
+    const bool in = x < p.nx;
+    const long long i = (long long)row * p.nx + x;
+    const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
+    const uint8_t k = fl & KIND;
+    warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
+    if (k != LIQ) continue;
     const size_t N = (size_t)p.N;
     R f[19];
     const bool fast = !(fl & NEARB) && x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 &&
@@ -146,13 +192,10 @@ __global__ void __launch_bounds__(128) k_bulk(Par p, View<P> v) {
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
     FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-    msum = (double)rho;
+    msum += (double)rho;
   }
   double s = block_sum128(msum);
-  if (threadIdx.x == 0) {
-    long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-    v.partials[b] = s;
-  }
+  if (threadIdx.x == 0) v.partials[blockIdx.x] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -283,11 +326,11 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ in, l
 // launchers
 // ---------------------------------------------------------------------------
 template <int P>
-int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int iface_blocks, void* timing_handle) {
-  dim3 blk(128, 1, 1);
-  dim3 grd((unsigned)((p.nx + 127) / 128), (unsigned)p.ny, (unsigned)p.nz);
-  int bulk_blocks = (int)(grd.x * grd.y * grd.z);
-  k_bulk<P><<<grd, blk, 0, st>>>(p, v);
+int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
+                        int* seglist, int* segcount, void* timing_handle) {
+  const long long nseg = (long long)((p.nx + 127) / 128) * p.ny * p.nz;
+  k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(p, v.flags, seglist, segcount);
+  k_bulk<P><<<bulk_blocks, 128, 0, st>>>(p, v, seglist, segcount);
   if (timing_handle && fslbm_mark_between(timing_handle)) return 1;
   k_iface<P><<<iface_blocks, 128, 0, st>>>(p, v, bulk_blocks);
   return (int)cudaGetLastError();
@@ -304,8 +347,8 @@ int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, co
   return (int)cudaGetLastError();
 }
 
-template int launch_step_kernels<P64>(const Par&, const View<P64>&, cudaStream_t, int, void*);
-template int launch_step_kernels<P32>(const Par&, const View<P32>&, cudaStream_t, int, void*);
-template int launch_step_kernels<P16>(const Par&, const View<P16>&, cudaStream_t, int, void*);
+template int launch_step_kernels<P64>(const Par&, const View<P64>&, cudaStream_t, int, int, int*, int*, void*);
+template int launch_step_kernels<P32>(const Par&, const View<P32>&, cudaStream_t, int, int, int*, int*, void*);
+template int launch_step_kernels<P16>(const Par&, const View<P16>&, cudaStream_t, int, int, int*, int*, void*);
 
 }  // namespace fsl

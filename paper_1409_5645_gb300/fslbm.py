@@ -36,7 +36,8 @@ class Params(C.Structure):
     _fields_ = [("dims", C.c_int * 3), ("tau", C.c_double), ("magic", C.c_double), ("g", C.c_double * 3),
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int), ("compressible", C.c_int),
                 ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
-                ("freeze", C.c_int), ("cleanup", C.c_int), ("delta_min", C.c_double), ("precision", C.c_int),
+                ("freeze", C.c_int), ("cleanup", C.c_int), ("keep_f0", C.c_int), ("delta_min", C.c_double),
+                ("precision", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -140,6 +141,7 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.zshift = int(params.get("zshift", 0))
     P.freeze = int(params.get("freeze", 0))
     P.cleanup = int(params.get("cleanup", P.cleanup))
+    P.keep_f0 = int(params.get("keep_f0", 0))
     P.delta_min = params.get("delta_min", P.delta_min)
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream
