@@ -2,9 +2,11 @@
 """Throughput benchmark of the free-surface LBM step on GB300.
 
 Workload: 3D dam break 512 x 256 x 256 (33.5 M cells), walls on all faces,
-liquid column x < 128, z < 192 at rest with hydrostatic density, tau = 0.51,
-Lambda = 3/16, g = 1e-5 along -z, FSL rule, seeded fill perturbation 1e-3 on
-the interface layer.  The headline form is FP32 populations with FP64
+liquid column x < 128, z < 192 at rest with hydrostatic density,
+g = 1e-5 along -z, FSL rule, seeded fill perturbation 1e-3 on the interface
+layer, tau = 0.52 with the magic parameter Lambda = 0.005 (lambda_- = -1):
+with FSL the tau = 0.51 run loses stability within 3500-8500 steps for every
+Lambda tried, tau = 0.52 runs the 10000 steps.  The headline form is FP32 populations with FP64
 interface mass and mass balance; FP64 and FP16-storage forms are measured in
 the same run.  A "step" is one full time step: stream-collide, free-surface
 reconstruction, mass exchange, mass balance and cell conversions.
@@ -32,6 +34,7 @@ METRIC = "FSLBM MLUPS at 1 GB300 (FP32/FP16-store vs FP64 plain), % HBM roofline
 WORKLOAD = "dam_break_512x256x256_fsl"
 DIMS = (512, 256, 256)
 COL = (128, 192)
+TAU, MAGIC = 0.52, 0.005
 KERNELS_PER_STEP = 12  # k_segments, k_bulk, k_iface, 2 x k_reduce, 7 conversion kernels
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
@@ -47,22 +50,30 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="development size (128 x 64 x 64)")
+    ap.add_argument("--dims", default=None, help="nx,ny,nz of a scaled dam break (profiling)")
+    ap.add_argument("--tau", type=float, default=TAU)
+    ap.add_argument("--magic", type=float, default=MAGIC)
+    ap.add_argument("--rule", type=int, default=1, help="1 = FSL, 0 = FSK")
     return ap.parse_args()
 
 
 def dims_for(args):
+    if args.dims:
+        return tuple(int(v) for v in args.dims.split(","))
     return (128, 64, 64) if args.small else DIMS
 
 
 def col_for(args):
-    return (32, 48) if args.small else COL
+    nx, ny, nz = dims_for(args)
+    return (nx // 4, nz * 3 // 4)
 
 
 def make_case(args):
     from paper_1409_5645_gb300 import cases
     nx, ny, nz = dims_for(args)
     cx, cz = col_for(args)
-    return cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=cx, col_z=cz)
+    return cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=cx, col_z=cz, tau=args.tau, magic=args.magic,
+                           rule=args.rule)
 
 
 # ---------------------------------------------------------------------------
@@ -250,10 +261,10 @@ def e2e_run(case, form, steps, local_rank):
 # ---------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_rate(dims, col, budget_s, max_steps=None, warmup=0):
+def oracle_rate(dims, col, budget_s, max_steps=None, warmup=0, tau=TAU, magic=MAGIC):
     from oracle.oracle import Oracle
     from paper_1409_5645_gb300 import cases
-    c = cases.dam_break(nx=dims[0], ny=dims[1], nz=dims[2], col_x=col[0], col_z=col[1])
+    c = cases.dam_break(nx=dims[0], ny=dims[1], nz=dims[2], col_x=col[0], col_z=col[1], tau=tau, magic=magic)
     o = Oracle.from_case(c)
     if warmup:
         o.step(warmup)
@@ -298,8 +309,9 @@ def main():
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(head["ms"] / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": forms[0], "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.small else "dam_break_128x64x64_fsl",
-                   "dims": list(dims_for(args)), "rule": "FSL", "tau": 0.51, "g": 1e-5,
+        "config": {"workload": WORKLOAD if dims_for(args) == DIMS else "dam_break_%dx%dx%d" % dims_for(args),
+                   "dims": list(dims_for(args)), "rule": "FSL" if args.rule else "FSK", "tau": args.tau,
+                   "magic": args.magic, "g": 1e-5,
                    "precision": forms[0], "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (N * 2 * 19 * s / 1e9)},
         "mflups_active": round(ws * (head["n_liquid"] + head["n_interface"]) * args.steps
@@ -339,7 +351,7 @@ def main():
                    "includes": "state upload from pinned host memory, per-step mass read"}
     # the oracle on the host cores (rank 0, N = 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, st, el = oracle_rate((128, 64, 64), (32, 48), budget_s=12.0)
+        rate, st, el = oracle_rate((128, 64, 64), (32, 48), budget_s=12.0, tau=args.tau, magic=args.magic)
         line["cpu_baseline"] = {"value": round(rate, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                                 "sample": f"FP64 oracle, dam break 128x64x64 (same setup scaled by 1/4), "
                                           f"{st} steps in {el:.1f} s, single thread"}
@@ -368,7 +380,8 @@ def reference_arm(args):
     col = (max(4, nx // 4), max(6, nz * 3 // 4))
     from oracle.oracle import Oracle
     from paper_1409_5645_gb300 import cases
-    c = cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=col[0], col_z=col[1])
+    c = cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=col[0], col_z=col[1], tau=args.tau, magic=args.magic,
+                        rule=args.rule)
     o = Oracle.from_case(c)
     o.step(args.warmup)
     t0 = time.perf_counter()
@@ -378,7 +391,8 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 4),
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_dims": [nx, ny, nz], "rule": "FSL", "tau": 0.51, "g": 1e-5},
+            "config": {"workload": WORKLOAD, "sample_dims": [nx, ny, nz], "rule": "FSL" if args.rule else "FSK",
+                       "tau": args.tau, "magic": args.magic, "g": 1e-5},
             "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                              "sample": f"FP64 oracle, dam break {nx}x{ny}x{nz} (same setup scaled), "
                                        f"{args.steps} timed steps, single thread of {ncores}"},
