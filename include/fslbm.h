@@ -68,7 +68,8 @@ enum fslbm_status {
   FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
   FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
-  FSLBM_ERR_TIMEOUT = -7   /* reserved for bounded waits */
+  FSLBM_ERR_TIMEOUT = -7,  /* reserved for bounded waits */
+  FSLBM_ERR_TOO_LARGE = -8 /* beyond the fixed scratch of fslbm_mass_balance_noalloc */
 };
 
 enum fslbm_cell { FSLBM_LIQUID = 1, FSLBM_INTERFACE = 2, FSLBM_GAS = 4, FSLBM_WALL = 8 };
@@ -226,6 +227,38 @@ int fslbm_adjoint_backward(fslbm_t *h, double *dJ_dnu, double dJ_dg[3], double *
  * and per adjoint step (segment recomputation excluded), and the device bytes
  * held (lattice + checkpoints + adjoint buffers). */
 int fslbm_adjoint_stats(fslbm_t *h, double *fwd_ms_per_step, double *adj_ms_per_step, size_t *peak_bytes);
+
+/* ---- Mass balance without device allocation --------------------------------
+ * The paper has no counterpart to this entry point; it is a service for
+ * callers that cannot allocate device memory once they run: applications whose
+ * framework owns the GPU's memory through its own pool and refuses other
+ * allocations, and time-critical loops where cudaMalloc/cudaFree would
+ * synchronise the device and stall other streams.  It computes
+ * M = sum_liquid rho + sum_interface m + lost over caller-owned device arrays
+ * and allocates nothing: its per-block partial sums live in a fixed array
+ * inside the library (FSLBM_NOALLOC_MAX_BLOCKS doubles, 32 KiB, held by every
+ * GPU that loads the library until the process exits).
+ *   flags     uint8 [n_cells] cell kinds, device memory
+ *   f_post    [19][n_cells] populations in the storage of `precision`:
+ *             double (FSLBM_F64), float (FSLBM_F32) or half holding f - w_q
+ *             (FSLBM_F16), device memory (e.g. from fslbm_get_fields)
+ *   m         double [n_cells] interface mass (read on interface cells only)
+ *   lost      added to the sum (the lost ledger of fslbm_total_mass)
+ *   mass_out  one double in device memory, written by the call
+ *   stream    cudaStream_t, NULL = legacy default stream; the call is
+ *             asynchronous on it and returns launch errors only
+ * At most FSLBM_NOALLOC_MAX_BLOCKS * FSLBM_NOALLOC_CELLS_PER_BLOCK cells
+ * (268,435,456); larger n_cells returns FSLBM_ERR_TOO_LARGE before any work.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's partial sums; each call writes every entry it reads first.
+ * Calls whose work overlaps on the GPU (concurrent streams) race on the
+ * array: order them. */
+#define FSLBM_NOALLOC_MAX_BLOCKS 4096
+#define FSLBM_NOALLOC_CELLS_PER_BLOCK 65536
+int fslbm_mass_balance_noalloc(const uint8_t *flags, const void *f_post, int precision, const double *m,
+                               long long n_cells, double lost, double *mass_out, void *stream);
 
 /* Steps taken since the last set_state. */
 long long fslbm_time(const fslbm_t *h);

@@ -19,7 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfslbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fslbm_step.cu", "fslbm_conv.cu", "fslbm_state.cu", "fslbm_api.cu", "fslbm_adjoint.cu"]
+SOURCES = ["fslbm_step.cu", "fslbm_conv.cu", "fslbm_state.cu", "fslbm_api.cu", "fslbm_adjoint.cu",
+           "fslbm_noalloc.cu"]
 
 
 def nvcc() -> str:
