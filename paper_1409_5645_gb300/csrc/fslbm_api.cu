@@ -2,8 +2,8 @@
 //
 // A handle owns every device buffer of one lattice.  fslbm_step enqueues, per
 // time step and with no host synchronisation:
-//   memset(counters) -> k_bulk -> k_iface -> mass reduction (2 kernels)
-//   -> 7 conversion kernels (dynamic interface only)
+//   memset(counters) -> k_segments -> k_bulk -> k_iface -> mass reduction
+//   (2 kernels) -> 5 conversion kernels (dynamic interface only)
 // and swaps the A/B population and fill-level buffers.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -126,12 +126,13 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;
-  const long long nseg = ((p.nx + 127) / 128) * (long long)p.ny * p.nz;
-  h->bulk_blocks = (int)(nseg < 152 * 12 ? nseg : 152 * 12);
+  // 32-cell segments; the bulk kernel runs one resident wave of warps
+  const long long nseg = ((p.nx + 31) / 32) * (long long)p.ny * p.nz;
+  h->bulk_blocks = 152 * (h->prec == FSLBM_F64 ? 4 : 8);
   h->iface_blocks = 152 * 8;
   h->list_blocks = 152 * 2;
   h->red_blocks = 152;
-  h->nparts = h->bulk_blocks + h->iface_blocks;
+  h->nparts = h->bulk_blocks * 4 + h->iface_blocks;  // one partial per bulk warp, per interface block
   if (h->nparts < 4096) h->nparts = 4096;
   bool ok = dalloc(h, &h->flags, N4) && dalloc(h, &h->mark, N4) &&
             dalloc(h, (char**)&h->fA, 19 * Nn * store_bytes(h->prec)) &&
@@ -353,7 +354,7 @@ static int step_t(fslbm* h) {
                              h->timing ? h : nullptr))
     return 1;
   if (mark_event(h, 2)) return 1;
-  if (launch_reduce(h->partials, (long long)h->bulk_blocks + h->iface_blocks, h->red, h->red_blocks, h->lost,
+  if (launch_reduce(h->partials, (long long)h->bulk_blocks * 4 + h->iface_blocks, h->red, h->red_blocks, h->lost,
                     h->step_mass, h->st))
     return 1;
   if (mark_event(h, 3)) return 1;

@@ -2,13 +2,13 @@
 // paper takes interface tracking from Koerner et al. and Thuerey).
 //
 // The step kernel appended interface cells with m > (1+eps) rho to the fill
-// list F and those with m < -eps rho to the empty list E.  Then, all as list
-// kernels (grid-stride; counts read on the device, no host synchronisation):
-//   mark     F / E marks on the cells
-//   fill     gas neighbours of F become new interface (NEWG, listed once by an
-//            atomic byte-OR); an E cell next to F leaves E
-//   newg     NEWG cells get f = f^eq(mean rho, mean u) over their liquid /
-//            interface neighbours (q order), collided, m = 0
+// list F and those with m < -eps rho to the empty list E, and marked them.
+// Then, all as list kernels (grid-stride; counts read on the device, no host
+// synchronisation):
+//   fill     gas neighbours of F become new interface (NEWG, claimed once by an
+//            atomic byte-OR; the claimant sets f = f^eq(mean rho, mean u) over
+//            their liquid / interface neighbours (q order), collided, m = 0);
+//            an E cell next to F leaves E
 //   empty    liquid neighbours of the remaining E become interface with m = rho
 //   share    excess (F: m - rho, E: m) / number of receivers (interface after
 //            the steps above, not converting); no receiver -> lost ledger
@@ -48,13 +48,47 @@ __device__ __forceinline__ typename Form<P>::R rho_out(const Par& p, const View<
   return r;
 }
 
+// A gas cell next to a filled cell becomes interface with f = f^eq(mean rho,
+// mean u) over its liquid/interface neighbours (kinds of step t, q order),
+// collided, m = 0, phi = 0.  Its neighbours' populations are final for the
+// step, and new cells are never read as neighbours (their kind is still gas).
 template <int P>
-__global__ void k_mark(Par p, View<P> v) {
-  int nf = min(load_count(&v.cnt[1]), v.cap), ne = min(load_count(&v.cnt[2]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf + ne; k += gridDim.x * blockDim.x) {
-    if (k < nf) v.mark[v.flist[k]] = MK_FILL;
-    else v.mark[v.elist[k - nf]] = MK_EMPTY;
+__device__ void init_new_cell(const Par& p, const View<P>& v, long long j) {
+  using R = typename Form<P>::R;
+  const size_t N = (size_t)p.N;
+  int x, y, z;
+  coords(p, j, x, y, z);
+  R rs = R(0), us0 = R(0), us1 = R(0), us2 = R(0);
+  int c = 0;
+#pragma unroll 1
+  for (int q = 1; q < 19; ++q) {
+    long long y2 = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+    if (y2 < 0) continue;
+    uint8_t ky = v.flags[y2] & KIND;
+    if (!is_fluid(ky)) continue;
+    R g[19];
+#pragma unroll
+    for (int r = 0; r < 19; ++r) g[r] = ldq<P>(v.fout, (size_t)r * N + (size_t)y2, r);
+    R rr, ux, uy, uz;
+    moments_post<R>(p, g, rr, ux, uy, uz);
+    rs += rr; us0 += ux; us1 += uy; us2 += uz;
+    ++c;
   }
+  R rbar = rs / R(c), u0 = us0 / R(c), u1 = us1 / R(c), u2 = us2 / R(c);
+  R r0 = p.compressible ? rbar : R(1);
+  R usq = u0 * u0 + u1 * u1 + u2 * u2;
+  R f[19];
+  f[0] = eplus<R, 0>(p, rbar, r0, u0, u1, u2, usq);
+#define FSL_EQ(q) f[q] = eplus<R, q>(p, rbar, r0, u0, u1, u2, usq) + eminus<R, q>(r0, u0, u1, u2);
+  FSL_EQ(1) FSL_EQ(2) FSL_EQ(3) FSL_EQ(4) FSL_EQ(5) FSL_EQ(6) FSL_EQ(7) FSL_EQ(8) FSL_EQ(9)
+  FSL_EQ(10) FSL_EQ(11) FSL_EQ(12) FSL_EQ(13) FSL_EQ(14) FSL_EQ(15) FSL_EQ(16) FSL_EQ(17) FSL_EQ(18)
+#undef FSL_EQ
+  R rho, ux, uy, uz;
+  collide<R>(p, f, rho, ux, uy, uz);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)j, q, f[q]);
+  v.m[j] = 0.0;
+  v.phout[j] = R(0);
 }
 
 template <int P>
@@ -71,54 +105,14 @@ __global__ void k_fill(Par p, View<P> v) {
       uint8_t kj = v.flags[j] & KIND;
       if (kj == GAS) {
         uint8_t old = or_u8(v.mark, j, MK_NEWG);
-        if (!(old & MK_NEWG)) push(v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
+        if (!(old & MK_NEWG)) {  // the first claimant initialises the new cell
+          push(v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
+          init_new_cell<P>(p, v, j);
+        }
       } else if (kj == IFC) {
         if (((volatile uint8_t*)v.mark)[j] & MK_EMPTY) clear_u8(v.mark, j, MK_EMPTY);
       }
     }
-  }
-}
-
-template <int P>
-__global__ void k_newg(Par p, View<P> v) {
-  using R = typename Form<P>::R;
-  const size_t N = (size_t)p.N;
-  int nn = min(load_count(&v.cnt[3]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
-    long long j = v.nglist[k];
-    int x, y, z;
-    coords(p, j, x, y, z);
-    R rs = R(0), us0 = R(0), us1 = R(0), us2 = R(0);
-    int c = 0;
-#pragma unroll 1
-    for (int q = 1; q < 19; ++q) {
-      long long y2 = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (y2 < 0) continue;
-      uint8_t ky = v.flags[y2] & KIND;
-      if (!is_fluid(ky)) continue;
-      R g[19];
-#pragma unroll
-      for (int r = 0; r < 19; ++r) g[r] = ldq<P>(v.fout, (size_t)r * N + (size_t)y2, r);
-      R rr, ux, uy, uz;
-      moments_post<R>(p, g, rr, ux, uy, uz);
-      rs += rr; us0 += ux; us1 += uy; us2 += uz;
-      ++c;
-    }
-    R rbar = rs / R(c), u0 = us0 / R(c), u1 = us1 / R(c), u2 = us2 / R(c);
-    R r0 = p.compressible ? rbar : R(1);
-    R usq = u0 * u0 + u1 * u1 + u2 * u2;
-    R f[19];
-    f[0] = eplus<R, 0>(p, rbar, r0, u0, u1, u2, usq);
-#define FSL_EQ(q) f[q] = eplus<R, q>(p, rbar, r0, u0, u1, u2, usq) + eminus<R, q>(r0, u0, u1, u2);
-    FSL_EQ(1) FSL_EQ(2) FSL_EQ(3) FSL_EQ(4) FSL_EQ(5) FSL_EQ(6) FSL_EQ(7) FSL_EQ(8) FSL_EQ(9)
-    FSL_EQ(10) FSL_EQ(11) FSL_EQ(12) FSL_EQ(13) FSL_EQ(14) FSL_EQ(15) FSL_EQ(16) FSL_EQ(17) FSL_EQ(18)
-#undef FSL_EQ
-    R rho, ux, uy, uz;
-    collide<R>(p, f, rho, ux, uy, uz);
-#pragma unroll
-    for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)j, q, f[q]);
-    v.m[j] = 0.0;
-    v.phout[j] = R(0);
   }
 }
 
@@ -264,9 +258,7 @@ __global__ void k_final(Par p, View<P> v) {
 
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks) {
-  k_mark<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_fill<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_newg<P><<<list_blocks, 128, 0, st>>>(p, v);
+  k_fill<P><<<list_blocks, 128, 0, st>>>(p, v);
   k_empty<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_share<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_recv<P><<<list_blocks, 256, 0, st>>>(p, v);

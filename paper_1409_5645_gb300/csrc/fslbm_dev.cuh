@@ -362,18 +362,33 @@ __device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const 
   R (&H)[9] = G.H;
   G.closed = false;
   G.a = 2; G.b = 0; G.s = 1;
+  // cells within 3 of the node are inside the lattice without a wrap: plain
+  // offsets; otherwise the general neighbour rule
+  const bool interior = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
+  const long long i0 = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
+  const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+  // fill level seen by the geometry; the phi load is issued whatever the kind
+  // so that all loads of the stencil are independent
+  auto sample = [&](int dx, int dy, int dz, uint8_t& kj) -> R {
+    long long j = interior ? i0 + dx + sy * dy + sz * dz : nbr(p, x, y, z, dx, dy, dz);
+    R raw = j >= 0 ? phin[j] : R(0);
+    kj = kind_at(flags, j);
+    if (kj == LIQ) return R(1);
+    if (kj == IFC || (kj == GAS && p.freeze)) return raw;
+    return R(0);
+  };
   R g0 = R(0), g1 = R(0), g2 = R(0);
-#pragma unroll 1
+#pragma unroll
   for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll 1
+#pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         if (!dx && !dy && !dz) continue;
-        long long j = nbr(p, x, y, z, dx, dy, dz);
-        uint8_t kj = kind_at(flags, j);
-        R pj = (kj == WALL) ? phic : phi_at<R>(p, phin, j, kj);
-        int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+        uint8_t kj;
+        R pj = sample(dx, dy, dz, kj);
+        if (kj == WALL) pj = phic;
+        const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
         if (dx) g0 += R(dx * (2 - ay) * (2 - az)) * pj;
         if (dy) g1 += R(dy * (2 - az) * (2 - ax)) * pj;
         if (dz) g2 += R(dz * (2 - ax) * (2 - ay)) * pj;
@@ -395,23 +410,25 @@ __device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const 
   const int s = (a == 0 ? n[0] : (a == 1 ? n[1] : n[2])) > R(0) ? 1 : -1;
   const int b = (a == 0) ? 1 : 0;  // the third axis is the remaining one
   G.a = a; G.b = b; G.s = s;
+  // heights over 3x3 columns of 7 cells along a; closed when every column
+  // has liquid at its liquid end, gas at its gas end and no wall
   bool closed = true;
-#pragma unroll 1
-  for (int ib = -1; ib <= 1 && closed; ++ib)
-#pragma unroll 1
-    for (int ic = -1; ic <= 1 && closed; ++ic) {
+#pragma unroll
+  for (int ib = -1; ib <= 1; ++ib)
+#pragma unroll
+    for (int ic = -1; ic <= 1; ++ic) {
       R sum = R(0);
-#pragma unroll 1
+#pragma unroll
       for (int k = -3; k <= 3; ++k) {
-        int o0 = (a == 0) ? k : ((b == 0) ? ib : ic);
-        int o1 = (a == 1) ? k : ((b == 1) ? ib : ic);
-        int o2 = (a == 2) ? k : ((b == 2) ? ib : ic);
-        long long j = nbr(p, x, y, z, o0, o1, o2);
-        uint8_t kj = kind_at(flags, j);
-        if (kj == WALL) { closed = false; break; }
-        if (k == -3 * s && kj != LIQ) { closed = false; break; }
-        if (k == 3 * s && kj != GAS) { closed = false; break; }
-        sum += phi_at<R>(p, phin, j, kj);
+        const int o0 = (a == 0) ? k : ((b == 0) ? ib : ic);
+        const int o1 = (a == 1) ? k : ((b == 1) ? ib : ic);
+        const int o2 = (a == 2) ? k : ((b == 2) ? ib : ic);
+        uint8_t kj;
+        R pj = sample(o0, o1, o2, kj);
+        closed = closed && kj != WALL;
+        if (k == -3) closed = closed && (s > 0 ? kj == LIQ : kj == GAS);
+        if (k == 3) closed = closed && (s > 0 ? kj == GAS : kj == LIQ);
+        sum += pj;
       }
       H[(ib + 1) * 3 + (ic + 1)] = sum;
     }

@@ -25,7 +25,7 @@ struct fslbm {
   void* phiB;
   double* wd;
   int* lists[6];
-  int* seglist;  // 128-cell x segments holding fluid (rebuilt every step)
+  int* seglist;  // 32-cell x segments holding fluid (rebuilt every step)
   int* cnt;
   double* share;
   double* partials;

@@ -1,8 +1,8 @@
 // fslbm_step.cu -- the stream-collide kernels of one FSLBM time step.
 //
-// k_segments  compact list of the 128-cell x segments holding fluid (so that
-//          gas-only stretches of the lattice cost one flag scan, not a block).
-// k_bulk   persistent blocks over that list, one thread per cell.  Liquid
+// k_segments  compact list of the 32-cell x segments holding fluid (so that
+//          gas-only stretches of the lattice cost one flag scan, not a warp).
+// k_bulk   every warp walks that list on its own, one lane per cell.  Liquid
 //          cells pull their 19 populations (Eq. lbe1), apply half-way
 //          bounce-back / CLI at walls, collide (Eq. lbe2) and store; interface
 //          cells are compacted into a list by warp ballot.  The liquid density
@@ -101,31 +101,27 @@ __device__ __forceinline__ void wall_links(const Par& p, const View<P>& v, long 
 }
 
 // ---------------------------------------------------------------------------
-// k_segments: compact list of the 128-cell x segments that hold a liquid or
-// interface cell (one thread per segment, one atomic per warp).
+// k_segments: compact list of the 32-cell x segments (one warp each) that
+// hold a liquid or interface cell; one thread per segment, one atomic per warp.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restrict__ flags, int* __restrict__ seglist,
                                                   int* __restrict__ count) {
-  const int nsx = (p.nx + 127) >> 7;
+  const int nsx = (p.nx + 31) >> 5;
   const long long nseg = (long long)nsx * p.ny * p.nz;
   const long long sgi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool act = false;
   if (sgi < nseg) {
     const long long row = sgi / nsx;
-    const int x0 = (int)(sgi - row * nsx) << 7;
-    const int len = min(128, p.nx - x0);
+    const int x0 = (int)(sgi - row * nsx) << 5;
+    const int len = min(32, p.nx - x0);
     const uint8_t* base = flags + row * p.nx + x0;
-    unsigned acc = 0u;
-    if (len == 128 && ((p.nx & 15) == 0)) {
+    if (len == 32 && ((p.nx & 15) == 0)) {
       const uint4* v4 = reinterpret_cast<const uint4*>(base);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        uint4 w = __ldg(v4 + k);
-        acc |= w.x | w.y | w.z | w.w;
-      }
-      // any byte with a liquid or interface bit
-      act = (acc & 0x03030303u) != 0u;
+      uint4 a = __ldg(v4), b = __ldg(v4 + 1);
+      unsigned acc = a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w;
+      act = (acc & 0x03030303u) != 0u;  // a byte with the liquid or interface bit
     } else {
+      unsigned acc = 0u;
       for (int k = 0; k < len; ++k) acc |= base[k];
       act = (acc & 0x03u) != 0u;
     }
@@ -140,19 +136,23 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
 }
 
 // ---------------------------------------------------------------------------
-// k_bulk: persistent blocks over the segment list, one thread per cell
+// k_bulk: every warp walks the segment list on its own (no block barrier),
+// one lane per cell; the liquid density is summed per warp.
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(128) k_bulk(Par p, View<P> v, const int* __restrict__ seglist,
+__global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P> v, const int* __restrict__ seglist,
                                               const int* __restrict__ segcount) {
   using R = typename Form<P>::R;
-  const int nsx = (p.nx + 127) >> 7;
+  const int nsx = (p.nx + 31) >> 5;
   const int nseg = *((volatile const int*)segcount);
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
   double msum = 0.0;
-  for (int si = blockIdx.x; si < nseg; si += gridDim.x) {
+  for (int si = gw; si < nseg; si += nw) {
     const int sg = seglist[si];
     const int row = sg / nsx;
-    const int x = ((sg - row * nsx) << 7) + threadIdx.x;
+    const int x = ((sg - row * nsx) << 5) + lane;
     const int y = row % p.ny, z = row / p.ny;
     const bool in = x < p.nx;
     const long long i = (long long)row * p.nx + x;
@@ -194,8 +194,9 @@ __global__ void __launch_bounds__(128) k_bulk(Par p, View<P> v, const int* __res
 #undef FSL_ST
     msum += (double)rho;
   }
-  double s = block_sum128(msum);
-  if (threadIdx.x == 0) v.partials[blockIdx.x] = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
+  if (lane == 0) v.partials[gw] = msum;
 }
 
 // ---------------------------------------------------------------------------
@@ -291,6 +292,8 @@ __global__ void __launch_bounds__(128) k_iface(Par p, View<P> v, int bulk_blocks
         // no liquid/interface neighbour -> empty
         fill = mm > (1.0 + p.eps) * (double)rho || ((p.cleanup & 1) && gasm == 0u);
         empty = !fill && (mm < -p.eps * (double)rho || ((p.cleanup & 2) && (wallm | gasm) == 0x7fffeu));
+        if (fill) v.mark[i] = MK_FILL;  // marks are zero between steps; each cell writes only its own
+        else if (empty) v.mark[i] = MK_EMPTY;
       }
       msum += mm;
     }
@@ -328,11 +331,11 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ in, l
 template <int P>
 int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
                         int* seglist, int* segcount, void* timing_handle) {
-  const long long nseg = (long long)((p.nx + 127) / 128) * p.ny * p.nz;
+  const long long nseg = (long long)((p.nx + 31) / 32) * p.ny * p.nz;
   k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(p, v.flags, seglist, segcount);
   k_bulk<P><<<bulk_blocks, 128, 0, st>>>(p, v, seglist, segcount);
   if (timing_handle && fslbm_mark_between(timing_handle)) return 1;
-  k_iface<P><<<iface_blocks, 128, 0, st>>>(p, v, bulk_blocks);
+  k_iface<P><<<iface_blocks, 128, 0, st>>>(p, v, bulk_blocks * 4);  // after the bulk warps' partials
   return (int)cudaGetLastError();
 }
 
