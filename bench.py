@@ -35,7 +35,7 @@ WORKLOAD = "dam_break_512x256x256_fsl"
 DIMS = (512, 256, 256)
 COL = (128, 192)
 TAU, MAGIC = 0.52, 0.005
-KERNELS_PER_STEP = 10  # k_segments, k_bulk, k_iface, 2 x k_reduce, 5 conversion kernels
+KERNELS_PER_STEP = 11  # k_segments, k_bulk, k_iface, 2 x k_reduce, 6 conversion kernels
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 

@@ -3,7 +3,7 @@
 // A handle owns every device buffer of one lattice.  fslbm_step enqueues, per
 // time step and with no host synchronisation:
 //   memset(counters) -> k_segments -> k_bulk -> k_iface -> mass reduction
-//   (2 kernels) -> 5 conversion kernels (dynamic interface only)
+//   (2 kernels) -> 6 conversion kernels (dynamic interface only)
 // and swaps the A/B population and fill-level buffers.
 #include <cuda_runtime.h>
 #include <stdio.h>

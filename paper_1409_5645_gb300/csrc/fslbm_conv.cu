@@ -5,10 +5,10 @@
 // list F and those with m < -eps rho to the empty list E, and marked them.
 // Then, all as list kernels (grid-stride; counts read on the device, no host
 // synchronisation):
-//   fill     gas neighbours of F become new interface (NEWG, claimed once by an
-//            atomic byte-OR; the claimant sets f = f^eq(mean rho, mean u) over
-//            their liquid / interface neighbours (q order), collided, m = 0);
-//            an E cell next to F leaves E
+//   fill     gas neighbours of F become new interface (NEWG, listed once by an
+//            atomic byte-OR); an E cell next to F leaves E
+//   newg     NEWG cells get f = f^eq(mean rho, mean u) over their liquid /
+//            interface neighbours (q order), collided, m = 0
 //   empty    liquid neighbours of the remaining E become interface with m = rho
 //   share    excess (F: m - rho, E: m) / number of receivers (interface after
 //            the steps above, not converting); no receiver -> lost ledger
@@ -32,10 +32,20 @@ __device__ __forceinline__ void clear_u8(uint8_t* base, long long j, unsigned bi
   unsigned sh = (unsigned)(j & 3) * 8u;
   atomicAnd(w, ~(bits << sh));
 }
-__device__ __forceinline__ void push(int* list, int* count, int cap, int value, int* err) {
-  int k = atomicAdd(count, 1);
-  if (k < cap) list[k] = value;
-  else atomicOr(err, ERRB_OVERFLOW);
+// append `value` for every converged lane with `pred`, one atomic per warp
+__device__ __forceinline__ void push(bool pred, int* list, int* count, int cap, int value, int* err) {
+  const unsigned act = __activemask();
+  const unsigned bal = __ballot_sync(act, pred);
+  if (!bal) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(bal));
+  base = __shfl_sync(act, base, leader);
+  if (pred) {
+    int k = base + __popc(bal & ((1u << lane) - 1u));
+    if (k < cap) list[k] = value;
+    else atomicOr(err, ERRB_OVERFLOW);
+  }
 }
 __device__ __forceinline__ int load_count(const int* c) { return *((volatile const int*)c); }
 
@@ -101,19 +111,24 @@ __global__ void k_fill(Par p, View<P> v) {
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
       long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (j < 0) continue;
-      uint8_t kj = v.flags[j] & KIND;
+      uint8_t kj = j < 0 ? (uint8_t)WALL : (uint8_t)(v.flags[j] & KIND);
+      bool won = false;
       if (kj == GAS) {
         uint8_t old = or_u8(v.mark, j, MK_NEWG);
-        if (!(old & MK_NEWG)) {  // the first claimant initialises the new cell
-          push(v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
-          init_new_cell<P>(p, v, j);
-        }
+        won = !(old & MK_NEWG);  // the first claimant lists the new cell
       } else if (kj == IFC) {
         if (((volatile uint8_t*)v.mark)[j] & MK_EMPTY) clear_u8(v.mark, j, MK_EMPTY);
       }
+      push(won, v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
     }
   }
+}
+
+template <int P>
+__global__ void k_newg(Par p, View<P> v) {
+  int nn = min(load_count(&v.cnt[3]), v.cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x)
+    init_new_cell<P>(p, v, v.nglist[k]);
 }
 
 template <int P>
@@ -136,7 +151,9 @@ __global__ void k_empty(Par p, View<P> v) {
         double mm = (double)r;
         v.m[j] = mm;
         v.phout[j] = (R)(mm / (double)r);
-        push(v.nllist, &v.cnt[4], v.cap, (int)j, v.err);
+        int kk = atomicAdd(&v.cnt[4], 1);
+        if (kk < v.cap) v.nllist[kk] = (int)j;
+        else atomicOr(v.err, ERRB_OVERFLOW);
       }
     }
   }
@@ -174,10 +191,14 @@ __global__ void k_share(Par p, View<P> v) {
     v.m[i] = isF ? rho : 0.0;
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
-      if (!(rm & (1u << q))) continue;
-      long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      uint8_t old = or_u8(v.mark, j, MK_RECV);
-      if (!(old & MK_RECV)) push(v.rlist, &v.cnt[5], v.cap, (int)j, v.err);
+      bool first = false;
+      long long j = 0;
+      if (rm & (1u << q)) {
+        j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+        uint8_t old = or_u8(v.mark, j, MK_RECV);
+        first = !(old & MK_RECV);
+      }
+      push(first, v.rlist, &v.cnt[5], v.cap, (int)j, v.err);
     }
   }
 }
@@ -258,7 +279,8 @@ __global__ void k_final(Par p, View<P> v) {
 
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks) {
-  k_fill<P><<<list_blocks, 128, 0, st>>>(p, v);
+  k_fill<P><<<list_blocks, 256, 0, st>>>(p, v);
+  k_newg<P><<<list_blocks, 128, 0, st>>>(p, v);
   k_empty<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_share<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_recv<P><<<list_blocks, 256, 0, st>>>(p, v);

@@ -299,7 +299,7 @@ __device__ __forceinline__ R cube_area(R a, R m1, R m2, R m3) {
 // the side n.(x - x_c) <= d) of the plane cutting volume fraction ph.  The
 // fill is kept in [1e-9, 1 - 1e-9] first: at an empty or full corner the
 // inverse volume grows like a cube root and would turn rounding of ph into
-// visible plane shifts.  Bisection on the plane constant.
+// visible plane shifts.  Bracketing bisection, then Newton on the convex half.
 template <class R>
 __device__ R plic_offset(R nx_, R ny_, R nz_, R ph) {
   R a0 = fabs(nx_), a1 = fabs(ny_), a2 = fabs(nz_);
@@ -312,15 +312,29 @@ __device__ R plic_offset(R nx_, R ny_, R nz_, R ph) {
   if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
   const R lo_ph = R(1e-9), hi_ph = R(1) - R(1e-9);
   ph = ph < lo_ph ? lo_ph : (ph > hi_ph ? hi_ph : ph);
-  R lo = R(0), hi = R(1);
-  constexpr int iters = sizeof(R) == 8 ? 96 : 48;
+  // the volume is point-symmetric about alpha = 1/2: solve on [0, 1/2] for
+  // min(ph, 1 - ph), where it is convex
+  const bool upper = ph > R(0.5);
+  const R tv = upper ? R(1) - ph : ph;
+  R lo = R(0), hi = R(0.5);
 #pragma unroll 1
-  for (int it = 0; it < iters; ++it) {
+  for (int it = 0; it < 20; ++it) {  // bracket to 2^-21
     R mid = R(0.5) * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (cube_vol(mid, a0, a1, a2) < ph) lo = mid; else hi = mid;
+    if (cube_vol_half(mid, a0, a1, a2) < tv) lo = mid; else hi = mid;
   }
-  return L1 * (R(0.5) * (lo + hi) - R(0.5));
+  // Newton from the right end of the bracket (convex, increasing: monotone),
+  // kept inside the bracket
+  R al = hi;
+  constexpr int newton = sizeof(R) == 8 ? 6 : 3;
+#pragma unroll 1
+  for (int it = 0; it < newton; ++it) {
+    R ar = cube_area_half(al, a0, a1, a2);
+    if (!(ar > R(0))) break;
+    R nx2 = al - (cube_vol_half(al, a0, a1, a2) - tv) / ar;
+    al = nx2 < lo ? lo : (nx2 > hi ? hi : nx2);
+  }
+  if (upper) al = R(1) - al;
+  return L1 * (al - R(0.5));
 }
 
 // fill level as seen by the geometry: 1 liquid, stored for interface cells

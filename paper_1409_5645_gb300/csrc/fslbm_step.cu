@@ -126,13 +126,19 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
       act = (acc & 0x03u) != 0u;
     }
   }
-  unsigned bal = __ballot_sync(0xffffffffu, act);
-  if (bal) {
-    int lane = threadIdx.x & 31, leader = __ffs(bal) - 1, b = 0;
-    if (lane == leader) b = atomicAdd(count, __popc(bal));
-    b = __shfl_sync(0xffffffffu, b, leader);
-    if (act) seglist[b + __popc(bal & ((1u << lane) - 1u))] = (int)sgi;
+  // one global atomic per block: warp counts -> block offsets in shared memory
+  __shared__ int wcount[8], wbase[8], bbase;
+  const unsigned bal = __ballot_sync(0xffffffffu, act);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wcount[w] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < 8; ++k) { wbase[k] = t; t += wcount[k]; }
+    bbase = t ? atomicAdd(count, t) : 0;
   }
+  __syncthreads();
+  if (act) seglist[bbase + wbase[w] + __popc(bal & ((1u << lane) - 1u))] = (int)sgi;
 }
 
 // ---------------------------------------------------------------------------
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
 // k_iface
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(128) k_iface(Par p, View<P> v, int bulk_blocks) {
+__global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int bulk_blocks) {
   using R = typename Form<P>::R;
   const size_t N = (size_t)p.N;
   const int count = min(*((volatile int*)&v.cnt[0]), v.cap);
