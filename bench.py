@@ -35,7 +35,7 @@ WORKLOAD = "dam_break_512x256x256_fsl"
 DIMS = (512, 256, 256)
 COL = (128, 192)
 TAU, MAGIC = 0.52, 0.005
-KERNELS_PER_STEP = 11  # k_segments, k_bulk, k_iface, 2 x k_reduce, 6 conversion kernels
+KERNELS_PER_STEP = 12  # k_segments, k_bulk, k_iface, 2 x k_reduce, 7 conversion kernels
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--tau", type=float, default=TAU)
     ap.add_argument("--magic", type=float, default=MAGIC)
     ap.add_argument("--rule", type=int, default=1, help="1 = FSL, 0 = FSK")
+    ap.add_argument("--bulk-loads", default="plain", choices=["plain", "async", "tma"],
+                    help="how the FP32/FP16 bulk kernel reaches its pulled values")
     return ap.parse_args()
 
 
@@ -73,7 +75,7 @@ def make_case(args):
     nx, ny, nz = dims_for(args)
     cx, cz = col_for(args)
     return cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=cx, col_z=cz, tau=args.tau, magic=args.magic,
-                           rule=args.rule)
+                           rule=args.rule, bulk_loads=args.bulk_loads)
 
 
 # ---------------------------------------------------------------------------
@@ -165,7 +167,7 @@ def hbm_peak():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("fslbm_step.cu", "fslbm_dev.cuh"):
+    for f in ("fslbm_step.cu", "fslbm_staged.cu", "fslbm_pull.cuh", "fslbm_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -228,7 +230,7 @@ def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False):
     nliq1, nifc1 = count_kinds(lat)
     out = dict(ms=ms, steps=steps, groups_ms=groups, timed_steps=nt, mass0=M0, mass1=M1, lost=lost,
                n_liquid=(nliq0 + nliq1) / 2, n_interface=(nifc0 + nifc1) / 2, clocks=clk,
-               device_bytes=lat.device_bytes, t_end=lat.time)
+               device_bytes=lat.device_bytes, t_end=lat.time, bulk_loads=lat.bulk_loads)
     lat.close()
     torch.cuda.synchronize(dev)
     return out
@@ -318,7 +320,8 @@ def main():
                                / (ms_max / 1e3) / 1e6, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": ncu_traffic(forms[0]),
-                     "kernel": "k_bulk", "peak_kind": peak_kind,
+                     "kernel": {"tma": "k_bulk_tma", "async": "k_bulk_async"}.get(head["bulk_loads"], "k_bulk"),
+                     "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bulk, "launch_ms": round(bulk_ms, 5)},
         "step_roofline": {"achieved": round(step_gbs, 1), "frac": round(step_gbs / peak, 4),
                           "alg_bytes_per_step": alg_step},

@@ -68,13 +68,25 @@ enum fslbm_status {
   FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
   FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
-  FSLBM_ERR_TIMEOUT = -7,  /* reserved for bounded waits */
+  FSLBM_ERR_TIMEOUT = -7,  /* a bounded device-side wait expired (staged loads of the bulk kernel) */
   FSLBM_ERR_TOO_LARGE = -8 /* beyond the fixed scratch of fslbm_mass_balance_noalloc */
 };
 
 enum fslbm_cell { FSLBM_LIQUID = 1, FSLBM_INTERFACE = 2, FSLBM_GAS = 4, FSLBM_WALL = 8 };
 
 enum fslbm_where { FSLBM_HOST = 0, FSLBM_DEVICE = 1 };
+
+/* Loads of the bulk stream-collide kernel (an implementation choice with no
+ * counterpart in the paper; the pull of Eq. lbe1 is the same every way, and
+ * so are the results, bit for bit).  FP64 lattices always load plainly. */
+enum fslbm_loads {
+  FSLBM_LOADS_PLAIN = 0, /* default: plain coalesced global loads (the fastest on GB300) */
+  FSLBM_LOADS_ASYNC = 1, /* each lane copies its 19 values into shared memory with cp.async,
+                            two 32-cell segments ahead of use */
+  FSLBM_LOADS_TMA = 2    /* the 19 rows of a segment by tensor-map (TMA) copies; needs nx a multiple
+                            of 16 bytes of elements and nx >= 32 cells + two 16-byte halos, else
+                            plain loads */
+};
 
 /* Field bits of fslbm_get_fields; out[] holds one pointer per set bit, in
  * increasing bit order. */
@@ -111,6 +123,8 @@ typedef struct {
                          it recovers them by inverting the collision from the stored populations
                          (exact in FP64, limited by the storage precision in FP32/FP16) */
   double delta_min;   /* lower clamp of the free-surface link fraction, default 0 */
+  int bulk_loads;     /* fslbm_loads: how the bulk kernel of FP32/FP16 lattices reaches the
+                         pulled values (FP64 always loads them plainly); same results every way */
   int precision;      /* fslbm_precision */
   void *stream;       /* cudaStream_t for all work of the handle; NULL = legacy default */
 } fslbm_params;
@@ -262,6 +276,10 @@ int fslbm_mass_balance_noalloc(const uint8_t *flags, const void *f_post, int pre
 
 /* Steps taken since the last set_state. */
 long long fslbm_time(const fslbm_t *h);
+
+/* The fslbm_loads the bulk kernel of this handle uses (FSLBM_ERR_ARG for
+ * NULL).  An implementation property with no counterpart in the paper. */
+int fslbm_bulk_loads(const fslbm_t *h);
 
 /* Bytes of device memory held by the handle. */
 size_t fslbm_device_bytes(const fslbm_t *h);

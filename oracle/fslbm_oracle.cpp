@@ -466,7 +466,7 @@ struct Sim {
   // ---------------------------------------------------------------------
   // One time step t -> t+1.
   // ---------------------------------------------------------------------
-  int step() {
+  void clear_scratch() {
     const long NN = N;
     ft.assign((size_t)Q * NN, T(0));
     nplus.assign((size_t)Q * NN, T(0));
@@ -476,10 +476,11 @@ struct Sim {
     gd.assign(NN, T(0));
     gk.assign(NN, T(0));
     gok.assign(NN, 0);
-    int st = OK;
+  }
 
-    // 1. geometry at time t
-    for (long i = 0; i < NN; ++i) {
+  // 1. geometry at time t
+  void stage_geometry() {
+    for (long i = 0; i < N; ++i) {
       if (flag[i] != IFC) continue;
       T n[3], d, k;
       bool ok;
@@ -487,7 +488,12 @@ struct Sim {
       for (int a = 0; a < 3; ++a) gn[3 * i + a] = n[a];
       gd[i] = d; gk[i] = k; gok[i] = ok ? 1 : 0;
     }
+  }
 
+  int step() {
+    const long NN = N;
+    clear_scratch();
+    stage_geometry();
     // 2. collision at time t (Eq. lbe2)
     for (long i = 0; i < NN; ++i) {
       if (!fluid(flag[i])) continue;
@@ -501,6 +507,45 @@ struct Sim {
       rho_t[i] = rho;
       for (int a = 0; a < 3; ++a) u_t[3 * i + a] = u[a];
     }
+    return stream_and_convert();
+  }
+
+  // One step from a post-collision state f~(t) given directly (test entry for
+  // sampled windows of a large lattice).  The moments of the pre-collision
+  // state follow from f~ (sum f~ = rho, sum c f~ = rho_0 U + F) and
+  // n^+ = (f~^+ - e^+) / (1 + lambda_+) (Eq. lbe2 restricted to the even part);
+  // n^- is not needed by the step.
+  int step_from_post(const double* ftp) {
+    const long NN = N;
+    clear_scratch();
+    stage_geometry();
+    for (long i = 0; i < NN; ++i) {
+      if (!fluid(flag[i])) continue;
+      T r = T(0), j[3] = {T(0), T(0), T(0)};
+      for (int q = 0; q < Q; ++q) {
+        T v = T(ftp[(size_t)q * NN + i]);
+        ft[(size_t)q * NN + i] = v;
+        r += v;
+        for (int a = 0; a < 3; ++a)
+          if (CV[q][a] != 0) j[a] += T((double)CV[q][a]) * v;
+      }
+      T r0 = rho0(r);
+      T u[3];
+      for (int a = 0; a < 3; ++a) u[a] = j[a] / r0 - T(0.5) * gv[a];
+      for (int q = 0; q < Q; ++q) {
+        T fp = T(0.5) * (ft[(size_t)q * NN + i] + ft[(size_t)opp[q] * NN + i]);
+        nplus[(size_t)q * NN + i] = (fp - e_plus(q, r, u, r0)) / (T(1.0) + lam_p);
+      }
+      rho_t[i] = r;
+      for (int a = 0; a < 3; ++a) u_t[3 * i + a] = u[a];
+    }
+    return stream_and_convert();
+  }
+
+  // stages 3-5 of a step, from ft / nplus / rho_t / u_t / geometry of time t
+  int stream_and_convert() {
+    const long NN = N;
+    int st = OK;
 
     // 3. pull streaming (Eq. lbe1) with closures for the missing populations
     std::vector<T> fn((size_t)Q * NN, T(0));
@@ -840,6 +885,23 @@ extern "C" int orc_set_state(void* hv, const uint8_t* flags, const double* f, co
   OrcHandle* h = (OrcHandle*)hv;
   return h->dual ? set_state_impl(h->sv, flags, f, phi, wall_delta)
                  : set_state_impl(h->sd, flags, f, phi, wall_delta);
+}
+
+// One step from a post-collision state: flags, f~(t) [19][N], interface m,
+// and fill levels phi (as the library reports them).  FP64 handles only.
+extern "C" int orc_step_from_post(void* hv, const uint8_t* flags, const double* ft, const double* m,
+                                  const double* phi) {
+  OrcHandle* h = (OrcHandle*)hv;
+  if (h->dual) return ERR_ARG;
+  Sim<double>* s = h->sd;
+  for (long i = 0; i < s->N; ++i) {
+    s->flag[i] = flags[i];
+    s->m[i] = (flags[i] == IFC) ? m[i] : 0.0;
+    s->phi[i] = (flags[i] == IFC || (flags[i] == GAS && s->p.freeze)) ? phi[i] : 0.0;
+  }
+  s->lost = 0.0;
+  int r = s->step_from_post(ft);
+  return r;
 }
 
 extern "C" int orc_step(void* hv, int n) {

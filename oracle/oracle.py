@@ -75,6 +75,7 @@ def lib():
             L.orc_plic_offset.argtypes = [dp, C.c_double]
             L.orc_counters.argtypes = [vp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
             L.orc_seed.argtypes = [vp, C.c_double, dp, dp]
+            L.orc_step_from_post.argtypes = [vp, u8p, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -155,6 +156,14 @@ class Oracle:
 
     def step(self, n: int = 1) -> int:
         return self.L.orc_step(self.h, int(n))
+
+    def step_from_post(self, flags, f_post, m, phi) -> int:
+        """One step from a post-collision state (FP64 handles)."""
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        f_post, m, phi = _f64(f_post), _f64(m), _f64(phi)
+        self._keep_post = (flags, f_post, m, phi)
+        return self.L.orc_step_from_post(self.h, flags.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(f_post),
+                                         _dp(m), _dp(phi))
 
     def get(self, field: int, tangent: bool = False) -> np.ndarray:
         size = {F_PRE: 19 * self.N, F_POST: 19 * self.N, VEL: 3 * self.N}.get(field, self.N)

@@ -3,7 +3,7 @@
 // A handle owns every device buffer of one lattice.  fslbm_step enqueues, per
 // time step and with no host synchronisation:
 //   memset(counters) -> k_segments -> k_bulk -> k_iface -> mass reduction
-//   (2 kernels) -> 6 conversion kernels (dynamic interface only)
+//   (2 kernels) -> 7 conversion kernels (dynamic interface only)
 // and swaps the A/B population and fill-level buffers.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -52,6 +52,8 @@ static void free_all(fslbm* h) {
     if (p) cudaFree(p);
   for (int k = 0; k < 6; ++k)
     if (h->lists[k]) cudaFree(h->lists[k]);
+  free(h->tmap);
+  h->tmap = nullptr;
 }
 
 template <class T>
@@ -89,6 +91,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   long long N = (long long)q.dims[0] * q.dims[1] * q.dims[2];
   if (N >= (1LL << 31)) return FSLBM_ERR_ARG;
   if (q.precision == FSLBM_F16 && q.compressible) return FSLBM_ERR_ARG;
+  if (q.bulk_loads < FSLBM_LOADS_PLAIN || q.bulk_loads > FSLBM_LOADS_TMA) return FSLBM_ERR_ARG;
 
   fslbm* h = (fslbm*)calloc(1, sizeof(fslbm));
   if (!h) return FSLBM_ERR_OOM;
@@ -135,8 +138,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   h->nparts = h->bulk_blocks * 4 + h->iface_blocks;  // one partial per bulk warp, per interface block
   if (h->nparts < 4096) h->nparts = 4096;
   bool ok = dalloc(h, &h->flags, N4) && dalloc(h, &h->mark, N4) &&
-            dalloc(h, (char**)&h->fA, 19 * Nn * store_bytes(h->prec)) &&
-            dalloc(h, (char**)&h->fB, 19 * Nn * store_bytes(h->prec)) && dalloc(h, &h->m, Nn * 8) &&
+            dalloc(h, (char**)&h->fA, 19 * Nn * store_bytes(h->prec) + 16) &&
+            dalloc(h, (char**)&h->fB, 19 * Nn * store_bytes(h->prec) + 16) && dalloc(h, &h->m, Nn * 8) &&
             dalloc(h, (char**)&h->phiA, Nn * real_bytes(h->prec)) &&
             dalloc(h, (char**)&h->phiB, Nn * real_bytes(h->prec)) && dalloc(h, &h->cnt, 16 * sizeof(int)) &&
             dalloc(h, &h->share, Nn * 8) && dalloc(h, &h->partials, (size_t)h->nparts * 8) &&
@@ -161,6 +164,19 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   cudaMemsetAsync(h->lost, 0, 8, h->st);
   cudaMemsetAsync(h->err, 0, 8, h->st);
   cudaMemsetAsync(h->step_mass, 0, 8, h->st);
+  // loads of the bulk kernel: staged ones only for FP32/FP16 (FP64 is bound by its arithmetic)
+  h->bulk_mode = BULK_PLAIN;
+  if (h->prec != FSLBM_F64 && q.bulk_loads == FSLBM_LOADS_ASYNC) h->bulk_mode = BULK_ASYNC;
+  if (h->prec != FSLBM_F64 && q.bulk_loads == FSLBM_LOADS_TMA && tma_shape_ok(p, h->prec)) {
+    // tensor maps of both population buffers
+    h->tmap = (CUtensorMap*)aligned_alloc(64, 2 * sizeof(CUtensorMap));
+    if (h->tmap && tma_encode(p, h->prec, h->fA, &h->tmap[0]) && tma_encode(p, h->prec, h->fB, &h->tmap[1])) {
+      h->bulk_mode = BULK_TMA;
+    } else {
+      free(h->tmap);
+      h->tmap = nullptr;
+    }
+  }
   if (cudaStreamSynchronize(h->st) != cudaSuccess) {
     free_all(h);
     free(h);
@@ -184,6 +200,11 @@ extern "C" int fslbm_create(const int dims[3], double tau, const double g[3], do
   p.sigma = sigma;
   p.rule = rule;
   return fslbm_create_ex(&p, out);
+}
+
+extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
+  if (!h) return FSLBM_ERR_ARG;
+  return h->bulk_mode == BULK_TMA ? FSLBM_LOADS_TMA : (h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC : FSLBM_LOADS_PLAIN);
 }
 
 extern "C" void fslbm_destroy(fslbm_t* h) {
@@ -222,6 +243,7 @@ static int read_err(fslbm* h) {
   if (e & ERRB_STATE) return fail(h, FSLBM_ERR_STATE, "invariant violated: a liquid cell touches gas, or a bad flag");
   if (e & ERRB_UNSTABLE) return fail(h, FSLBM_ERR_UNSTABLE, "non-finite or non-positive density");
   if (e & ERRB_OVERFLOW) return fail(h, FSLBM_ERR_OVERFLOW, "conversion list overflow");
+  if (e & ERRB_TMA) return fail(h, FSLBM_ERR_TIMEOUT, "staged loads of the bulk kernel failed (bounded wait expired)");
   return FSLBM_OK;
 }
 
@@ -351,7 +373,7 @@ static int step_t(fslbm* h) {
   if (cudaMemsetAsync(h->cnt + 9, 0, sizeof(int), h->st) != cudaSuccess) return 1;
   if (mark_event(h, 0)) return 1;
   if (launch_step_kernels<P>(h->par, v, h->st, h->bulk_blocks, h->iface_blocks, h->seglist, h->cnt + 9,
-                             h->timing ? h : nullptr))
+                             h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr))
     return 1;
   if (mark_event(h, 2)) return 1;
   if (launch_reduce(h->partials, (long long)h->bulk_blocks * 4 + h->iface_blocks, h->red, h->red_blocks, h->lost,

@@ -9,7 +9,8 @@
 //            atomic byte-OR); an E cell next to F leaves E
 //   newg     NEWG cells get f = f^eq(mean rho, mean u) over their liquid /
 //            interface neighbours (q order), collided, m = 0
-//   empty    liquid neighbours of the remaining E become interface with m = rho
+//   empty    liquid neighbours of the remaining E become interface (NEWL)
+//   newl     NEWL cells get m = rho
 //   share    excess (F: m - rho, E: m) / number of receivers (interface after
 //            the steps above, not converting); no receiver -> lost ledger
 //   recv     each receiver gathers the shares of its converting neighbours in q
@@ -58,49 +59,6 @@ __device__ __forceinline__ typename Form<P>::R rho_out(const Par& p, const View<
   return r;
 }
 
-// A gas cell next to a filled cell becomes interface with f = f^eq(mean rho,
-// mean u) over its liquid/interface neighbours (kinds of step t, q order),
-// collided, m = 0, phi = 0.  Its neighbours' populations are final for the
-// step, and new cells are never read as neighbours (their kind is still gas).
-template <int P>
-__device__ void init_new_cell(const Par& p, const View<P>& v, long long j) {
-  using R = typename Form<P>::R;
-  const size_t N = (size_t)p.N;
-  int x, y, z;
-  coords(p, j, x, y, z);
-  R rs = R(0), us0 = R(0), us1 = R(0), us2 = R(0);
-  int c = 0;
-#pragma unroll 1
-  for (int q = 1; q < 19; ++q) {
-    long long y2 = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-    if (y2 < 0) continue;
-    uint8_t ky = v.flags[y2] & KIND;
-    if (!is_fluid(ky)) continue;
-    R g[19];
-#pragma unroll
-    for (int r = 0; r < 19; ++r) g[r] = ldq<P>(v.fout, (size_t)r * N + (size_t)y2, r);
-    R rr, ux, uy, uz;
-    moments_post<R>(p, g, rr, ux, uy, uz);
-    rs += rr; us0 += ux; us1 += uy; us2 += uz;
-    ++c;
-  }
-  R rbar = rs / R(c), u0 = us0 / R(c), u1 = us1 / R(c), u2 = us2 / R(c);
-  R r0 = p.compressible ? rbar : R(1);
-  R usq = u0 * u0 + u1 * u1 + u2 * u2;
-  R f[19];
-  f[0] = eplus<R, 0>(p, rbar, r0, u0, u1, u2, usq);
-#define FSL_EQ(q) f[q] = eplus<R, q>(p, rbar, r0, u0, u1, u2, usq) + eminus<R, q>(r0, u0, u1, u2);
-  FSL_EQ(1) FSL_EQ(2) FSL_EQ(3) FSL_EQ(4) FSL_EQ(5) FSL_EQ(6) FSL_EQ(7) FSL_EQ(8) FSL_EQ(9)
-  FSL_EQ(10) FSL_EQ(11) FSL_EQ(12) FSL_EQ(13) FSL_EQ(14) FSL_EQ(15) FSL_EQ(16) FSL_EQ(17) FSL_EQ(18)
-#undef FSL_EQ
-  R rho, ux, uy, uz;
-  collide<R>(p, f, rho, ux, uy, uz);
-#pragma unroll
-  for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)j, q, f[q]);
-  v.m[j] = 0.0;
-  v.phout[j] = R(0);
-}
-
 template <int P>
 __global__ void k_fill(Par p, View<P> v) {
   int nf = min(load_count(&v.cnt[1]), v.cap);
@@ -124,11 +82,77 @@ __global__ void k_fill(Par p, View<P> v) {
   }
 }
 
+// one warp per new cell: lane l (1..18) reads neighbour l's populations; the
+// means are summed in neighbour order; lane q builds and collides population q
 template <int P>
-__global__ void k_newg(Par p, View<P> v) {
-  int nn = min(load_count(&v.cnt[3]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x)
-    init_new_cell<P>(p, v, v.nglist[k]);
+__global__ void __launch_bounds__(256) k_newg(Par p, View<P> v) {
+  using R = typename Form<P>::R;
+  const unsigned FULL = 0xffffffffu;
+  const size_t N = (size_t)p.N;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nn = min(load_count(&v.cnt[3]), v.cap);
+  const int q = lane < 19 ? lane : 0;
+  for (int k = gw; k < nn; k += nw) {
+    const long long j = v.nglist[k];
+    int x, y, z;
+    coords(p, j, x, y, z);
+    bool use = false;
+    R rr = R(0), ux = R(0), uy = R(0), uz = R(0);
+    if (lane >= 1 && lane < 19) {
+      long long y2 = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      use = y2 >= 0 && is_fluid(v.flags[y2] & KIND);
+      if (use) {
+        R g[19];
+#pragma unroll
+        for (int r = 0; r < 19; ++r) g[r] = ldq<P>(v.fout, (size_t)r * N + (size_t)y2, r);
+        moments_post<R>(p, g, rr, ux, uy, uz);
+      }
+    }
+    R rs = R(0), s0 = R(0), s1 = R(0), s2 = R(0);
+    int c = 0;
+#pragma unroll
+    for (int l = 1; l < 19; ++l) {
+      const bool ul = __shfl_sync(FULL, use, l);
+      const R a = __shfl_sync(FULL, rr, l), b0 = __shfl_sync(FULL, ux, l);
+      const R b1 = __shfl_sync(FULL, uy, l), b2 = __shfl_sync(FULL, uz, l);
+      if (ul) { rs += a; s0 += b0; s1 += b1; s2 += b2; ++c; }
+    }
+    const R rbar = rs / R(c), u0 = s0 / R(c), u1 = s1 / R(c), u2 = s2 / R(c);
+    const R r0 = p.compressible ? rbar : R(1);
+    const R usq = u0 * u0 + u1 * u1 + u2 * u2;
+    const R wq_ = q == 0 ? R(1) / R(3) : (q <= 6 ? R(1) / R(18) : R(1) / R(36));
+    // f^eq(rbar, ubar) with u^eq = ubar
+    const R f = eplus_q<R>(p, q, rbar, r0, u0, u1, u2, usq) +
+                R(3) * wq_ * r0 * (R(cx(q)) * u0 + R(cy(q)) * u1 + R(cz(q)) * u2);
+    // collision (Eq. lbe2) of the new cell, lane q -> population q
+    const R f19 = lane < 19 ? f : R(0);
+    R rho = f19, jx = R(cx(q)) * f19, jy = R(cy(q)) * f19, jz = R(cz(q)) * f19;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rho += __shfl_xor_sync(FULL, rho, o);
+      jx += __shfl_xor_sync(FULL, jx, o);
+      jy += __shfl_xor_sync(FULL, jy, o);
+      jz += __shfl_xor_sync(FULL, jz, o);
+    }
+    const R rc = p.compressible ? rho : R(1);
+    const R Ux = jx / rc, Uy = jy / rc, Uz = jz / rc;
+    const R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
+    const R vx_ = Ux + R(0.5) * gx, vy_ = Uy + R(0.5) * gy, vz_ = Uz + R(0.5) * gz;
+    const R ilm = R(1) / R(p.lam_m);
+    const R ex = Ux - gx * ilm, ey = Uy - gy * ilm, ez = Uz - gz * ilm;
+    const R usq2 = vx_ * vx_ + vy_ * vy_ + vz_ * vz_;
+    const R fb = __shfl_sync(FULL, f, inv(q));
+    const R ep = eplus_q<R>(p, q, rho, rc, vx_, vy_, vz_, usq2);
+    const R em = R(3) * wq_ * rc * (R(cx(q)) * ex + R(cy(q)) * ey + R(cz(q)) * ez);
+    const R out = f + R(p.lam_p) * (R(0.5) * (f + fb) - ep) + R(p.lam_m) * (R(0.5) * (f - fb) - em);
+    if (lane < 19) stq<P>(v.fout, (size_t)q * N + (size_t)j, q, out);
+    if (lane == 0) {
+      v.m[j] = 0.0;
+      v.phout[j] = R(0);
+    }
+  }
 }
 
 template <int P>
@@ -146,16 +170,26 @@ __global__ void k_empty(Par p, View<P> v) {
       if (j < 0) continue;
       if ((v.flags[j] & KIND) != LIQ) continue;
       uint8_t old = or_u8(v.mark, j, MK_NEWL);
-      if (!(old & MK_NEWL)) {
-        R r = rho_out<P>(p, v, j);
-        double mm = (double)r;
-        v.m[j] = mm;
-        v.phout[j] = (R)(mm / (double)r);
+      if (!(old & MK_NEWL)) {  // the first claimant lists it; k_newl sets m = rho
         int kk = atomicAdd(&v.cnt[4], 1);
         if (kk < v.cap) v.nllist[kk] = (int)j;
         else atomicOr(v.err, ERRB_OVERFLOW);
       }
     }
+  }
+}
+
+// liquid cells turned interface next to an emptied cell: m = rho, phi = m/rho
+template <int P>
+__global__ void k_newl(Par p, View<P> v) {
+  using R = typename Form<P>::R;
+  int nl = min(load_count(&v.cnt[4]), v.cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x) {
+    long long j = v.nllist[k];
+    R r = rho_out<P>(p, v, j);
+    double mm = (double)r;
+    v.m[j] = mm;
+    v.phout[j] = (R)(mm / (double)r);
   }
 }
 
@@ -280,8 +314,9 @@ __global__ void k_final(Par p, View<P> v) {
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks) {
   k_fill<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_newg<P><<<list_blocks, 128, 0, st>>>(p, v);
+  k_newg<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_empty<P><<<list_blocks, 256, 0, st>>>(p, v);
+  k_newl<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_share<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_recv<P><<<list_blocks, 256, 0, st>>>(p, v);
   k_final<P><<<list_blocks, 256, 0, st>>>(p, v);

@@ -41,7 +41,7 @@ __host__ __device__ constexpr R wq(int q) {
 
 enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16 };
 enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16 };
-enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4 };
+enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8 };
 
 // ---------------------------------------------------------------------------
 // Precision forms
@@ -427,18 +427,32 @@ __device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const 
   // heights over 3x3 columns of 7 cells along a; closed when every column
   // has liquid at its liquid end, gas at its gas end and no wall
   bool closed = true;
+  // strides of the dominant axis a, of b and of the third axis (interior cells)
+  const int c3 = 3 - a - b;
+  const long long sa = a == 0 ? 1 : (a == 1 ? sy : sz);
+  const long long sb = b == 0 ? 1 : (b == 1 ? sy : sz);
+  const long long sc = c3 == 0 ? 1 : (c3 == 1 ? sy : sz);
 #pragma unroll
   for (int ib = -1; ib <= 1; ++ib)
 #pragma unroll
     for (int ic = -1; ic <= 1; ++ic) {
       R sum = R(0);
+      const long long col = i0 + ib * sb + ic * sc;
 #pragma unroll
       for (int k = -3; k <= 3; ++k) {
-        const int o0 = (a == 0) ? k : ((b == 0) ? ib : ic);
-        const int o1 = (a == 1) ? k : ((b == 1) ? ib : ic);
-        const int o2 = (a == 2) ? k : ((b == 2) ? ib : ic);
         uint8_t kj;
-        R pj = sample(o0, o1, o2, kj);
+        R pj;
+        if (interior) {
+          const long long j = col + k * sa;
+          const R raw = phin[j];
+          kj = kind_at(flags, j);
+          pj = kj == LIQ ? R(1) : ((kj == IFC || (kj == GAS && p.freeze)) ? raw : R(0));
+        } else {
+          const int o0 = (a == 0) ? k : ((b == 0) ? ib : ic);
+          const int o1 = (a == 1) ? k : ((b == 1) ? ib : ic);
+          const int o2 = (a == 2) ? k : ((b == 2) ? ib : ic);
+          pj = sample(o0, o1, o2, kj);
+        }
         closed = closed && kj != WALL;
         if (k == -3) closed = closed && (s > 0 ? kj == LIQ : kj == GAS);
         if (k == 3) closed = closed && (s > 0 ? kj == GAS : kj == LIQ);

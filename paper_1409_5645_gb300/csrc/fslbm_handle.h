@@ -1,6 +1,7 @@
 // fslbm_handle.h -- the handle behind the opaque fslbm_t of the C interface
 // (shared by the host translation units of the library).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <vector>
 
@@ -47,6 +48,8 @@ struct fslbm {
   AdjointState* adj;  // checkpoints and buffers of a differentiation, or NULL
   double* f0;         // FP64 pre-collision initial populations (keep_f0), or NULL
   int f0_valid;       // f0 holds the populations of the current initial state
+  int bulk_mode;      // fsl::BulkMode of the bulk kernel
+  CUtensorMap* tmap;  // [2] tensor maps of fA and fB for the TMA bulk kernel (64-byte aligned), or NULL
 };
 
 

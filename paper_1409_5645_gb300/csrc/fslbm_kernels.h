@@ -1,5 +1,6 @@
 // fslbm_kernels.h -- launchers shared by the translation units of the library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -7,9 +8,25 @@
 
 namespace fsl {
 
+// how the bulk kernel reaches its pulled values (fslbm_bulk_loads)
+enum BulkMode { BULK_PLAIN = 0, BULK_TMA = 1, BULK_ASYNC = 2 };
+
+// bulk_mode: BulkMode (FP32/FP16 only for the staged modes); tmap: tensor map
+// of v.fin for BULK_TMA
 template <int P>
 int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
-                        int* seglist, int* segcount, void* timing_handle);
+                        int* seglist, int* segcount, void* timing_handle, int bulk_mode, const CUtensorMap* tmap);
+
+// staged bulk kernels (fslbm_staged.cu): TMA shape test, tensor map of a
+// population buffer, launchers
+bool tma_shape_ok(const Par& p, int prec);
+bool tma_encode(const Par& p, int prec, const void* base, CUtensorMap* map);
+template <int P>
+int launch_bulk_tma(const Par& p, const View<P>& v, const CUtensorMap* map, cudaStream_t st, int bulk_blocks,
+                    const int* seglist, const int* segcount);
+template <int P>
+int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
+                      const int* segcount);
 
 // records the handle's between-kernel timing event (host side, fslbm_api.cu)
 int fslbm_mark_between(void* handle);

@@ -16,27 +16,9 @@
 // Both read f~(t) from fin and write f~(t+1) to fout; they touch disjoint cells.
 #include "fslbm_dev.cuh"
 #include "fslbm_kernels.h"
+#include "fslbm_pull.cuh"
 
 namespace fsl {
-
-// ---------------------------------------------------------------------------
-// warp-aggregated append of `pred` lanes' values to list[*count ...]
-// (all 32 lanes of the warp must call it)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void warp_append(bool pred, int value, int* list, int* count, int cap, int* err) {
-  unsigned bal = __ballot_sync(0xffffffffu, pred);
-  if (!bal) return;
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(bal) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(bal));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) {
-    int k = base + __popc(bal & ((1u << lane) - 1u));
-    if (k < cap) list[k] = value;
-    else atomicOr(err, ERRB_OVERFLOW);
-  }
-}
 
 // deterministic block sum of a double (blockDim.x == 128)
 __device__ __forceinline__ double block_sum128(double v) {
@@ -50,54 +32,6 @@ __device__ __forceinline__ double block_sum128(double v) {
   if (threadIdx.x == 0) s = (red[0] + red[1]) + (red[2] + red[3]);
   __syncthreads();
   return s;
-}
-
-// ---------------------------------------------------------------------------
-// General pull for a cell next to a wall, a face or gas.  Fills f[q] from
-// fluid sources and returns masks of wall and gas sources.
-// ---------------------------------------------------------------------------
-template <int P>
-__device__ __forceinline__ void pull_general(const Par& p, const View<P>& v, int x, int y, int z,
-                                             typename Form<P>::R (&f)[19], unsigned& wallm, unsigned& gasm) {
-  const size_t N = (size_t)p.N;
-  wallm = 0u;
-  gasm = 0u;
-#pragma unroll
-  for (int q = 1; q < 19; ++q) {
-    long long s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
-    uint8_t ks = kind_at(v.flags, s);
-    if (is_fluid(ks)) f[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)s, q);
-    else if (ks == WALL) { wallm |= 1u << q; f[q] = 0; }
-    else { gasm |= 1u << q; f[q] = 0; }
-  }
-}
-
-// Wall closure for the links in wallm (needs the cell's own f~ and the
-// pulled values): half-way bounce-back f_q = f~_p(x), p = qbar, or CLI with
-// kappa = (1 - 2 dw)/(1 + 2 dw): f_q = f~_p(x) + kappa (f~_p(x - c_p) - f~_q(x)),
-// where f~_p(x - c_p) is the value pulled along p (used only if that source is
-// fluid).
-template <int P>
-__device__ __forceinline__ void wall_links(const Par& p, const View<P>& v, long long i, unsigned wallm,
-                                           unsigned gasm, const typename Form<P>::R (&own)[19],
-                                           typename Form<P>::R (&f)[19]) {
-  using R = typename Form<P>::R;
-  const size_t N = (size_t)p.N;
-#pragma unroll
-  for (int q = 1; q < 19; ++q) {
-    if (!(wallm & (1u << q))) continue;
-    const int pq = inv(q);
-    R val = own[pq];
-    if (p.has_wd) {
-      R dw = (R)v.wd[(size_t)pq * N + (size_t)i];
-      bool up_fluid = !((wallm | gasm) & (1u << pq));
-      if (dw >= R(0) && up_fluid) {
-        R kap = (R(1) - R(2) * dw) / (R(1) + R(2) * dw);
-        val = val + kap * (f[pq] - own[q]);
-      }
-    }
-    f[q] = val;
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -232,8 +166,9 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
       R rt, utx, uty, utz;
       moments_post<R>(p, own, rt, utx, uty, utz);
       f[0] = own[0];
-      unsigned wallm, gasm;
-      pull_general<P>(p, v, x, y, z, f, wallm, gasm);
+      unsigned wallm, gasm, liqm;
+      int srcs[19];
+      pull_general<P>(p, v, x, y, z, f, wallm, gasm, &liqm, srcs);
       const R phic = v.phin[i];
       // mass exchange (Sec. 2.3) with the pulled values, before any rebuild
       double dm = 0.0;
@@ -241,16 +176,22 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
 #pragma unroll
         for (int q = 1; q < 19; ++q) {
           if ((wallm | gasm) & (1u << q)) continue;
-          long long s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
-          uint8_t ks = v.flags[s] & KIND;
-          R sw = (ks == LIQ) ? R(1) : R(0.5) * (phic + v.phin[s]);
+          R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + v.phin[srcs[q]]);
           dm += (double)(sw * (f[q] - own[inv(q)]));
         }
       }
       if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
       if (gasm) {
         Geo<R> G;
-        geometry<R>(p, v.flags, v.phin, x, y, z, phic, G);
+        // FSK without surface tension needs neither the plane nor the curvature
+        if (p.rule != 0 || p.sigma != 0.0) {
+          geometry<R>(p, v.flags, v.phin, x, y, z, phic, G);
+        } else {
+          G.ok = false;
+          G.d = R(0);
+          G.kap = R(0);
+          G.n[0] = G.n[1] = G.n[2] = R(0);
+        }
         const R* n = G.n;
         const R d = G.d, kap = G.kap;
         const bool ok = G.ok;
@@ -336,10 +277,21 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ in, l
 // ---------------------------------------------------------------------------
 template <int P>
 int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
-                        int* seglist, int* segcount, void* timing_handle) {
+                        int* seglist, int* segcount, void* timing_handle, int bulk_mode,
+                        const CUtensorMap* tmap) {
   const long long nseg = (long long)((p.nx + 31) / 32) * p.ny * p.nz;
   k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(p, v.flags, seglist, segcount);
-  k_bulk<P><<<bulk_blocks, 128, 0, st>>>(p, v, seglist, segcount);
+  bool launched = false;
+  if constexpr (P != P64) {
+    if (bulk_mode == BULK_TMA && tmap) {
+      if (launch_bulk_tma<P>(p, v, tmap, st, bulk_blocks, seglist, segcount)) return 1;
+      launched = true;
+    } else if (bulk_mode == BULK_ASYNC) {
+      if (launch_bulk_async<P>(p, v, st, bulk_blocks, seglist, segcount)) return 1;
+      launched = true;
+    }
+  }
+  if (!launched) k_bulk<P><<<bulk_blocks, 128, 0, st>>>(p, v, seglist, segcount);
   if (timing_handle && fslbm_mark_between(timing_handle)) return 1;
   k_iface<P><<<iface_blocks, 128, 0, st>>>(p, v, bulk_blocks * 4);  // after the bulk warps' partials
   return (int)cudaGetLastError();
@@ -356,8 +308,11 @@ int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, co
   return (int)cudaGetLastError();
 }
 
-template int launch_step_kernels<P64>(const Par&, const View<P64>&, cudaStream_t, int, int, int*, int*, void*);
-template int launch_step_kernels<P32>(const Par&, const View<P32>&, cudaStream_t, int, int, int*, int*, void*);
-template int launch_step_kernels<P16>(const Par&, const View<P16>&, cudaStream_t, int, int, int*, int*, void*);
+template int launch_step_kernels<P64>(const Par&, const View<P64>&, cudaStream_t, int, int, int*, int*, void*,
+                                      int, const CUtensorMap*);
+template int launch_step_kernels<P32>(const Par&, const View<P32>&, cudaStream_t, int, int, int*, int*, void*,
+                                      int, const CUtensorMap*);
+template int launch_step_kernels<P16>(const Par&, const View<P16>&, cudaStream_t, int, int, int*, int*, void*,
+                                      int, const CUtensorMap*);
 
 }  // namespace fsl

@@ -22,6 +22,7 @@ F64, F32, F16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 FIELD_FLAGS, FIELD_F, FIELD_MASS, FIELD_PHI, FIELD_RHO, FIELD_U = 1, 2, 4, 8, 16, 32
 PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}
+LOADS = {"plain": 0, "async": 1, "tma": 2}  # fslbm_loads
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE", -5: "ERR_UNSTABLE",
           -6: "ERR_OVERFLOW", -7: "ERR_TIMEOUT", -8: "ERR_TOO_LARGE"}
 
@@ -37,7 +38,7 @@ class Params(C.Structure):
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int), ("compressible", C.c_int),
                 ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
                 ("freeze", C.c_int), ("cleanup", C.c_int), ("keep_f0", C.c_int), ("delta_min", C.c_double),
-                ("precision", C.c_int),
+                ("bulk_loads", C.c_int), ("precision", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -75,6 +76,8 @@ def lib():
             L.fslbm_adjoint_stats.argtypes = [vp, dp, dp, C.POINTER(C.c_size_t)]
             L.fslbm_time.argtypes = [vp]
             L.fslbm_time.restype = C.c_longlong
+            L.fslbm_bulk_loads.argtypes = [vp]
+            L.fslbm_bulk_loads.restype = C.c_int
             L.fslbm_device_bytes.argtypes = [vp]
             L.fslbm_device_bytes.restype = C.c_size_t
             L.fslbm_last_error.argtypes = [vp]
@@ -143,6 +146,7 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.cleanup = int(params.get("cleanup", P.cleanup))
     P.keep_f0 = int(params.get("keep_f0", 0))
     P.delta_min = params.get("delta_min", P.delta_min)
+    P.bulk_loads = LOADS[params.get("bulk_loads", "plain")]
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream
     return P
@@ -284,6 +288,12 @@ class Lattice:
     @property
     def time(self) -> int:
         return int(self.L.fslbm_time(self.h))
+
+    @property
+    def bulk_loads(self) -> str:
+        """How the bulk kernel reaches its pulled values: 'async' (cp.async into
+        shared memory), 'plain' (global loads) or 'tma' (tensor-map row copies)."""
+        return {v: k for k, v in LOADS.items()}[self.L.fslbm_bulk_loads(self.h)]
 
     @property
     def device_bytes(self) -> int:

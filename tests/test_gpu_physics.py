@@ -1,0 +1,137 @@
+"""Workloads of the paper's validation on the CUDA path: convergence orders on
+the inclined film (Sec. 4.3), the standing capillary-gravity wave against its
+dispersion relation, and the reduced-precision forms against FP64."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1409_5645_gb300 import cases, fslbm
+
+pytestmark = pytest.mark.gpu
+
+
+def _inclined_error(h, rule, precision, tol, max_checks=4000):
+    c = cases.inclined_film(h=h, rule=rule)
+    g = fslbm.Lattice.from_case(c, precision=precision)
+    fl = c["flags"]
+    fluid = (fl == 1) | (fl == 2)
+    n = np.clip(c["ncoord"], 0, None)
+    H, nu, gm = c["H"], c["nu"], c["gmag"]
+    ex = (gm / (2 * nu) * (2 * H * n - n * n))[:, None] * c["t_hat"][None, :]
+    prev = g.get(fslbm.FIELD_U)["u"][fluid]
+    for _ in range(max_checks):
+        g.step(500)
+        u = g.get(fslbm.FIELD_U)["u"][fluid]
+        ch = np.sqrt(((u - prev) ** 2).sum() / (u ** 2).sum())
+        prev = u
+        if ch < tol:
+            break
+    e = u - ex[fluid]
+    return np.sqrt((e ** 2).sum() / (ex[fluid] ** 2).sum())
+
+
+def test_inclined_film_orders_fp64():
+    """Slope-1/2 film, CLI wall, frozen interface, fixed Reynolds number:
+    FSL second order, FSK first order (Sec. 4.3), h = 8 ... 64."""
+    hs = [8, 16, 32, 64]
+    e = {r: np.array([_inclined_error(h, r, "f64", 1e-11) for h in hs]) for r in (0, 1)}
+    o = {r: np.log2(e[r][:-1] / e[r][1:]) for r in (0, 1)}
+    print("FSK errors", e[0], "orders", o[0])
+    print("FSL errors", e[1], "orders", o[1])
+    assert np.all(o[1] > 1.8)
+    assert np.all((o[0] > 0.8) & (o[0] < 1.3))
+
+
+def test_inclined_film_fsl_order_fp32():
+    """FP32 keeps the second order of FSL (relative change per 500 steps below
+    1e-5, at most 30 diffusion times H^2/nu at h = 32)."""
+    hs = [8, 16, 32]
+    e = np.array([_inclined_error(h, 1, "f32", 1e-5, max_checks=500) for h in hs])
+    o = np.log2(e[:-1] / e[1:])
+    print("FSL FP32 errors", e, "orders", o)
+    assert np.all(o > 1.7)
+
+
+def _wave_frequency(precision, sigma, steps=9000, every=50):
+    import torch
+    n = 128
+    # periodic in x and y: the (2, 2) mode without side-wall boundary layers
+    c = cases.standing_wave(n=n, sigma=sigma, periodic=(1, 1, 0))
+    dev = torch.device("cuda:0")
+    g = fslbm.Lattice(c["dims"], c["params"], precision=precision)
+    t = {k: torch.from_numpy(c[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
+    g.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
+    M0, _ = g.total_mass()
+    ts, hs = [], []
+    for s in range(0, steps + 1, every):
+        if s:
+            g.step(every)
+        ph = g.get(fslbm.FIELD_PHI, device=dev)["phi"].view(n, n, n)
+        # liquid height of the crest column (x, y) = (0, 0) and of the trough column
+        hs.append(float(ph[:, 0, 0].sum() - ph[:, 0, n // 2].sum()))
+        ts.append(s)
+    M1, _ = g.total_mass()
+    ts, hs = np.array(ts, float), np.array(hs)
+    from scipy.optimize import curve_fit
+    k = 2 * math.pi * math.sqrt(2) / n
+    nu = (c["params"]["tau"] - 0.5) / 3
+    gm = -c["params"]["g"][2]
+    w0 = math.sqrt((gm * k + sigma * k ** 3) * math.tanh(k * c["depth"]))
+    f = lambda t_, A, gam, w, ph0, b: A * np.exp(-gam * t_) * np.cos(w * t_ + ph0) + b
+    popt, _ = curve_fit(f, ts, hs, p0=[hs[0], 2 * nu * k * k, w0, 0.0, 0.0], maxfev=20000)
+    return abs(popt[2]), w0, popt[1], 2 * nu * k * k, (M1 - M0) / M0, hs
+
+
+def test_standing_wave_dispersion_and_surface_tension():
+    """128^3 standing wave, periodic in x and y (depth 64, amplitude 2): the
+    oscillation frequency follows w^2 = (g k + sigma k^3) tanh(k h) (damping
+    2 nu k^2), with and without surface tension; the sigma k^3 shift has the
+    right sign and size."""
+    w_a, th_a, gam_a, gth, drift_a, _ = _wave_frequency("f64", 0.0)
+    w_b, th_b, gam_b, _, drift_b, _ = _wave_frequency("f64", 2e-3)
+    print(f"sigma=0: w {w_a:.4e} theory {th_a:.4e}; sigma=2e-3: w {w_b:.4e} theory {th_b:.4e}; "
+          f"damping {gam_a:.2e} vs {gth:.2e}")
+    assert w_a == pytest.approx(math.sqrt(th_a ** 2 - gth ** 2), rel=0.03)
+    assert w_b == pytest.approx(math.sqrt(th_b ** 2 - gth ** 2), rel=0.03)
+    assert (w_b / w_a) == pytest.approx(th_b / th_a, rel=0.03)
+    assert abs(drift_a) < 1e-11 and abs(drift_b) < 1e-11
+
+
+def test_standing_wave_reduced_precision_against_fp64():
+    """FP32 and FP16-storage forms of the standing wave: frequency, surface
+    signal and mass drift against FP64 (errors stated)."""
+    w64, _, _, _, d64, h64 = _wave_frequency("f64", 1e-4, steps=6000, every=100)
+    out = {}
+    for prec in ("f32", "f16"):
+        w, _, _, _, d, h = _wave_frequency(prec, 1e-4, steps=6000, every=100)
+        out[prec] = (abs(w - w64) / w64, np.abs(h - h64).max() / np.abs(h64).max(), d)
+        print(prec, "freq err %.2e  surface err %.2e  mass drift %.2e" % out[prec])
+    assert out["f32"][0] < 5e-3 and out["f32"][1] < 2e-2 and abs(out["f32"][2]) < 1e-3
+    assert out["f16"][0] < 2e-2 and out["f16"][1] < 1e-1 and abs(out["f16"][2]) < 1e-2
+
+
+def test_film_velocity_reduced_precision_against_fp64():
+    """Film 4x4x32 (depth 20) after 2000 steps: velocity L2 error of FP32 and
+    FP16 storage against FP64 on the liquid cells, and the mass drift of each
+    form (stated)."""
+    c = cases.film()
+    res, drift = {}, {}
+    both = np.ones(c.N, dtype=bool)
+    for prec in ("f64", "f32", "f16"):
+        g = fslbm.Lattice.from_case(c, precision=prec)
+        M0, _ = g.total_mass()
+        g.step(2000)
+        M1, _ = g.total_mass()
+        st = g.get(fslbm.FIELD_U | fslbm.FIELD_FLAGS)
+        res[prec] = st["u"][:, 0]
+        both &= st["flags"] == cases.LIQUID
+        drift[prec] = (M1 - M0) / M0
+    # over the cells liquid in all three runs (a drift-driven fill adds a layer)
+    ref = res["f64"][both]
+    e = {p: np.sqrt(((res[p][both] - ref) ** 2).sum() / (ref ** 2).sum()) for p in ("f32", "f16")}
+    print("film velocity L2 vs FP64: FP32 %.2e, FP16 storage %.2e; mass drift over 2000 steps: "
+          "FP64 %.1e, FP32 %.1e, FP16 %.1e" % (e["f32"], e["f16"], drift["f64"], drift["f32"], drift["f16"]))
+    assert abs(drift["f64"]) < 1e-12
+    assert e["f32"] < 1e-3 and abs(drift["f32"]) < 1e-4
+    assert e["f16"] < 5e-2 and abs(drift["f16"]) < 1e-3
