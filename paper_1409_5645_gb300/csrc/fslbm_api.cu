@@ -34,6 +34,18 @@ static int fail(fslbm* h, int code, const char* what, cudaError_t e = cudaSucces
     if (e_ != cudaSuccess) return fail(h, FSLBM_ERR_CUDA, what, e_); \
   } while (0)
 
+// magic numbers of fsl::fdiv for the divisor d >= 1 (d < 2^31)
+static FDiv make_fdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  FDiv f;
+  f.m = (unsigned)m;
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
 static size_t store_bytes(int prec) { return prec == FSLBM_F64 ? 8 : (prec == FSLBM_F32 ? 4 : 2); }
 static size_t real_bytes(int prec) { return prec == FSLBM_F64 ? 8 : 4; }
 
@@ -101,6 +113,10 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   strcpy(h->msg, k_ok);
   Par& p = h->par;
   p.nx = q.dims[0]; p.ny = q.dims[1]; p.nz = q.dims[2];
+  p.dnx = make_fdiv((unsigned)p.nx);
+  p.dny = make_fdiv((unsigned)p.ny);
+  p.dnxy = make_fdiv((unsigned)(p.nx * p.ny));
+  p.dnsx = make_fdiv((unsigned)((p.nx + 31) / 32));
   p.N = N;
   p.px = q.periodic[0] != 0; p.py = q.periodic[1] != 0; p.pz = q.periodic[2] != 0;
   p.zshift = q.zshift;
@@ -369,8 +385,7 @@ static int mark_event(fslbm* h, int k) {
 template <int P>
 static int step_t(fslbm* h) {
   View<P> v = make_view<P>(h);
-  if (cudaMemsetAsync(h->cnt, 0, 8 * sizeof(int), h->st) != cudaSuccess) return 1;
-  if (cudaMemsetAsync(h->cnt + 9, 0, sizeof(int), h->st) != cudaSuccess) return 1;
+  if (launch_reset(h->cnt, h->st)) return 1;
   if (mark_event(h, 0)) return 1;
   if (launch_step_kernels<P>(h->par, v, h->st, h->bulk_blocks, h->iface_blocks, h->seglist, h->cnt + 9,
                              h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr))

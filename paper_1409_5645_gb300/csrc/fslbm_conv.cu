@@ -59,26 +59,32 @@ __device__ __forceinline__ typename Form<P>::R rho_out(const Par& p, const View<
   return r;
 }
 
+// one warp per fill cell, lane q (1..18) takes link q
 template <int P>
-__global__ void k_fill(Par p, View<P> v) {
-  int nf = min(load_count(&v.cnt[1]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
-    long long i = v.flist[k];
+__global__ void __launch_bounds__(256) k_fill(Par p, View<P> v) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nf = min(load_count(&v.cnt[1]), v.cap);
+  const int q = (lane >= 1 && lane < 19) ? lane : 0;
+  for (int k = gw; k < nf; k += nw) {
+    const long long i = v.flist[k];
     int x, y, z;
     coords(p, i, x, y, z);
-#pragma unroll
-    for (int q = 1; q < 19; ++q) {
-      long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      uint8_t kj = j < 0 ? (uint8_t)WALL : (uint8_t)(v.flags[j] & KIND);
-      bool won = false;
+    bool won = false;
+    long long j = -1;
+    if (q) {
+      j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      const uint8_t kj = j < 0 ? (uint8_t)WALL : (uint8_t)(v.flags[j] & KIND);
       if (kj == GAS) {
-        uint8_t old = or_u8(v.mark, j, MK_NEWG);
+        const uint8_t old = or_u8(v.mark, j, MK_NEWG);
         won = !(old & MK_NEWG);  // the first claimant lists the new cell
       } else if (kj == IFC) {
         if (((volatile uint8_t*)v.mark)[j] & MK_EMPTY) clear_u8(v.mark, j, MK_EMPTY);
       }
-      push(won, v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
     }
+    push(won, v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
   }
 }
 
@@ -86,6 +92,7 @@ __global__ void k_fill(Par p, View<P> v) {
 // means are summed in neighbour order; lane q builds and collides population q
 template <int P>
 __global__ void __launch_bounds__(256) k_newg(Par p, View<P> v) {
+  pdl_begin();
   using R = typename Form<P>::R;
   const unsigned FULL = 0xffffffffu;
   const size_t N = (size_t)p.N;
@@ -155,33 +162,37 @@ __global__ void __launch_bounds__(256) k_newg(Par p, View<P> v) {
   }
 }
 
+// one warp per empty cell still marked, lane q (1..18) takes link q
 template <int P>
-__global__ void k_empty(Par p, View<P> v) {
-  using R = typename Form<P>::R;
-  int ne = min(load_count(&v.cnt[2]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
-    long long i = v.elist[k];
-    if (!(v.mark[i] & MK_EMPTY)) continue;
+__global__ void __launch_bounds__(256) k_empty(Par p, View<P> v) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int ne = min(load_count(&v.cnt[2]), v.cap);
+  const int q = (lane >= 1 && lane < 19) ? lane : 0;
+  for (int k = gw; k < ne; k += nw) {
+    const long long i = v.elist[k];
+    if (!(v.mark[i] & MK_EMPTY)) continue;  // warp-uniform
     int x, y, z;
     coords(p, i, x, y, z);
-#pragma unroll 1
-    for (int q = 1; q < 19; ++q) {
-      long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (j < 0) continue;
-      if ((v.flags[j] & KIND) != LIQ) continue;
-      uint8_t old = or_u8(v.mark, j, MK_NEWL);
-      if (!(old & MK_NEWL)) {  // the first claimant lists it; k_newl sets m = rho
-        int kk = atomicAdd(&v.cnt[4], 1);
-        if (kk < v.cap) v.nllist[kk] = (int)j;
-        else atomicOr(v.err, ERRB_OVERFLOW);
+    bool won = false;
+    long long j = -1;
+    if (q) {
+      j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      if (j >= 0 && (v.flags[j] & KIND) == LIQ) {
+        const uint8_t old = or_u8(v.mark, j, MK_NEWL);
+        won = !(old & MK_NEWL);  // the first claimant lists it; k_newl sets m = rho
       }
     }
+    push(won, v.nllist, &v.cnt[4], v.cap, (int)j, v.err);
   }
 }
 
 // liquid cells turned interface next to an emptied cell: m = rho, phi = m/rho
 template <int P>
 __global__ void k_newl(Par p, View<P> v) {
+  pdl_begin();
   using R = typename Form<P>::R;
   int nl = min(load_count(&v.cnt[4]), v.cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x) {
@@ -193,74 +204,99 @@ __global__ void k_newl(Par p, View<P> v) {
   }
 }
 
+// one warp per fill / empty cell: lane q (1..18) tests neighbour q as a
+// receiver; lane 0 computes the share (rho summed in q order, as a thread would)
 template <int P>
-__global__ void k_share(Par p, View<P> v) {
-  using R = typename Form<P>::R;
-  int nf = min(load_count(&v.cnt[1]), v.cap), ne = min(load_count(&v.cnt[2]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf + ne; k += gridDim.x * blockDim.x) {
-    bool isF = k < nf;
-    long long i = isF ? v.flist[k] : v.elist[k - nf];
-    if (!isF && !(v.mark[i] & MK_EMPTY)) continue;
+__global__ void __launch_bounds__(256) k_share(Par p, View<P> v) {
+  pdl_begin();
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nf = min(load_count(&v.cnt[1]), v.cap), ne = min(load_count(&v.cnt[2]), v.cap);
+  const int q = (lane >= 1 && lane < 19) ? lane : 0;
+  for (int k = gw; k < nf + ne; k += nw) {
+    const bool isF = k < nf;
+    const long long i = isF ? v.flist[k] : v.elist[k - nf];
+    if (!isF && !(v.mark[i] & MK_EMPTY)) continue;  // warp-uniform
     int x, y, z;
     coords(p, i, x, y, z);
-    double rho = (double)rho_out<P>(p, v, i);
-    double ex = isF ? v.m[i] - rho : v.m[i];
-    int nr = 0;
-    unsigned rm = 0u;
-#pragma unroll
-    for (int q = 1; q < 19; ++q) {
-      long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (j < 0) continue;
-      uint8_t mk = ((volatile uint8_t*)v.mark)[j];
-      uint8_t kj = v.flags[j] & KIND;
-      bool recv = (mk & (MK_NEWG | MK_NEWL)) || (kj == IFC && !(mk & (MK_FILL | MK_EMPTY)));
-      if (recv) { ++nr; rm |= 1u << q; }
-    }
-    if (nr == 0) {
-      atomicAdd(v.lost, ex);
-      v.share[i] = 0.0;
-    } else {
-      v.share[i] = ex / (double)nr;
-    }
-    v.m[i] = isF ? rho : 0.0;
-#pragma unroll
-    for (int q = 1; q < 19; ++q) {
-      bool first = false;
-      long long j = 0;
-      if (rm & (1u << q)) {
-        j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-        uint8_t old = or_u8(v.mark, j, MK_RECV);
-        first = !(old & MK_RECV);
+    bool recv = false;
+    long long j = -1;
+    if (q) {
+      j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      if (j >= 0) {
+        const uint8_t mk = ((volatile uint8_t*)v.mark)[j];
+        const uint8_t kj = v.flags[j] & KIND;
+        recv = (mk & (MK_NEWG | MK_NEWL)) || (kj == IFC && !(mk & (MK_FILL | MK_EMPTY)));
       }
-      push(first, v.rlist, &v.cnt[5], v.cap, (int)j, v.err);
     }
+    const unsigned rm = __ballot_sync(FULL, recv);
+    if (lane == 0) {
+      const double rho = (double)rho_out<P>(p, v, i);
+      const double ex = isF ? v.m[i] - rho : v.m[i];
+      const int nr = __popc(rm);
+      if (nr == 0) {
+        atomicAdd(v.lost, ex);
+        v.share[i] = 0.0;
+      } else {
+        v.share[i] = ex / (double)nr;
+      }
+      v.m[i] = isF ? rho : 0.0;
+    }
+    bool first = false;
+    if (recv) {
+      const uint8_t old = or_u8(v.mark, j, MK_RECV);
+      first = !(old & MK_RECV);
+    }
+    push(first, v.rlist, &v.cnt[5], v.cap, (int)j, v.err);
   }
 }
 
+// one warp per receiver: lane q (1..18) fetches the share of neighbour q;
+// lane 0 adds them in q order (deterministic, as a thread would)
 template <int P>
-__global__ void k_recv(Par p, View<P> v) {
+__global__ void __launch_bounds__(256) k_recv(Par p, View<P> v) {
+  pdl_begin();
   using R = typename Form<P>::R;
-  int nr = min(load_count(&v.cnt[5]), v.cap);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
-    long long yj = v.rlist[k];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nr = min(load_count(&v.cnt[5]), v.cap);
+  const int q = (lane >= 1 && lane < 19) ? lane : 0;
+  for (int k = gw; k < nr; k += nw) {
+    const long long yj = v.rlist[k];
     int x, y, z;
     coords(p, yj, x, y, z);
+    bool has = false;
+    double sh = 0.0;
+    if (q) {
+      const long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      if (j >= 0 && (v.mark[j] & (MK_FILL | MK_EMPTY))) {
+        has = true;
+        sh = v.share[j];
+      }
+    }
+    const unsigned hm = __ballot_sync(FULL, has);
     double acc = 0.0;
 #pragma unroll
-    for (int q = 1; q < 19; ++q) {
-      long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (j < 0) continue;
-      if (v.mark[j] & (MK_FILL | MK_EMPTY)) acc += v.share[j];
+    for (int l = 1; l < 19; ++l) {
+      const double t = __shfl_sync(FULL, sh, l);
+      if (hm & (1u << l)) acc += t;
     }
-    double mm = v.m[yj] + acc;
-    v.m[yj] = mm;
-    R r = rho_out<P>(p, v, yj);
-    v.phout[yj] = (R)(mm / (double)r);
+    if (lane == 0) {
+      const double mm = v.m[yj] + acc;
+      v.m[yj] = mm;
+      const R r = rho_out<P>(p, v, yj);
+      v.phout[yj] = (R)(mm / (double)r);
+    }
   }
 }
 
 template <int P>
 __global__ void k_final(Par p, View<P> v) {
+  pdl_begin();
   using R = typename Form<P>::R;
   int nf = min(load_count(&v.cnt[1]), v.cap), ne = min(load_count(&v.cnt[2]), v.cap);
   int ng = min(load_count(&v.cnt[3]), v.cap), nl = min(load_count(&v.cnt[4]), v.cap);
@@ -313,14 +349,10 @@ __global__ void k_final(Par p, View<P> v) {
 
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks) {
-  k_fill<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_newg<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_empty<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_newl<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_share<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_recv<P><<<list_blocks, 256, 0, st>>>(p, v);
-  k_final<P><<<list_blocks, 256, 0, st>>>(p, v);
-  return (int)cudaGetLastError();
+  void (*ks[7])(Par, View<P>) = {k_fill<P>, k_newg<P>, k_empty<P>, k_newl<P>, k_share<P>, k_recv<P>, k_final<P>};
+  for (auto k : ks)
+    if (launch_k(k, list_blocks, 256, 0, st, p, v)) return 1;
+  return 0;
 }
 
 template int launch_conversions<P64>(const Par&, const View<P64>&, cudaStream_t, int);

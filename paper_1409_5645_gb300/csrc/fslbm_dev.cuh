@@ -76,8 +76,23 @@ __device__ __forceinline__ void stq(typename Form<P>::S* __restrict__ p, size_t 
 // ---------------------------------------------------------------------------
 // Parameters passed by value to every kernel
 // ---------------------------------------------------------------------------
+// Division of a 32-bit unsigned n by a fixed divisor d >= 1 with one high
+// multiply (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, Fig. 4.1): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), exact for all n < 2^32.
+struct FDiv {
+  unsigned m;
+  int s1, s2;
+};
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FDiv& d) {
+  const unsigned t = __umulhi(n, d.m);
+  return (t + ((n - t) >> d.s1)) >> d.s2;
+}
+
 struct Par {
   int nx, ny, nz;
+  FDiv dnx, dny, dnxy, dnsx;  // fast division by nx, ny, nx*ny and the segments per row
   long long N;
   int px, py, pz, zshift;
   double lam_p, lam_m;     // TRT rates
@@ -136,12 +151,24 @@ __device__ __forceinline__ long long nbr(const Par& p, int x, int y, int z, int 
   if ((unsigned)X >= (unsigned)p.nx || (unsigned)Y >= (unsigned)p.ny || (unsigned)Z >= (unsigned)p.nz) return -1;
   return (long long)X + (long long)p.nx * ((long long)Y + (long long)p.ny * Z);
 }
+// (x, y, z) of cell i (i < N < 2^31)
 __device__ __forceinline__ void coords(const Par& p, long long i, int& x, int& y, int& z) {
-  long long s = (long long)p.nx * p.ny;
-  z = (int)(i / s);
-  long long r = i - (long long)z * s;
-  y = (int)(r / p.nx);
-  x = (int)(r - (long long)y * p.nx);
+  const unsigned u = (unsigned)i;
+  const unsigned zz = fdiv(u, p.dnxy);
+  const unsigned r = u - zz * (unsigned)(p.nx * p.ny);
+  const unsigned yy = fdiv(r, p.dnx);
+  z = (int)zz;
+  y = (int)yy;
+  x = (int)(r - yy * (unsigned)p.nx);
+}
+// row (y + ny z), first x and (y, z) of 32-cell x segment sg
+__device__ __forceinline__ void seg_coords(const Par& p, int sg, int& row, int& x0, int& y, int& z) {
+  const unsigned r = fdiv((unsigned)sg, p.dnsx);
+  const unsigned zz = fdiv(r, p.dny);
+  row = (int)r;
+  x0 = (int)(((unsigned)sg - r * (unsigned)((p.nx + 31) >> 5)) << 5);
+  z = (int)zz;
+  y = (int)(r - zz * (unsigned)p.ny);
 }
 __device__ __forceinline__ uint8_t kind_at(const uint8_t* flags, long long j) {
   return j < 0 ? (uint8_t)WALL : (uint8_t)(flags[j] & KIND);
@@ -155,12 +182,10 @@ __device__ __forceinline__ bool is_fluid(uint8_t k) { return k == LIQ || k == IF
 // ---------------------------------------------------------------------------
 template <class R, int q>
 __device__ __forceinline__ R eplus(const Par& p, R rho, R r0, R ux, R uy, R uz, R usq) {
-  R e = wq<R>(q) * rho;
-  if (!p.linear_eq) {
-    R cu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
-    e += wq<R>(q) * R(1.5) * r0 * (R(3) * cu * cu - usq);
-  }
-  return e;
+  // branch-free in linear_eq: the non-linear part is scaled by 0 or 1
+  const R nl = p.linear_eq ? R(0) : R(1);
+  const R cu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
+  return wq<R>(q) * rho + (wq<R>(q) * R(1.5) * r0 * nl) * (R(3) * cu * cu - usq);
 }
 template <class R>
 __device__ __forceinline__ R eplus_q(const Par& p, int q, R rho, R r0, R ux, R uy, R uz, R usq) {
@@ -366,9 +391,9 @@ struct Geo {
   R H[9];        // column heights H[(ib+1)*3 + (ic+1)]
 };
 
-template <class R>
-__device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const R* __restrict__ phin,
-                         int x, int y, int z, R phic, Geo<R>& G) {
+template <class R, bool IN = false>
+__device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict__ flags,
+                                         const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
   R (&n)[3] = G.n;
   R& d = G.d;
   R& kap = G.kap;
@@ -378,15 +403,24 @@ __device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const 
   G.a = 2; G.b = 0; G.s = 1;
   // cells within 3 of the node are inside the lattice without a wrap: plain
   // offsets; otherwise the general neighbour rule
-  const bool interior = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
+  // (IN: the caller knows it)
+  const bool interior = IN || (x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3);
   const long long i0 = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
-  const long long sy = p.nx, sz = (long long)p.nx * p.ny;
   // fill level seen by the geometry; the phi load is issued whatever the kind
   // so that all loads of the stencil are independent
+  // interior cells index in 32 bits (N < 2^31)
+  const int i0i = (int)i0, syi = p.nx, szi = p.nx * p.ny;
   auto sample = [&](int dx, int dy, int dz, uint8_t& kj) -> R {
-    long long j = interior ? i0 + dx + sy * dy + sz * dz : nbr(p, x, y, z, dx, dy, dz);
-    R raw = j >= 0 ? phin[j] : R(0);
-    kj = kind_at(flags, j);
+    R raw;
+    if (interior) {
+      const unsigned j = (unsigned)(i0i + dx + syi * dy + szi * dz);
+      raw = phin[j];
+      kj = (uint8_t)(flags[j] & KIND);
+    } else {
+      const long long j = nbr(p, x, y, z, dx, dy, dz);
+      raw = j >= 0 ? phin[j] : R(0);
+      kj = kind_at(flags, j);
+    }
     if (kj == LIQ) return R(1);
     if (kj == IFC || (kj == GAS && p.freeze)) return raw;
     return R(0);
@@ -429,21 +463,21 @@ __device__ void geometry(const Par& p, const uint8_t* __restrict__ flags, const 
   bool closed = true;
   // strides of the dominant axis a, of b and of the third axis (interior cells)
   const int c3 = 3 - a - b;
-  const long long sa = a == 0 ? 1 : (a == 1 ? sy : sz);
-  const long long sb = b == 0 ? 1 : (b == 1 ? sy : sz);
-  const long long sc = c3 == 0 ? 1 : (c3 == 1 ? sy : sz);
+  const int sa = a == 0 ? 1 : (a == 1 ? syi : szi);
+  const int sb = b == 0 ? 1 : (b == 1 ? syi : szi);
+  const int sc = c3 == 0 ? 1 : (c3 == 1 ? syi : szi);
 #pragma unroll
   for (int ib = -1; ib <= 1; ++ib)
 #pragma unroll
     for (int ic = -1; ic <= 1; ++ic) {
       R sum = R(0);
-      const long long col = i0 + ib * sb + ic * sc;
+      const int col = i0i + ib * sb + ic * sc;
 #pragma unroll
       for (int k = -3; k <= 3; ++k) {
         uint8_t kj;
         R pj;
         if (interior) {
-          const long long j = col + k * sa;
+          const unsigned j = (unsigned)(col + k * sa);
           const R raw = phin[j];
           kj = kind_at(flags, j);
           pj = kj == LIQ ? R(1) : ((kj == IFC || (kj == GAS && p.freeze)) ? raw : R(0));

@@ -8,6 +8,37 @@
 
 namespace fsl {
 
+// Programmatic dependent launch.  Every kernel of the step starts with
+// pdl_begin(): wait until the previous kernel of the stream has completed and
+// its writes are visible (a no-op when launched without the attribute), then
+// allow the next kernel to be launched, so that its launch and block
+// scheduling overlap this kernel instead of following it.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch with the programmatic-stream-serialization attribute
+template <typename... KArgs, typename... Args>
+inline int launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                    Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// zero the per-step counters cnt[0..7] and cnt[9] (one small kernel, so that
+// the whole step is a chain of kernels)
+int launch_reset(int* cnt, cudaStream_t st);
+
 // how the bulk kernel reaches its pulled values (fslbm_bulk_loads)
 enum BulkMode { BULK_PLAIN = 0, BULK_TMA = 1, BULK_ASYNC = 2 };
 

@@ -29,7 +29,7 @@ __device__ __forceinline__ void warp_append(bool pred, int value, int* list, int
 // General pull for a cell next to a wall, a face or gas.  Fills f[q] from
 // fluid sources and returns masks of wall and gas sources.
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, bool IN = false>
 __device__ __forceinline__ void pull_general(const Par& p, const View<P>& v, int x, int y, int z,
                                              typename Form<P>::R (&f)[19], unsigned& wallm, unsigned& gasm,
                                              unsigned* liqm = nullptr, int* srcs = nullptr) {
@@ -38,12 +38,14 @@ __device__ __forceinline__ void pull_general(const Par& p, const View<P>& v, int
   gasm = 0u;
   unsigned lm = 0u;
   // away from the faces the sources are plain offsets
-  const bool in1 = x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1;
+  // (IN: the caller knows the cell is at least one cell away from every face)
+  const bool in1 = IN || (x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1);
   const long long i = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
   const long long sy = p.nx, sz = (long long)p.nx * p.ny;
 #pragma unroll
   for (int q = 1; q < 19; ++q) {
-    long long s = in1 ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
+    long long s = IN ? i - (cx(q) + sy * cy(q) + sz * cz(q))
+                     : (in1 ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, -cx(q), -cy(q), -cz(q)));
     uint8_t ks = kind_at(v.flags, s);
     if (srcs) srcs[q] = (int)s;
     if (is_fluid(ks)) {

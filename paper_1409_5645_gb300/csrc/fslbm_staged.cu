@@ -113,13 +113,13 @@ template <int P>
 __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, View<P> v, const __grid_constant__ CUtensorMap tmap,
                                                    const int* __restrict__ seglist,
                                                    const int* __restrict__ segcount) {
+  pdl_begin();
   using R = typename Form<P>::R;
   using G = TmaGeom<P>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[TMA_WARPS][TMA_STAGES];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbuf = smem + warp * (TMA_STAGES * G::STAGE);
-  const int nsx = (p.nx + 31) >> 5;
   const int nseg = *((volatile const int*)segcount);
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -140,9 +140,8 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
   // lane 0: start the copies of segment si into stage s
   auto issue = [&](int si, int s) {
     const int sg = seglist[si];
-    const int row = sg / nsx;
-    const int x0 = (sg - row * nsx) << 5;
-    const int y = row % p.ny, z = row / p.ny;
+    int row, x0, y, z;
+    seg_coords(p, sg, row, x0, y, z);
     uint64_t* bar = &bars[warp][s];
     mbar_expect_tx(bar, 19u * (unsigned)G::ROWB);
     unsigned char* dst = wbuf + s * G::STAGE;
@@ -174,9 +173,9 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     const unsigned char* buf = wbuf + stage * G::STAGE;
 
     const int sg = seglist[si];
-    const int row = sg / nsx;
-    const int x = ((sg - row * nsx) << 5) + lane;
-    const int y = row % p.ny, z = row / p.ny;
+    int row, x0s, y, z;
+    seg_coords(p, sg, row, x0s, y, z);
+    const int x = x0s + lane;
     const bool in = x < p.nx;
     const long long i = (long long)row * p.nx + x;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
@@ -253,6 +252,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <int P>
 __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const int* __restrict__ seglist,
                                                      const int* __restrict__ segcount) {
+  pdl_begin();
   using R = typename Form<P>::R;
   using S = typename Form<P>::S;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -260,7 +260,6 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
   // slot (stage, k) of this lane: k = 0..18 values, 19 the word holding its flag
   const unsigned base = smem_u32(smem) + (unsigned)(warp * AS_STAGES * 20 * 128 + lane * 4);
   const uint32_t* slots = reinterpret_cast<const uint32_t*>(smem) + warp * AS_STAGES * 20 * 32 + lane;
-  const int nsx = (p.nx + 31) >> 5;
   const int nseg = *((volatile const int*)segcount);
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -271,9 +270,9 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
   auto issue = [&](int si, int stg) {
     if (si < nseg) {
       const int sg = seglist[si];
-      const int row = sg / nsx;
-      const int x = ((sg - row * nsx) << 5) + lane;
-      const int y = row % p.ny, z = row / p.ny;
+      int row, x0s, y, z;
+      seg_coords(p, sg, row, x0s, y, z);
+      const int x = x0s + lane;
       const long long i = (long long)row * p.nx + x;
       const bool in = x < p.nx;
       const bool xm = x >= 1, xp = x < p.nx - 1, ym = y >= 1, yp = y < p.ny - 1, zm = z >= 1, zp = z < p.nz - 1;
@@ -309,9 +308,9 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
     cp_async_wait<AS_STAGES - 1>();  // this lane's copies of segment si have landed
     const uint32_t* sl = slots + stg * 20 * 32;
     const int sg = seglist[si];
-    const int row = sg / nsx;
-    const int x = ((sg - row * nsx) << 5) + lane;
-    const int y = row % p.ny, z = row / p.ny;
+    int row, x0s, y, z;
+    seg_coords(p, sg, row, x0s, y, z);
+    const int x = x0s + lane;
     const bool in = x < p.nx;
     const long long i = (long long)row * p.nx + x;
     const uint8_t fl = in ? (uint8_t)(sl[19 * 32] >> (8 * (int)(i & 3))) : (uint8_t)GAS;
@@ -426,8 +425,7 @@ int launch_bulk_tma(const Par& p, const View<P>& v, const CUtensorMap* map, cuda
       return 1;
     attr = true;
   }
-  k_bulk_tma<P><<<bulk_blocks, 128, TmaGeom<P>::SMEM, st>>>(p, v, *map, seglist, segcount);
-  return (int)cudaGetLastError();
+  return launch_k(k_bulk_tma<P>, bulk_blocks, 128, TmaGeom<P>::SMEM, st, p, v, *map, seglist, segcount);
 }
 
 template <int P>
@@ -441,8 +439,7 @@ int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_
       return 1;
     attr = true;
   }
-  k_bulk_async<P><<<bulk_blocks, 128, AS_SMEM, st>>>(p, v, seglist, segcount);
-  return (int)cudaGetLastError();
+  return launch_k(k_bulk_async<P>, bulk_blocks, 128, AS_SMEM, st, p, v, seglist, segcount);
 }
 
 template int launch_bulk_async<P32>(const Par&, const View<P32>&, cudaStream_t, int, const int*, const int*);

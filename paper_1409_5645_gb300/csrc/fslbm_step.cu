@@ -40,12 +40,13 @@ __device__ __forceinline__ double block_sum128(double v) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restrict__ flags, int* __restrict__ seglist,
                                                   int* __restrict__ count) {
+  pdl_begin();
   const int nsx = (p.nx + 31) >> 5;
   const long long nseg = (long long)nsx * p.ny * p.nz;
   const long long sgi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool act = false;
   if (sgi < nseg) {
-    const long long row = sgi / nsx;
+    const long long row = (long long)fdiv((unsigned)sgi, p.dnsx);
     const int x0 = (int)(sgi - row * nsx) << 5;
     const int len = min(32, p.nx - x0);
     const uint8_t* base = flags + row * p.nx + x0;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
 template <int P>
 __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P> v, const int* __restrict__ seglist,
                                               const int* __restrict__ segcount) {
+  pdl_begin();
   using R = typename Form<P>::R;
   const int nsx = (p.nx + 31) >> 5;
   const int nseg = *((volatile const int*)segcount);
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
   double msum = 0.0;
   for (int si = gw; si < nseg; si += nw) {
     const int sg = seglist[si];
+    // (plain division measured faster here than the multiply-shift form)
     const int row = sg / nsx;
     const int x = ((sg - row * nsx) << 5) + lane;
     const int y = row % p.ny, z = row / p.ny;
@@ -142,10 +145,103 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
 // ---------------------------------------------------------------------------
 // k_iface
 // ---------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int bulk_blocks) {
+// The work of one interface cell (pull, mass exchange, wall and gas-link
+// closures, collision, store, fill/empty marks); returns its mass m.  IN:
+// every cell within 3 of it lies inside the lattice, so all stencil offsets
+// are plain (the hot path, kept apart from the face and wrap logic).
+template <int P, bool IN>
+__device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, long long i, int x, int y, int z,
+                                             bool& fill, bool& empty) {
   using R = typename Form<P>::R;
   const size_t N = (size_t)p.N;
+  R own[19], f[19];
+#pragma unroll
+  for (int q = 0; q < 19; ++q) own[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)i, q);
+  R rt, utx, uty, utz;
+  moments_post<R>(p, own, rt, utx, uty, utz);
+  f[0] = own[0];
+  unsigned wallm, gasm, liqm;
+  int srcs[19];
+  pull_general<P, IN>(p, v, x, y, z, f, wallm, gasm, &liqm, srcs);
+  const R phic = v.phin[i];
+  // mass exchange (Sec. 2.3) with the pulled values, before any rebuild
+  double dm = 0.0;
+  if (!p.freeze) {
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      if ((wallm | gasm) & (1u << q)) continue;
+      R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + v.phin[srcs[q]]);
+      dm += (double)(sw * (f[q] - own[inv(q)]));
+    }
+  }
+  if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
+  if (gasm) {
+    Geo<R> G;
+    // FSK without surface tension needs neither the plane nor the curvature
+    if (p.rule != 0 || p.sigma != 0.0) {
+      geometry<R, IN>(p, v.flags, v.phin, x, y, z, phic, G);
+    } else {
+      G.ok = false;
+      G.d = R(0);
+      G.kap = R(0);
+      G.n[0] = G.n[1] = G.n[2] = R(0);
+    }
+    const R* n = G.n;
+    const R d = G.d, kap = G.kap;
+    const bool ok = G.ok;
+    R rb = R(p.rho_G);
+    if (p.sigma != 0.0) rb = rb + R(3.0 * p.sigma) * kap;
+    const R r0b = p.compressible ? rb : R(1);
+    const R r0t = p.compressible ? rt : R(1);
+    const R usq = utx * utx + uty * uty + utz * utz;
+    const R lp = R(p.lam_p);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      if (!(gasm & (1u << q))) continue;
+      const int pq = inv(q);  // boundary link: x + c_p is gas, missing f_pbar = f_q
+      R eb = eplus_q<R>(p, pq, rb, r0b, utx, uty, utz, usq);
+      bool up_fluid = !((wallm | gasm) & (1u << pq));
+      if (p.rule == 0 || !up_fluid) {
+        f[q] = -own[pq] + R(2) * eb;  // FSK, Eq. koerner
+      } else {
+        R dl = R(0.5);
+        if (ok) {
+          R cn = R(cx(pq)) * n[0] + R(cy(pq)) * n[1] + R(cz(pq)) * n[2];
+          if (cn > R(0)) {
+            dl = d / cn;
+            dl = dl < R(p.delta_min) ? R(p.delta_min) : (dl > R(1) ? R(1) : dl);
+          }
+        }
+        R et = eplus_q<R>(p, pq, rt, r0t, utx, uty, utz, usq);
+        R nplus = (R(0.5) * (own[pq] + own[q]) - et) * R(p.inv_1plp);
+        R C = lp * (R(0.5) + dl) - R(2) * lp;
+        f[q] = (R(0.5) - dl) * own[pq] + R(0.5) * own[q] + (dl - R(1)) * f[pq] + C * nplus + eb;
+      }
+    }
+  }
+  R rho, ux, uy, uz;
+  collide<R>(p, f, rho, ux, uy, uz);
+  if (!(rho > R(0)) || !(rho < R(1e30))) atomicOr(v.err, ERRB_UNSTABLE);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
+  double mm = v.m[i];
+  if (!p.freeze) {
+    mm = mm + dm;
+    v.m[i] = mm;
+    v.phout[i] = (R)(mm / (double)rho);
+    // thresholds, plus the isolated-cell rules: no gas neighbour -> fill,
+    // no liquid/interface neighbour -> empty
+    fill = mm > (1.0 + p.eps) * (double)rho || ((p.cleanup & 1) && gasm == 0u);
+    empty = !fill && (mm < -p.eps * (double)rho || ((p.cleanup & 2) && (wallm | gasm) == 0x7fffeu));
+    if (fill) v.mark[i] = MK_FILL;  // marks are zero between steps; each cell writes only its own
+    else if (empty) v.mark[i] = MK_EMPTY;
+  }
+  return mm;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int bulk_blocks) {
+  pdl_begin();
   const int count = min(*((volatile int*)&v.cnt[0]), v.cap);
   const int stride = gridDim.x * blockDim.x;
   const int rounds = (count + stride - 1) / stride;
@@ -160,89 +256,9 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
       icell = (int)i;
       int x, y, z;
       coords(p, i, x, y, z);
-      R own[19], f[19];
-#pragma unroll
-      for (int q = 0; q < 19; ++q) own[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)i, q);
-      R rt, utx, uty, utz;
-      moments_post<R>(p, own, rt, utx, uty, utz);
-      f[0] = own[0];
-      unsigned wallm, gasm, liqm;
-      int srcs[19];
-      pull_general<P>(p, v, x, y, z, f, wallm, gasm, &liqm, srcs);
-      const R phic = v.phin[i];
-      // mass exchange (Sec. 2.3) with the pulled values, before any rebuild
-      double dm = 0.0;
-      if (!p.freeze) {
-#pragma unroll
-        for (int q = 1; q < 19; ++q) {
-          if ((wallm | gasm) & (1u << q)) continue;
-          R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + v.phin[srcs[q]]);
-          dm += (double)(sw * (f[q] - own[inv(q)]));
-        }
-      }
-      if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
-      if (gasm) {
-        Geo<R> G;
-        // FSK without surface tension needs neither the plane nor the curvature
-        if (p.rule != 0 || p.sigma != 0.0) {
-          geometry<R>(p, v.flags, v.phin, x, y, z, phic, G);
-        } else {
-          G.ok = false;
-          G.d = R(0);
-          G.kap = R(0);
-          G.n[0] = G.n[1] = G.n[2] = R(0);
-        }
-        const R* n = G.n;
-        const R d = G.d, kap = G.kap;
-        const bool ok = G.ok;
-        R rb = R(p.rho_G);
-        if (p.sigma != 0.0) rb = rb + R(3.0 * p.sigma) * kap;
-        const R r0b = p.compressible ? rb : R(1);
-        const R r0t = p.compressible ? rt : R(1);
-        const R usq = utx * utx + uty * uty + utz * utz;
-        const R lp = R(p.lam_p);
-#pragma unroll
-        for (int q = 1; q < 19; ++q) {
-          if (!(gasm & (1u << q))) continue;
-          const int pq = inv(q);  // boundary link: x + c_p is gas, missing f_pbar = f_q
-          R eb = eplus_q<R>(p, pq, rb, r0b, utx, uty, utz, usq);
-          bool up_fluid = !((wallm | gasm) & (1u << pq));
-          if (p.rule == 0 || !up_fluid) {
-            f[q] = -own[pq] + R(2) * eb;  // FSK, Eq. koerner
-          } else {
-            R dl = R(0.5);
-            if (ok) {
-              R cn = R(cx(pq)) * n[0] + R(cy(pq)) * n[1] + R(cz(pq)) * n[2];
-              if (cn > R(0)) {
-                dl = d / cn;
-                dl = dl < R(p.delta_min) ? R(p.delta_min) : (dl > R(1) ? R(1) : dl);
-              }
-            }
-            R et = eplus_q<R>(p, pq, rt, r0t, utx, uty, utz, usq);
-            R nplus = (R(0.5) * (own[pq] + own[q]) - et) * R(p.inv_1plp);
-            R C = lp * (R(0.5) + dl) - R(2) * lp;
-            f[q] = (R(0.5) - dl) * own[pq] + R(0.5) * own[q] + (dl - R(1)) * f[pq] + C * nplus + eb;
-          }
-        }
-      }
-      R rho, ux, uy, uz;
-      collide<R>(p, f, rho, ux, uy, uz);
-      if (!(rho > R(0)) || !(rho < R(1e30))) atomicOr(v.err, ERRB_UNSTABLE);
-#pragma unroll
-      for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
-      double mm = v.m[i];
-      if (!p.freeze) {
-        mm = mm + dm;
-        v.m[i] = mm;
-        v.phout[i] = (R)(mm / (double)rho);
-        // thresholds, plus the isolated-cell rules: no gas neighbour -> fill,
-        // no liquid/interface neighbour -> empty
-        fill = mm > (1.0 + p.eps) * (double)rho || ((p.cleanup & 1) && gasm == 0u);
-        empty = !fill && (mm < -p.eps * (double)rho || ((p.cleanup & 2) && (wallm | gasm) == 0x7fffeu));
-        if (fill) v.mark[i] = MK_FILL;  // marks are zero between steps; each cell writes only its own
-        else if (empty) v.mark[i] = MK_EMPTY;
-      }
-      msum += mm;
+      const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
+      msum += in3 ? iface_cell<P, true>(p, v, i, x, y, z, fill, empty)
+                  : iface_cell<P, false>(p, v, i, x, y, z, fill, empty);
     }
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);
@@ -256,6 +272,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ in, long long n, long long chunk,
                                                 double* __restrict__ out, const double* add, double* final_out) {
+  pdl_begin();
   __shared__ double red[8];
   long long lo = (long long)blockIdx.x * chunk;
   long long hi = lo + chunk < n ? lo + chunk : n;
@@ -280,7 +297,7 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
                         int* seglist, int* segcount, void* timing_handle, int bulk_mode,
                         const CUtensorMap* tmap) {
   const long long nseg = (long long)((p.nx + 31) / 32) * p.ny * p.nz;
-  k_segments<<<(unsigned)((nseg + 255) / 256), 256, 0, st>>>(p, v.flags, seglist, segcount);
+  if (launch_k(k_segments, (unsigned)((nseg + 255) / 256), 256, 0, st, p, v.flags, seglist, segcount)) return 1;
   bool launched = false;
   if constexpr (P != P64) {
     if (bulk_mode == BULK_TMA && tmap) {
@@ -291,11 +308,20 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
       launched = true;
     }
   }
-  if (!launched) k_bulk<P><<<bulk_blocks, 128, 0, st>>>(p, v, seglist, segcount);
+  if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
+    return 1;
   if (timing_handle && fslbm_mark_between(timing_handle)) return 1;
-  k_iface<P><<<iface_blocks, 128, 0, st>>>(p, v, bulk_blocks * 4);  // after the bulk warps' partials
+  // the interface partials follow the bulk warps' ones
+  if (launch_k(k_iface<P>, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) return 1;
   return (int)cudaGetLastError();
 }
+
+__global__ void k_reset(int* cnt) {
+  pdl_begin();
+  if (threadIdx.x < 10 && threadIdx.x != 8) cnt[threadIdx.x] = 0;
+}
+
+int launch_reset(int* cnt, cudaStream_t st) { return launch_k(k_reset, 1, 32, 0, st, cnt); }
 
 int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, const double* add, double* out,
                   cudaStream_t st) {
@@ -303,8 +329,9 @@ int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, co
   if (chunk < 1) chunk = 1;
   int nb = (int)((n + chunk - 1) / chunk);
   if (nb < 1) nb = 1;
-  k_reduce<<<nb, 256, 0, st>>>(in, n, chunk, tmp, nullptr, nullptr);
-  k_reduce<<<1, 256, 0, st>>>(tmp, nb, nb, tmp + tmp_blocks, add, out);
+  if (launch_k(k_reduce, nb, 256, 0, st, in, n, chunk, tmp, (const double*)nullptr, (double*)nullptr)) return 1;
+  if (launch_k(k_reduce, 1, 256, 0, st, (const double*)tmp, (long long)nb, (long long)nb, tmp + tmp_blocks, add, out))
+    return 1;
   return (int)cudaGetLastError();
 }
 
