@@ -58,7 +58,7 @@ static void drop_events(fslbm* h) {
 
 static void free_all(fslbm* h) {
   drop_events(h);
-  void* ptrs[] = {h->flags, h->mark, h->fA, h->fB, h->m, h->phiA, h->phiB, h->wd, h->cnt, h->share,
+  void* ptrs[] = {h->flags, h->mark, h->fA, h->fB, h->m, h->phiA, h->phiB, h->wd, h->cnt, h->share, h->geo,
                   h->partials, h->red, h->lost, h->err, h->step_mass, h->total_out, h->f0, h->seglist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -158,7 +158,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
             dalloc(h, (char**)&h->fB, 19 * Nn * store_bytes(h->prec) + 16) && dalloc(h, &h->m, Nn * 8) &&
             dalloc(h, (char**)&h->phiA, Nn * real_bytes(h->prec)) &&
             dalloc(h, (char**)&h->phiB, Nn * real_bytes(h->prec)) && dalloc(h, &h->cnt, 16 * sizeof(int)) &&
-            dalloc(h, &h->share, Nn * 8) && dalloc(h, &h->partials, (size_t)h->nparts * 8) &&
+            dalloc(h, &h->share, Nn * 8) && dalloc(h, (char**)&h->geo, 5 * Nn * real_bytes(h->prec)) &&
+            dalloc(h, &h->partials, (size_t)h->nparts * 8) &&
             dalloc(h, &h->red, (size_t)(h->red_blocks + 2) * 8) && dalloc(h, &h->lost, 8) &&
             dalloc(h, &h->err, 8) && dalloc(h, &h->step_mass, 8) && dalloc(h, &h->total_out, 8);
   for (int k = 0; k < 6 && ok; ++k) ok = dalloc(h, &h->lists[k], Nn * sizeof(int));

@@ -308,7 +308,7 @@ __global__ void k_final(Par p, View<P> v) {
     int kk = k;
     if (kk < nf) {
       long long i = v.flist[kk];
-      v.flags[i] = (uint8_t)((v.flags[i] & NEARB) | LIQ);
+      v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | LIQ);
       v.mark[i] = 0;
       continue;
     }
@@ -316,7 +316,7 @@ __global__ void k_final(Par p, View<P> v) {
     if (kk < ne) {
       long long i = v.elist[kk];
       if (v.mark[i] & MK_EMPTY) {
-        v.flags[i] = (uint8_t)((v.flags[i] & NEARB) | GAS);
+        v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | GAS);
         v.phout[i] = R(0);
         v.mark[i] = 0;
         atomicAdd(&v.cnt[7], 1);
@@ -327,14 +327,14 @@ __global__ void k_final(Par p, View<P> v) {
     kk -= ne;
     if (kk < ng) {
       long long i = v.nglist[kk];
-      v.flags[i] = (uint8_t)((v.flags[i] & NEARB) | IFC);
+      v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | IFC);
       v.mark[i] = 0;
       continue;
     }
     kk -= ng;
     if (kk < nl) {
       long long i = v.nllist[kk];
-      v.flags[i] = (uint8_t)((v.flags[i] & NEARB) | IFC);
+      v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | IFC);
       v.mark[i] = 0;
       continue;
     }

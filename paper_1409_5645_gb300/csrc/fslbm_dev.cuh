@@ -39,7 +39,9 @@ __host__ __device__ constexpr R wq(int q) {
   return q == 0 ? R(1) / R(3) : (q <= 6 ? R(1) / R(18) : R(1) / R(36));
 }
 
-enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16 };
+// static bits beside the kind: NEARB a neighbour is a wall (a WALL cell or
+// beyond a non-periodic face); NEARW a neighbour is a WALL cell of the lattice
+enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16, NEARW = 32, STATIC_BITS = 48 };
 enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16 };
 enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8 };
 
@@ -125,6 +127,7 @@ struct View {
   int* cnt;     // [0] ilist [1] flist [2] elist [3] ng [4] nl [5] rl [7] emptied; [8] all conversions since set; [9] fluid segments
   int cap;
   double* share;
+  R* geo;            // interface geometry per list entry: [5][cap] n0, n1, n2, d, kappa (n = 0: none)
   double* partials;  // block partial sums of the mass balance
   double* lost;
   int* err;
@@ -203,43 +206,83 @@ __device__ __forceinline__ R eminus(R r0, R vx, R vy, R vz) {
   return R(3) * wq<R>(q) * r0 * cu;
 }
 
+// Arithmetic with the rounding of every operation fixed (no compiler choice
+// of fused multiply-adds), so that a collision gives the same bits in every
+// kernel it is inlined into.
+__device__ __forceinline__ float fx_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fx_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fx_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fx_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fx_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double fx_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float fx_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double fx_sub(double a, double b) { return __dsub_rn(a, b); }
+
+// c.u for a lattice direction (components 0 or +-1: exact adds)
+template <class R, int q>
+__device__ __forceinline__ R cdot(R ux, R uy, R uz) {
+  R s = R(0);
+  if (cx(q) == 1) s = fx_add(s, ux);
+  if (cx(q) == -1) s = fx_sub(s, ux);
+  if (cy(q) == 1) s = fx_add(s, uy);
+  if (cy(q) == -1) s = fx_sub(s, uy);
+  if (cz(q) == 1) s = fx_add(s, uz);
+  if (cz(q) == -1) s = fx_sub(s, uz);
+  return s;
+}
+
 // TRT collision of one cell (Eq. lbe2) in place: f <- f + l+ n^+ + l- n^-,
 // with u = U + g/2 in e^+ and u^eq = U - g/lambda_- in e^- (Sec. 2.1).
 // On return rho holds sum f and (ux,uy,uz) the velocity u of the
 // pre-collision state.
 template <class R>
 __device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux, R& uy, R& uz) {
-  R r = R(0), jx = R(0), jy = R(0), jz = R(0);
+  R r = f[0], jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
-  for (int q = 0; q < 19; ++q) {
-    r += f[q];
-    if (cx(q)) jx += R(cx(q)) * f[q];
-    if (cy(q)) jy += R(cy(q)) * f[q];
-    if (cz(q)) jz += R(cz(q)) * f[q];
+  for (int q = 1; q < 19; ++q) r = fx_add(r, f[q]);
+#pragma unroll
+  for (int q = 1; q < 19; ++q) {
+    if (cx(q) == 1) jx = fx_add(jx, f[q]);
+    if (cx(q) == -1) jx = fx_sub(jx, f[q]);
+    if (cy(q) == 1) jy = fx_add(jy, f[q]);
+    if (cy(q) == -1) jy = fx_sub(jy, f[q]);
+    if (cz(q) == 1) jz = fx_add(jz, f[q]);
+    if (cz(q) == -1) jz = fx_sub(jz, f[q]);
   }
-  R r0 = p.compressible ? r : R(1);
-  R ir0 = R(1) / r0;
-  R Ux = jx * ir0, Uy = jy * ir0, Uz = jz * ir0;
-  R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
-  ux = Ux + R(0.5) * gx; uy = Uy + R(0.5) * gy; uz = Uz + R(0.5) * gz;
-  R ilm = R(1) / R(p.lam_m);
-  R vx = Ux - gx * ilm, vy = Uy - gy * ilm, vz = Uz - gz * ilm;
-  R usq = ux * ux + uy * uy + uz * uz;
-  R lp = R(p.lam_p), lm = R(p.lam_m);
+  const R r0 = p.compressible ? r : R(1);
+  const R ir0 = R(1) / r0;
+  const R Ux = fx_mul(jx, ir0), Uy = fx_mul(jy, ir0), Uz = fx_mul(jz, ir0);
+  const R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
+  ux = fx_fma(R(0.5), gx, Ux);
+  uy = fx_fma(R(0.5), gy, Uy);
+  uz = fx_fma(R(0.5), gz, Uz);
+  const R ilm = R(1) / R(p.lam_m);
+  const R vx = fx_fma(-gx, ilm, Ux), vy = fx_fma(-gy, ilm, Uy), vz = fx_fma(-gz, ilm, Uz);
+  const R usq = fx_fma(uz, uz, fx_fma(uy, uy, fx_mul(ux, ux)));
+  const R lp = R(p.lam_p), lm = R(p.lam_m);
+  // e^+_q = w rho + K_w (3 (c.u)^2 - u.u), K_w = 3/2 w rho_0 (0 for linear e^+);
+  // e^-_q = 3 w rho_0 (c.u^eq)
+  const R nl = p.linear_eq ? R(0) : R(1);
+  const R k0 = fx_mul(fx_mul(R(1.5) * wq<R>(0), r0), nl);
+  const R k1 = fx_mul(fx_mul(R(1.5) * wq<R>(1), r0), nl);
+  const R k7 = fx_mul(fx_mul(R(1.5) * wq<R>(7), r0), nl);
+  const R m1 = fx_mul(R(3) * wq<R>(1), r0), m7 = fx_mul(R(3) * wq<R>(7), r0);
   R out[19];
   {
-    R ep = eplus<R, 0>(p, r, r0, ux, uy, uz, usq);
-    out[0] = f[0] + lp * (f[0] - ep);
+    const R ep = fx_fma(k0, -usq, fx_mul(wq<R>(0), r));
+    out[0] = fx_fma(lp, fx_sub(f[0], ep), f[0]);
   }
-#define FSL_PAIR(q)                                                       \
-  {                                                                       \
-    constexpr int qb = inv(q);                                            \
-    R ep = eplus<R, q>(p, r, r0, ux, uy, uz, usq);                        \
-    R em = eminus<R, q>(r0, vx, vy, vz);                                  \
-    R np = R(0.5) * (f[q] + f[qb]) - ep;                                  \
-    R nm = R(0.5) * (f[q] - f[qb]) - em;                                  \
-    out[q] = f[q] + lp * np + lm * nm;                                    \
-    out[qb] = f[qb] + lp * np - lm * nm;                                  \
+#define FSL_PAIR(q)                                                                  \
+  {                                                                                  \
+    constexpr int qb = inv(q);                                                       \
+    const R kq = q <= 6 ? k1 : k7, mq = q <= 6 ? m1 : m7;                            \
+    const R cu = cdot<R, q>(ux, uy, uz), cv = cdot<R, q>(vx, vy, vz);                \
+    const R ep = fx_fma(kq, fx_fma(R(3) * cu, cu, -usq), fx_mul(wq<R>(q), r));       \
+    const R em = fx_mul(mq, cv);                                                     \
+    const R np = fx_fma(R(0.5), fx_add(f[q], f[qb]), -ep);                           \
+    const R nm = fx_fma(R(0.5), fx_sub(f[q], f[qb]), -em);                           \
+    out[q] = fx_fma(lm, nm, fx_fma(lp, np, f[q]));                                   \
+    out[qb] = fx_fma(-lm, nm, fx_fma(lp, np, f[qb]));                                \
   }
   FSL_PAIR(1) FSL_PAIR(3) FSL_PAIR(5) FSL_PAIR(7) FSL_PAIR(9)
   FSL_PAIR(11) FSL_PAIR(13) FSL_PAIR(15) FSL_PAIR(17)

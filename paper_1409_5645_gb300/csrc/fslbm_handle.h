@@ -29,6 +29,7 @@ struct fslbm {
   int* seglist;  // 32-cell x segments holding fluid (rebuilt every step)
   int* cnt;
   double* share;
+  void* geo;  // interface geometry scratch [5][cap] in the arithmetic type
   double* partials;
   long long nparts;
   int bulk_blocks, iface_blocks, list_blocks, red_blocks;
@@ -82,6 +83,7 @@ inline fsl::View<P> make_view(fslbm* h) {
   v.cnt = h->cnt;
   v.cap = h->cap;
   v.share = h->share;
+  v.geo = (R*)h->geo;
   v.partials = h->partials;
   v.lost = h->lost;
   v.err = h->err;

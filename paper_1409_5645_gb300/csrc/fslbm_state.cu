@@ -95,16 +95,17 @@ __global__ void k_prepare_flags(Par p, uint8_t* flags, int* err) {
     if (k != LIQ && k != IFC && k != GAS && k != WALL) { atomicOr(err, ERRB_STATE); continue; }
     int x, y, z;
     coords(p, i, x, y, z);
-    bool nearb = false, gas = false;
+    bool nearb = false, nearw = false, gas = false;
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
       long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
       uint8_t kj = kind_at(flags, j);
       nearb |= (kj == WALL);
+      nearw |= (j >= 0 && kj == WALL);
       gas |= (kj == GAS);
     }
     if (k == LIQ && gas) atomicOr(err, ERRB_STATE);
-    flags[i] = (uint8_t)(k | (nearb ? NEARB : 0));
+    flags[i] = (uint8_t)(k | (nearb ? NEARB : 0) | (nearw ? NEARW : 0));
   }
 }
 

@@ -102,18 +102,43 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
     warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
-    if (k != LIQ) continue;
     const size_t N = (size_t)p.N;
     R f[19];
-    const bool fast = !(fl & NEARB) && x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 &&
-                      z < p.nz - 1;
-    if (fast) {
+    // Fast path: every source is a fluid cell at a plain offset, or lies beyond
+    // a non-periodic face (half-way bounce-back f_q = f~_qbar(x), read by
+    // selecting the cell's own slot).  Cells next to a WALL cell, on a
+    // periodic face, or with CLI link fractions take the general path.
+    const bool ax0 = x == 0, ax1 = x == p.nx - 1, ay0 = y == 0, ay1 = y == p.ny - 1, az0 = z == 0,
+               az1 = z == p.nz - 1;
+    const bool onface = ax0 || ax1 || ay0 || ay1 || az0 || az1;
+    const bool fast = k == LIQ &&
+                      (p.has_wd ? !(fl & NEARB) && !onface
+                                : !(fl & NEARW) && !((ax0 || ax1) && p.px) && !((ay0 || ay1) && p.py) &&
+                                      !((az0 || az1) && p.pz));
+    const bool face_warp = __any_sync(0xffffffffu, fast && onface);
+    if (k != LIQ) continue;
+    if (fast && !face_warp) {
       const long long sy = p.nx, sz = (long long)p.nx * p.ny;
 #define FSL_LD(q) f[q] = ld<P, q>(v.fin, (size_t)q * N + (size_t)(i - (cx(q) + sy * cy(q) + sz * cz(q))));
       FSL_LD(0) FSL_LD(1) FSL_LD(2) FSL_LD(3) FSL_LD(4) FSL_LD(5) FSL_LD(6) FSL_LD(7) FSL_LD(8)
       FSL_LD(9) FSL_LD(10) FSL_LD(11) FSL_LD(12) FSL_LD(13) FSL_LD(14) FSL_LD(15) FSL_LD(16)
       FSL_LD(17) FSL_LD(18)
 #undef FSL_LD
+    } else if (fast) {
+      const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+#define FSL_LDF(q)                                                                                              \
+  {                                                                                                             \
+    const bool bb = (cx(q) == 1 && ax0) || (cx(q) == -1 && ax1) || (cy(q) == 1 && ay0) || (cy(q) == -1 && ay1) || \
+                    (cz(q) == 1 && az0) || (cz(q) == -1 && az1);                                                \
+    const size_t k_ = bb ? (size_t)inv(q) * N + (size_t)i                                                       \
+                         : (size_t)q * N + (size_t)(i - (cx(q) + sy * cy(q) + sz * cz(q)));                    \
+    f[q] = bb ? ld<P, inv(q)>(v.fin, k_) : ld<P, q>(v.fin, k_);                                                 \
+  }
+      f[0] = ld<P, 0>(v.fin, (size_t)i);
+      FSL_LDF(1) FSL_LDF(2) FSL_LDF(3) FSL_LDF(4) FSL_LDF(5) FSL_LDF(6) FSL_LDF(7) FSL_LDF(8)
+      FSL_LDF(9) FSL_LDF(10) FSL_LDF(11) FSL_LDF(12) FSL_LDF(13) FSL_LDF(14) FSL_LDF(15) FSL_LDF(16)
+      FSL_LDF(17) FSL_LDF(18)
+#undef FSL_LDF
     } else {
       unsigned wallm, gasm;
       f[0] = ld<P, 0>(v.fin, (size_t)i);
@@ -150,8 +175,8 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
 // every cell within 3 of it lies inside the lattice, so all stencil offsets
 // are plain (the hot path, kept apart from the face and wrap logic).
 template <int P, bool IN>
-__device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, long long i, int x, int y, int z,
-                                             bool& fill, bool& empty) {
+__device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int li, long long i, int x, int y,
+                                             int z, bool& fill, bool& empty) {
   using R = typename Form<P>::R;
   const size_t N = (size_t)p.N;
   R own[19], f[19];
@@ -161,8 +186,9 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, lon
   moments_post<R>(p, own, rt, utx, uty, utz);
   f[0] = own[0];
   unsigned wallm, gasm, liqm;
-  int srcs[19];
-  pull_general<P, IN>(p, v, x, y, z, f, wallm, gasm, &liqm, srcs);
+  int srcs[19];  // sources of the pull (only kept off the interior path)
+  pull_general<P, IN>(p, v, x, y, z, f, wallm, gasm, &liqm, IN ? nullptr : srcs);
+  const long long sy = p.nx, sz = (long long)p.nx * p.ny;
   const R phic = v.phin[i];
   // mass exchange (Sec. 2.3) with the pulled values, before any rebuild
   double dm = 0.0;
@@ -170,25 +196,24 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, lon
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
       if ((wallm | gasm) & (1u << q)) continue;
-      R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + v.phin[srcs[q]]);
+      const long long sq = IN ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : (long long)srcs[q];
+      R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + v.phin[sq]);
       dm += (double)(sw * (f[q] - own[inv(q)]));
     }
   }
   if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
   if (gasm) {
-    Geo<R> G;
-    // FSK without surface tension needs neither the plane nor the curvature
+    // the plane and curvature of k_geom (FSK without surface tension needs neither)
+    R n[3] = {R(0), R(0), R(0)}, d = R(0), kap = R(0);
     if (p.rule != 0 || p.sigma != 0.0) {
-      geometry<R, IN>(p, v.flags, v.phin, x, y, z, phic, G);
-    } else {
-      G.ok = false;
-      G.d = R(0);
-      G.kap = R(0);
-      G.n[0] = G.n[1] = G.n[2] = R(0);
+      const size_t cap = (size_t)v.cap;
+      n[0] = v.geo[li];
+      n[1] = v.geo[cap + li];
+      n[2] = v.geo[2 * cap + li];
+      d = v.geo[3 * cap + li];
+      kap = v.geo[4 * cap + li];
     }
-    const R* n = G.n;
-    const R d = G.d, kap = G.kap;
-    const bool ok = G.ok;
+    const bool ok = true;  // no normal is stored as n = 0: c.n > 0 fails and delta stays 1/2
     R rb = R(p.rho_G);
     if (p.sigma != 0.0) rb = rb + R(3.0 * p.sigma) * kap;
     const R r0b = p.compressible ? rb : R(1);
@@ -239,6 +264,34 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, lon
   return mm;
 }
 
+// ---------------------------------------------------------------------------
+// k_geom: plane (normal, offset) and curvature of every listed interface cell
+// from phi(t) (Sec. 2.2, Sec. 5), one thread per cell, into v.geo; kept apart
+// from k_iface so that each kernel holds fewer registers and less code.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
+  pdl_begin();
+  using R = typename Form<P>::R;
+  const int count = min(*((volatile int*)&v.cnt[0]), v.cap);
+  const size_t cap = (size_t)v.cap;
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < count; li += gridDim.x * blockDim.x) {
+    const long long i = v.ilist[li];
+    int x, y, z;
+    coords(p, i, x, y, z);
+    const R phic = v.phin[i];
+    Geo<R> G;
+    const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
+    if (in3) geometry<R, true>(p, v.flags, v.phin, x, y, z, phic, G);
+    else geometry<R, false>(p, v.flags, v.phin, x, y, z, phic, G);
+    v.geo[li] = G.ok ? G.n[0] : R(0);
+    v.geo[cap + li] = G.ok ? G.n[1] : R(0);
+    v.geo[2 * cap + li] = G.ok ? G.n[2] : R(0);
+    v.geo[3 * cap + li] = G.d;
+    v.geo[4 * cap + li] = G.kap;
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int bulk_blocks) {
   pdl_begin();
@@ -257,8 +310,8 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
       int x, y, z;
       coords(p, i, x, y, z);
       const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
-      msum += in3 ? iface_cell<P, true>(p, v, i, x, y, z, fill, empty)
-                  : iface_cell<P, false>(p, v, i, x, y, z, fill, empty);
+      msum += in3 ? iface_cell<P, true>(p, v, li, i, x, y, z, fill, empty)
+                  : iface_cell<P, false>(p, v, li, i, x, y, z, fill, empty);
     }
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);
@@ -311,6 +364,7 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
     return 1;
   if (timing_handle && fslbm_mark_between(timing_handle)) return 1;
+  if ((p.rule != 0 || p.sigma != 0.0) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v)) return 1;
   // the interface partials follow the bulk warps' ones
   if (launch_k(k_iface<P>, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) return 1;
   return (int)cudaGetLastError();
