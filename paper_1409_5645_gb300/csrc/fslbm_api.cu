@@ -148,10 +148,10 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   // 32-cell segments; the bulk kernel runs one resident wave of warps
   const long long nseg = ((p.nx + 31) / 32) * (long long)p.ny * p.nz;
   h->bulk_blocks = 152 * (h->prec == FSLBM_F64 ? 4 : 8);
-  h->iface_blocks = 152 * 8;
+  h->iface_blocks = 152 * 16;  // one thread per interface cell up to 311 296 cells per round
   h->list_blocks = 152 * 2;
   h->red_blocks = 152;
-  h->nparts = h->bulk_blocks * 4 + h->iface_blocks;  // one partial per bulk warp, per interface block
+  h->nparts = (h->bulk_blocks + h->iface_blocks) * 4;  // one partial per bulk and per interface warp
   if (h->nparts < 4096) h->nparts = 4096;
   bool ok = dalloc(h, &h->flags, N4) && dalloc(h, &h->mark, N4) &&
             dalloc(h, (char**)&h->fA, 19 * Nn * store_bytes(h->prec) + 16) &&
@@ -164,7 +164,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
             dalloc(h, &h->err, 8) && dalloc(h, &h->step_mass, 8) && dalloc(h, &h->total_out, 8);
   for (int k = 0; k < 6 && ok; ++k) ok = dalloc(h, &h->lists[k], Nn * sizeof(int));
   if (ok && q.keep_f0) ok = dalloc(h, &h->f0, 19 * Nn * 8);
-  if (ok) ok = dalloc(h, &h->seglist, (size_t)nseg * sizeof(int));
+  if (ok) ok = dalloc(h, &h->seglist, (size_t)nseg * 4 * sizeof(int));  // int4 per segment
   if (!ok) {
     free_all(h);
     free(h);
@@ -392,7 +392,7 @@ static int step_t(fslbm* h) {
                              h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr))
     return 1;
   if (mark_event(h, 2)) return 1;
-  if (launch_reduce(h->partials, (long long)h->bulk_blocks * 4 + h->iface_blocks, h->red, h->red_blocks, h->lost,
+  if (launch_reduce(h->partials, (long long)(h->bulk_blocks + h->iface_blocks) * 4, h->red, h->red_blocks, h->lost,
                     h->step_mass, h->st))
     return 1;
   if (mark_event(h, 3)) return 1;

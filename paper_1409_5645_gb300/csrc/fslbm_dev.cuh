@@ -164,15 +164,6 @@ __device__ __forceinline__ void coords(const Par& p, long long i, int& x, int& y
   y = (int)yy;
   x = (int)(r - yy * (unsigned)p.nx);
 }
-// row (y + ny z), first x and (y, z) of 32-cell x segment sg
-__device__ __forceinline__ void seg_coords(const Par& p, int sg, int& row, int& x0, int& y, int& z) {
-  const unsigned r = fdiv((unsigned)sg, p.dnsx);
-  const unsigned zz = fdiv(r, p.dny);
-  row = (int)r;
-  x0 = (int)(((unsigned)sg - r * (unsigned)((p.nx + 31) >> 5)) << 5);
-  z = (int)zz;
-  y = (int)(r - zz * (unsigned)p.ny);
-}
 __device__ __forceinline__ uint8_t kind_at(const uint8_t* flags, long long j) {
   return j < 0 ? (uint8_t)WALL : (uint8_t)(flags[j] & KIND);
 }
@@ -385,8 +376,11 @@ __device__ R plic_offset(R nx_, R ny_, R nz_, R ph) {
   const bool upper = ph > R(0.5);
   const R tv = upper ? R(1) - ph : ph;
   R lo = R(0), hi = R(0.5);
+  // bracket to 2^-21 (FP64) or 2^-13 (FP32, where the Newton steps below then
+  // reach the float resolution); the fill clamp keeps the root above ~1e-3
+  constexpr int bisect = sizeof(R) == 8 ? 20 : 12;
 #pragma unroll 1
-  for (int it = 0; it < 20; ++it) {  // bracket to 2^-21
+  for (int it = 0; it < bisect; ++it) {
     R mid = R(0.5) * (lo + hi);
     if (cube_vol_half(mid, a0, a1, a2) < tv) lo = mid; else hi = mid;
   }

@@ -42,17 +42,32 @@ __device__ __forceinline__ void pull_general(const Par& p, const View<P>& v, int
   const bool in1 = IN || (x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1);
   const long long i = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
   const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+  if constexpr (IN) {
+    // every source lies inside the lattice: issue the population and flag
+    // loads together (a gas source's stale populations are read and dropped)
 #pragma unroll
-  for (int q = 1; q < 19; ++q) {
-    long long s = IN ? i - (cx(q) + sy * cy(q) + sz * cz(q))
-                     : (in1 ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, -cx(q), -cy(q), -cz(q)));
-    uint8_t ks = kind_at(v.flags, s);
-    if (srcs) srcs[q] = (int)s;
-    if (is_fluid(ks)) {
-      f[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)s, q);
-      if (ks == LIQ) lm |= 1u << q;
-    } else if (ks == WALL) { wallm |= 1u << q; f[q] = 0; }
-    else { gasm |= 1u << q; f[q] = 0; }
+    for (int q = 1; q < 19; ++q) {
+      const long long s = i - (cx(q) + sy * cy(q) + sz * cz(q));
+      const uint8_t ks = v.flags[s] & KIND;
+      const typename Form<P>::R fq = ldq<P>(v.fin, (size_t)q * N + (size_t)s, q);
+      if (is_fluid(ks)) {
+        f[q] = fq;
+        if (ks == LIQ) lm |= 1u << q;
+      } else if (ks == WALL) { wallm |= 1u << q; f[q] = 0; }
+      else { gasm |= 1u << q; f[q] = 0; }
+    }
+  } else {
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      long long s = in1 ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
+      uint8_t ks = kind_at(v.flags, s);
+      if (srcs) srcs[q] = (int)s;
+      if (is_fluid(ks)) {
+        f[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)s, q);
+        if (ks == LIQ) lm |= 1u << q;
+      } else if (ks == WALL) { wallm |= 1u << q; f[q] = 0; }
+      else { gasm |= 1u << q; f[q] = 0; }
+    }
   }
   if (liqm) *liqm = lm;
 }

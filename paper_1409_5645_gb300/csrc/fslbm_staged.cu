@@ -139,9 +139,8 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
 
   // lane 0: start the copies of segment si into stage s
   auto issue = [&](int si, int s) {
-    const int sg = seglist[si];
-    int row, x0, y, z;
-    seg_coords(p, sg, row, x0, y, z);
+    const int4 sd = reinterpret_cast<const int4*>(seglist)[si];
+    const int x0 = sd.x, y = sd.y, z = sd.z;
     uint64_t* bar = &bars[warp][s];
     mbar_expect_tx(bar, 19u * (unsigned)G::ROWB);
     unsigned char* dst = wbuf + s * G::STAGE;
@@ -172,12 +171,11 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     pending &= ~(1u << stage);
     const unsigned char* buf = wbuf + stage * G::STAGE;
 
-    const int sg = seglist[si];
-    int row, x0s, y, z;
-    seg_coords(p, sg, row, x0s, y, z);
-    const int x = x0s + lane;
+    const int4 sd = reinterpret_cast<const int4*>(seglist)[si];
+    const int x = sd.x + lane, y = sd.y, z = sd.z;
+    const long long rowstart = (long long)sd.w - sd.x;  // index of x = 0 in this row
     const bool in = x < p.nx;
-    const long long i = (long long)row * p.nx + x;
+    const long long i = rowstart + x;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
     warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
@@ -269,16 +267,15 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
   // all lanes: start the copies of segment si (if any) into stage stg, one commit group
   auto issue = [&](int si, int stg) {
     if (si < nseg) {
-      const int sg = seglist[si];
-      int row, x0s, y, z;
-      seg_coords(p, sg, row, x0s, y, z);
-      const int x = x0s + lane;
-      const long long i = (long long)row * p.nx + x;
+      const int4 sd = reinterpret_cast<const int4*>(seglist)[si];
+      const int x = sd.x + lane, y = sd.y, z = sd.z;
+      const long long rowstart = (long long)sd.w - sd.x;  // index of x = 0 in this row
+      const long long i = rowstart + x;
       const bool in = x < p.nx;
       const bool xm = x >= 1, xp = x < p.nx - 1, ym = y >= 1, yp = y < p.ny - 1, zm = z >= 1, zp = z < p.nz - 1;
       const unsigned dst = base + (unsigned)(stg * 20 * 128);
       // the flag word (the flag array is padded to a multiple of 4 bytes)
-      cp_async4(dst + 19 * 128, v.flags + ((in ? i : (long long)row * p.nx) & ~3LL), true);
+      cp_async4(dst + 19 * 128, v.flags + ((in ? i : rowstart) & ~3LL), true);
 #pragma unroll
       for (int q = 0; q < 19; ++q) {
         const int ccx = cx(q), ccy = cy(q), ccz = cz(q);
@@ -307,12 +304,11 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
   for (int si = gw; si < nseg; si += nw) {
     cp_async_wait<AS_STAGES - 1>();  // this lane's copies of segment si have landed
     const uint32_t* sl = slots + stg * 20 * 32;
-    const int sg = seglist[si];
-    int row, x0s, y, z;
-    seg_coords(p, sg, row, x0s, y, z);
-    const int x = x0s + lane;
+    const int4 sd = reinterpret_cast<const int4*>(seglist)[si];
+    const int x = sd.x + lane, y = sd.y, z = sd.z;
+    const long long rowstart = (long long)sd.w - sd.x;  // index of x = 0 in this row
     const bool in = x < p.nx;
-    const long long i = (long long)row * p.nx + x;
+    const long long i = rowstart + x;
     const uint8_t fl = in ? (uint8_t)(sl[19 * 32] >> (8 * (int)(i & 3))) : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
     warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);

@@ -73,7 +73,15 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
     bbase = t ? atomicAdd(count, t) : 0;
   }
   __syncthreads();
-  if (act) seglist[bbase + wbase[w] + __popc(bal & ((1u << lane) - 1u))] = (int)sgi;
+  if (act) {
+    // the segment's first x, y, z and first cell index, so that the bulk
+    // kernels need no division
+    const unsigned row = fdiv((unsigned)sgi, p.dnsx);
+    const unsigned zz = fdiv(row, p.dny);
+    const int x0 = (int)((unsigned)sgi - row * (unsigned)nsx) << 5;
+    reinterpret_cast<int4*>(seglist)[bbase + wbase[w] + __popc(bal & ((1u << lane) - 1u))] =
+        make_int4(x0, (int)(row - zz * (unsigned)p.ny), (int)zz, (int)row * p.nx + x0);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -85,20 +93,16 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
                                               const int* __restrict__ segcount) {
   pdl_begin();
   using R = typename Form<P>::R;
-  const int nsx = (p.nx + 31) >> 5;
   const int nseg = *((volatile const int*)segcount);
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   double msum = 0.0;
   for (int si = gw; si < nseg; si += nw) {
-    const int sg = seglist[si];
-    // (plain division measured faster here than the multiply-shift form)
-    const int row = sg / nsx;
-    const int x = ((sg - row * nsx) << 5) + lane;
-    const int y = row % p.ny, z = row / p.ny;
+    const int4 sd = reinterpret_cast<const int4*>(seglist)[si];  // x0, y, z, first cell
+    const int x = sd.x + lane, y = sd.y, z = sd.z;
     const bool in = x < p.nx;
-    const long long i = (long long)row * p.nx + x;
+    const long long i = (long long)sd.w + lane;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
     warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
@@ -197,7 +201,8 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     for (int q = 1; q < 19; ++q) {
       if ((wallm | gasm) & (1u << q)) continue;
       const long long sq = IN ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : (long long)srcs[q];
-      R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + v.phin[sq]);
+      const R phs = v.phin[sq];  // (loaded whatever the kind, so the loads overlap)
+      R sw = (liqm & (1u << q)) ? R(1) : R(0.5) * (phic + phs);
       dm += (double)(sw * (f[q] - own[inv(q)]));
     }
   }
@@ -264,6 +269,14 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
   return mm;
 }
 
+// the geometry of cells within 3 of a face, out of line so that the
+// interior path of k_geom stays compact
+template <class R>
+__device__ __noinline__ void geometry_edge(const Par& p, const uint8_t* __restrict__ flags,
+                                           const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
+  geometry<R, false>(p, flags, phin, x, y, z, phic, G);
+}
+
 // ---------------------------------------------------------------------------
 // k_geom: plane (normal, offset) and curvature of every listed interface cell
 // from phi(t) (Sec. 2.2, Sec. 5), one thread per cell, into v.geo; kept apart
@@ -280,20 +293,26 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
     int x, y, z;
     coords(p, i, x, y, z);
     const R phic = v.phin[i];
-    Geo<R> G;
     const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
-    if (in3) geometry<R, true>(p, v.flags, v.phin, x, y, z, phic, G);
-    else geometry<R, false>(p, v.flags, v.phin, x, y, z, phic, G);
-    v.geo[li] = G.ok ? G.n[0] : R(0);
-    v.geo[cap + li] = G.ok ? G.n[1] : R(0);
-    v.geo[2 * cap + li] = G.ok ? G.n[2] : R(0);
-    v.geo[3 * cap + li] = G.d;
-    v.geo[4 * cap + li] = G.kap;
+    R o[5];
+    if (in3) {
+      Geo<R> G;  // (in registers)
+      geometry<R, true>(p, v.flags, v.phin, x, y, z, phic, G);
+      o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
+      o[3] = G.d; o[4] = G.kap;
+    } else {
+      Geo<R> G;  // (in local memory: passed out of line)
+      geometry_edge<R>(p, v.flags, v.phin, x, y, z, phic, G);
+      o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
+      o[3] = G.d; o[4] = G.kap;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v.geo[k * cap + li] = o[k];
   }
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int bulk_blocks) {
+__global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int part_base) {
   pdl_begin();
   const int count = min(*((volatile int*)&v.cnt[0]), v.cap);
   const int stride = gridDim.x * blockDim.x;
@@ -316,8 +335,10 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);
   }
-  double s = block_sum128(msum);
-  if (threadIdx.x == 0) v.partials[bulk_blocks + blockIdx.x] = s;
+  // per-warp partial sums (no block barrier), after the bulk warps' ones
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
+  if ((threadIdx.x & 31) == 0) v.partials[part_base + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5)] = msum;
 }
 
 // ---------------------------------------------------------------------------
