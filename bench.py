@@ -4,9 +4,11 @@
 Workload: 3D dam break 512 x 256 x 256 (33.5 M cells), walls on all faces,
 liquid column x < 128, z < 192 at rest with hydrostatic density,
 g = 1e-5 along -z, FSL rule, seeded fill perturbation 1e-3 on the interface
-layer, tau = 0.52 with the magic parameter Lambda = 0.005 (lambda_- = -1):
-with FSL the tau = 0.51 run loses stability within 3500-8500 steps for every
-Lambda tried, tau = 0.52 runs the 10000 steps.  The headline form is FP32 populations with FP64
+layer, tau = 0.53 with the magic parameter Lambda = 0.005: droplets thrown
+off the splash fall freely (the free-surface model has no gas drag) and at
+tau = 0.51 and 0.52 a run loses stability between 4000 and 9000 steps,
+depending on Lambda and on rounding; tau = 0.53 with Lambda = 0.005 runs
+13000 steps in FP32 and FP16.  The headline form is FP32 populations with FP64
 interface mass and mass balance; FP64 and FP16-storage forms are measured in
 the same run.  A "step" is one full time step: stream-collide, free-surface
 reconstruction, mass exchange, mass balance and cell conversions.
@@ -34,8 +36,11 @@ METRIC = "FSLBM MLUPS at 1 GB300 (FP32/FP16-store vs FP64 plain), % HBM roofline
 WORKLOAD = "dam_break_512x256x256_fsl"
 DIMS = (512, 256, 256)
 COL = (128, 192)
-TAU, MAGIC = 0.52, 0.005
-KERNELS_PER_STEP = 12  # k_segments, k_bulk, k_iface, 2 x k_reduce, 7 conversion kernels
+TAU, MAGIC = 0.53, 0.005
+# kernels of one step: k_reset, k_segments, k_bulk, k_geom (FSL or surface
+# tension only), k_iface, 2 x k_reduce, 7 conversion kernels
+def kernels_per_step(rule, sigma=0.0):
+    return 13 + (1 if (rule != 0 or sigma != 0.0) else 0)
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 
@@ -49,6 +54,7 @@ def parse():
     ap.add_argument("--form-steps", type=int, default=2000, help="timed steps of the non-headline forms")
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--small", action="store_true", help="development size (128 x 64 x 64)")
     ap.add_argument("--dims", default=None, help="nx,ny,nz of a scaled dam break (profiling)")
     ap.add_argument("--tau", type=float, default=TAU)
@@ -236,6 +242,25 @@ def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False):
     return out
 
 
+def adjoint_run(form, steps=4000, K=200):
+    """Differentiation workload: film 8 x 4 x 64, depth 40, objective the mean
+    x-velocity of the interface cells after `steps` steps, checkpoints every K
+    steps with recompute; forward and adjoint cost per step and peak memory."""
+    from paper_1409_5645_gb300 import cases, fslbm
+    lat = fslbm.Lattice.from_case(cases.adjoint_film(), precision=form)
+    try:
+        lat.adjoint_forward(steps, K)
+        lat.adjoint_backward()
+    except fslbm.FslbmError as e:  # e.g. a conversion inside the window
+        lat.close()
+        return {"steps": steps, "checkpoint_every": K, "error": str(e)}
+    fwd, adj, peak = lat.adjoint_stats()
+    lat.close()
+    return {"steps": steps, "checkpoint_every": K, "fwd_ms_per_step": round(fwd, 5),
+            "adj_ms_per_step": round(adj, 5), "adj_over_fwd": round(adj / fwd, 3) if fwd > 0 else None,
+            "peak_bytes": int(peak)}
+
+
 def e2e_run(case, form, steps, local_rank):
     """The user's call sequence with host buffers: state from pinned host
     memory, then every step fslbm_step + a device->host read of that step's
@@ -329,7 +354,7 @@ def main():
                                "reduce": round(head["groups_ms"][2], 5), "conversions": round(head["groups_ms"][3], 5)},
         "cells": {"total": N, "liquid_avg": head["n_liquid"], "interface_avg": head["n_interface"]},
         "mass_drift_rel": (head["mass1"] - head["mass0"]) / head["mass0"],
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": kernels_per_step(args.rule) * args.steps,
         "clocks": head["clocks"],
     }
     # the other precision forms on the same workload
@@ -352,6 +377,14 @@ def main():
                    "h2d_bytes_per_step": e2e["h2d_bytes"] // args.e2e_steps,
                    "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "steps": args.e2e_steps,
                    "includes": "state upload from pinned host memory, per-step mass read"}
+    # differentiation: adjoint step cost per forward step (FP64 and FP32)
+    if not args.no_adjoint:
+        # (FP32 rounding drifts the film's mass and fills a surface cell after
+        # about 4000 steps; a conversion ends a differentiated window, so the
+        # FP32 form is timed on the first 1000 steps)
+        line["adjoint"] = {"workload": "film 8x4x64 depth 40, checkpoints with recompute",
+                           "objective": "mean x-velocity of interface cells",
+                           "f64": adjoint_run("f64", 4000, 200), "f32": adjoint_run("f32", 1000, 100)}
     # the oracle on the host cores (rank 0, N = 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, st, el = oracle_rate((128, 64, 64), (32, 48), budget_s=12.0, tau=args.tau, magic=args.magic)

@@ -149,7 +149,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   const long long nseg = ((p.nx + 31) / 32) * (long long)p.ny * p.nz;
   h->bulk_blocks = 152 * (h->prec == FSLBM_F64 ? 4 : 8);
   h->iface_blocks = 152 * 16;  // one thread per interface cell up to 311 296 cells per round
-  h->list_blocks = 152 * 2;
+  h->list_blocks = 152 * 8;  // 8 warps each: one warp per listed cell, 9728 cells per round
   h->red_blocks = 152;
   h->nparts = (h->bulk_blocks + h->iface_blocks) * 4;  // one partial per bulk and per interface warp
   if (h->nparts < 4096) h->nparts = 4096;

@@ -253,44 +253,30 @@ __global__ void __launch_bounds__(256) k_share(Par p, View<P> v) {
   }
 }
 
-// one warp per receiver: lane q (1..18) fetches the share of neighbour q;
-// lane 0 adds them in q order (deterministic, as a thread would)
+// one thread per receiver (the lists are long late in a run): gathers the
+// shares of its converting neighbours in q order (deterministic)
 template <int P>
 __global__ void __launch_bounds__(256) k_recv(Par p, View<P> v) {
   pdl_begin();
   using R = typename Form<P>::R;
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
   const int nr = min(load_count(&v.cnt[5]), v.cap);
-  const int q = (lane >= 1 && lane < 19) ? lane : 0;
-  for (int k = gw; k < nr; k += nw) {
+  const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
     const long long yj = v.rlist[k];
     int x, y, z;
     coords(p, yj, x, y, z);
-    bool has = false;
-    double sh = 0.0;
-    if (q) {
-      const long long j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (j >= 0 && (v.mark[j] & (MK_FILL | MK_EMPTY))) {
-        has = true;
-        sh = v.share[j];
-      }
-    }
-    const unsigned hm = __ballot_sync(FULL, has);
+    const bool in1 = x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1;
     double acc = 0.0;
 #pragma unroll
-    for (int l = 1; l < 19; ++l) {
-      const double t = __shfl_sync(FULL, sh, l);
-      if (hm & (1u << l)) acc += t;
+    for (int q = 1; q < 19; ++q) {
+      const long long j = in1 ? yj + (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, cx(q), cy(q), cz(q));
+      if (j < 0) continue;
+      if (v.mark[j] & (MK_FILL | MK_EMPTY)) acc += v.share[j];
     }
-    if (lane == 0) {
-      const double mm = v.m[yj] + acc;
-      v.m[yj] = mm;
-      const R r = rho_out<P>(p, v, yj);
-      v.phout[yj] = (R)(mm / (double)r);
-    }
+    const double mm = v.m[yj] + acc;
+    v.m[yj] = mm;
+    const R r = rho_out<P>(p, v, yj);
+    v.phout[yj] = (R)(mm / (double)r);
   }
 }
 

@@ -354,6 +354,57 @@ __device__ __forceinline__ R cube_area(R a, R m1, R m2, R m3) {
   return cube_area_half(a, m1, m2, m3);
 }
 
+// Inverse of cube_vol_half by region, for the float forms: with the sorted
+// normal (m1 <= m2 <= m3, sum 1) the volume is alpha^3 / (6 m1 m2 m3) on
+// [0, m1] (a cube root), a quadratic on [m1, m2] (a square root), linear on
+// [m1 + m2, m3] when m3 >= m1 + m2, and
+// cubic on the remaining ranges, where Newton iterations from a secant
+// start, kept inside the range, reach the float resolution.  tv in (0, 1/2].
+template <class R>
+__host__ __device__ __forceinline__ R cube_vol_r3(R a, R m1, R m2, R m3) {
+  const R s = a - m2;
+  return (R(3) * a * a - R(3) * a * m1 + m1 * m1 - s * s * s / m1) / (R(6) * m2 * m3);
+}
+template <class R>
+__host__ __device__ __forceinline__ R plic_alpha_regions(R tv, R m1, R m2, R m3) {
+  const R m12 = m1 + m2;
+  const R den = R(6) * m2 * m3;
+  if (m1 > R(0) && tv <= m1 * m1 / den) return cbrt(R(6) * m1 * m2 * m3 * tv);
+  if (m2 > R(0) && tv <= (R(3) * m2 * m2 - R(3) * m2 * m1 + m1 * m1) / den) {
+    const R t = R(2) * m2 * m3 * tv - m1 * m1 / R(12);
+    return R(0.5) * m1 + sqrt(t > R(0) ? t : R(0));
+  }
+  R lo = m2, hi, vlo, vhi;
+  bool four = false;  // the range [m3, 1/2] of a cube with m3 < m1 + m2
+  if (m3 >= m12) {
+    if (tv >= R(0.5) * m12 / m3) return m3 * tv + R(0.5) * m12;
+    hi = m12;
+    vhi = R(0.5) * m12 / m3;
+  } else {
+    const R v3 = cube_vol_r3(m3, m1, m2, m3);
+    if (tv <= v3) {
+      hi = m3;
+      vhi = v3;
+    } else {
+      four = true;
+      lo = m3;
+      hi = R(0.5);
+      vhi = R(0.5);
+    }
+  }
+  vlo = four ? cube_vol_r3(m3, m1, m2, m3) : (R(3) * m2 * m2 - R(3) * m2 * m1 + m1 * m1) / den;
+  R al = vhi > vlo ? lo + (hi - lo) * (tv - vlo) / (vhi - vlo) : hi;
+  for (int it = 0; it < 5; ++it) {
+    const R sa = al - m2, ra = four ? al - m3 : R(0);
+    const R v = (R(3) * al * al - R(3) * al * m1 + m1 * m1 - (sa * sa * sa + ra * ra * ra) / m1) / den;
+    const R dv = (R(6) * al - R(3) * m1 - R(3) * (sa * sa + ra * ra) / m1) / den;
+    if (!(dv > R(0))) break;
+    R nx = al - (v - tv) / dv;
+    al = nx < lo ? lo : (nx > hi ? hi : nx);
+  }
+  return al;
+}
+
 // Signed offset d (from the cell centre along the unit normal n, liquid on
 // the side n.(x - x_c) <= d) of the plane cutting volume fraction ph.  The
 // fill is kept in [1e-9, 1 - 1e-9] first: at an empty or full corner the
@@ -375,12 +426,14 @@ __device__ R plic_offset(R nx_, R ny_, R nz_, R ph) {
   // min(ph, 1 - ph), where it is convex
   const bool upper = ph > R(0.5);
   const R tv = upper ? R(1) - ph : ph;
+  if constexpr (sizeof(R) == 4) {
+    R al = plic_alpha_regions(tv, a0, a1, a2);
+    if (upper) al = R(1) - al;
+    return L1 * (al - R(0.5));
+  }
   R lo = R(0), hi = R(0.5);
-  // bracket to 2^-21 (FP64) or 2^-13 (FP32, where the Newton steps below then
-  // reach the float resolution); the fill clamp keeps the root above ~1e-3
-  constexpr int bisect = sizeof(R) == 8 ? 20 : 12;
 #pragma unroll 1
-  for (int it = 0; it < bisect; ++it) {
+  for (int it = 0; it < 20; ++it) {  // bracket to 2^-21
     R mid = R(0.5) * (lo + hi);
     if (cube_vol_half(mid, a0, a1, a2) < tv) lo = mid; else hi = mid;
   }

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);
   }
-  // per-warp partial sums (no block barrier), after the bulk warps' ones
+  // per-warp partial sums, after the bulk warps' ones
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
   if ((threadIdx.x & 31) == 0) v.partials[part_base + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5)] = msum;
