@@ -131,6 +131,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
     p.lam_m = -1.0 / (Lm + 0.5);
   }
   p.inv_1plp = 1.0 / (1.0 + p.lam_p);
+  p.inv_lam_m = 1.0 / p.lam_m;
   for (int a = 0; a < 3; ++a) p.g[a] = q.g[a];
   p.rho_G = q.rho_G;
   p.sigma = q.sigma;

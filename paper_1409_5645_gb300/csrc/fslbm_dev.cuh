@@ -98,6 +98,7 @@ struct Par {
   long long N;
   int px, py, pz, zshift;
   double lam_p, lam_m;     // TRT rates
+  double inv_lam_m;        // 1/lambda_-
   double inv_1plp;         // 1/(1 + lambda_+), recovers n^+ from f~
   double g[3];
   double rho_G, sigma, eps, delta_min;
@@ -241,13 +242,13 @@ __device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux,
     if (cz(q) == -1) jz = fx_sub(jz, f[q]);
   }
   const R r0 = p.compressible ? r : R(1);
-  const R ir0 = R(1) / r0;
+  const R ir0 = p.compressible ? R(1) / r0 : R(1);
   const R Ux = fx_mul(jx, ir0), Uy = fx_mul(jy, ir0), Uz = fx_mul(jz, ir0);
   const R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
   ux = fx_fma(R(0.5), gx, Ux);
   uy = fx_fma(R(0.5), gy, Uy);
   uz = fx_fma(R(0.5), gz, Uz);
-  const R ilm = R(1) / R(p.lam_m);
+  const R ilm = R(p.inv_lam_m);
   const R vx = fx_fma(-gx, ilm, Ux), vy = fx_fma(-gy, ilm, Uy), vz = fx_fma(-gz, ilm, Uz);
   const R usq = fx_fma(uz, uz, fx_fma(uy, uy, fx_mul(ux, ux)));
   const R lp = R(p.lam_p), lm = R(p.lam_m);
@@ -360,6 +361,16 @@ __device__ __forceinline__ R cube_area(R a, R m1, R m2, R m3) {
 // [m1 + m2, m3] when m3 >= m1 + m2, and
 // cubic on the remaining ranges, where Newton iterations from a secant
 // start, kept inside the range, reach the float resolution.  tv in (0, 1/2].
+// a / b: IEEE for double; for float on the device the fast approximate
+// division (2 ulp, the operands here are O(1)), which the float forms accept
+template <class R>
+__host__ __device__ __forceinline__ R qdiv(R a, R b) {
+#ifdef __CUDA_ARCH__
+  if constexpr (sizeof(R) == 4) return __fdividef(a, b);
+#endif
+  return a / b;
+}
+
 template <class R>
 __host__ __device__ __forceinline__ R cube_vol_r3(R a, R m1, R m2, R m3) {
   const R s = a - m2;
@@ -393,13 +404,15 @@ __host__ __device__ __forceinline__ R plic_alpha_regions(R tv, R m1, R m2, R m3)
     }
   }
   vlo = four ? cube_vol_r3(m3, m1, m2, m3) : (R(3) * m2 * m2 - R(3) * m2 * m1 + m1 * m1) / den;
-  R al = vhi > vlo ? lo + (hi - lo) * (tv - vlo) / (vhi - vlo) : hi;
+  R al = vhi > vlo ? lo + (hi - lo) * qdiv(tv - vlo, vhi - vlo) : hi;
+  // (the cubic ranges have m1 > 0)
+  const R im1 = qdiv(R(1), m1), iden = qdiv(R(1), den);
   for (int it = 0; it < 5; ++it) {
     const R sa = al - m2, ra = four ? al - m3 : R(0);
-    const R v = (R(3) * al * al - R(3) * al * m1 + m1 * m1 - (sa * sa * sa + ra * ra * ra) / m1) / den;
-    const R dv = (R(6) * al - R(3) * m1 - R(3) * (sa * sa + ra * ra) / m1) / den;
+    const R v = (R(3) * al * al - R(3) * al * m1 + m1 * m1 - (sa * sa * sa + ra * ra * ra) * im1) * iden;
+    const R dv = (R(6) * al - R(3) * m1 - R(3) * (sa * sa + ra * ra) * im1) * iden;
     if (!(dv > R(0))) break;
-    R nx = al - (v - tv) / dv;
+    R nx = al - qdiv(v - tv, dv);
     al = nx < lo ? lo : (nx > hi ? hi : nx);
   }
   return al;
@@ -481,7 +494,11 @@ struct Geo {
   R H[9];        // column heights H[(ib+1)*3 + (ic+1)]
 };
 
-template <class R, bool IN = false>
+// MODE 0: any cell (plain offsets when every stencil cell is inside the
+// lattice, else the general neighbour rule); 1: the caller knows every cell
+// within 3 is inside; 2: a lattice without periodic axes (a stencil cell past
+// a face is a wall: a bounds test per cell instead of the neighbour rule).
+template <class R, int MODE = 0>
 __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict__ flags,
                                          const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
   R (&n)[3] = G.n;
@@ -493,8 +510,7 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
   G.a = 2; G.b = 0; G.s = 1;
   // cells within 3 of the node are inside the lattice without a wrap: plain
   // offsets; otherwise the general neighbour rule
-  // (IN: the caller knows it)
-  const bool interior = IN || (x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3);
+  const bool interior = MODE == 1 || (x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3);
   const long long i0 = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
   // fill level seen by the geometry; the phi load is issued whatever the kind
   // so that all loads of the stencil are independent
@@ -506,6 +522,12 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
       const unsigned j = (unsigned)(i0i + dx + syi * dy + szi * dz);
       raw = phin[j];
       kj = (uint8_t)(flags[j] & KIND);
+    } else if (MODE == 2) {
+      const bool inside = (unsigned)(x + dx) < (unsigned)p.nx && (unsigned)(y + dy) < (unsigned)p.ny &&
+                          (unsigned)(z + dz) < (unsigned)p.nz;
+      const unsigned j = inside ? (unsigned)(i0i + dx + syi * dy + szi * dz) : 0u;
+      raw = inside ? phin[j] : R(0);
+      kj = inside ? (uint8_t)(flags[j] & KIND) : (uint8_t)WALL;
     } else {
       const long long j = nbr(p, x, y, z, dx, dy, dz);
       raw = j >= 0 ? phin[j] : R(0);
@@ -591,8 +613,13 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
     R v0 = (a == 0) ? R(s) : ((b == 0) ? -Hb : -Hc);
     R v1 = (a == 1) ? R(s) : ((b == 1) ? -Hb : -Hc);
     R v2 = (a == 2) ? R(s) : ((b == 2) ? -Hb : -Hc);
-    R len = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-    n[0] = v0 / len; n[1] = v1 / len; n[2] = v2 / len;
+    if constexpr (sizeof(R) == 4) {
+      const R il = rsqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+      n[0] = v0 * il; n[1] = v1 * il; n[2] = v2 * il;
+    } else {
+      R len = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+      n[0] = v0 / len; n[1] = v1 / len; n[2] = v2 / len;
+    }
     R nabs = fabs(a == 0 ? n[0] : (a == 1 ? n[1] : n[2]));
     d = nabs * (H[4] - R(3.5));
     if (p.sigma != 0.0) {
@@ -604,8 +631,13 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
       kap = -num / (q2 * sqrt(q2));
     }
   } else {
-    R len = sqrt(nn);
-    n[0] /= len; n[1] /= len; n[2] /= len;
+    if constexpr (sizeof(R) == 4) {
+      const R il = rsqrtf(nn);
+      n[0] *= il; n[1] *= il; n[2] *= il;
+    } else {
+      R len = sqrt(nn);
+      n[0] /= len; n[1] /= len; n[2] /= len;
+    }
     d = plic_offset<R>(n[0], n[1], n[2], phic);
   }
 }

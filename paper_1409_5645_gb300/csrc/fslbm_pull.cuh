@@ -57,9 +57,20 @@ __device__ __forceinline__ void pull_general(const Par& p, const View<P>& v, int
       else { gasm |= 1u << q; f[q] = 0; }
     }
   } else {
+    // a lattice without periodic axes: a source past a face is a wall
+    const bool bounded = !p.px && !p.py && !p.pz;
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
-      long long s = in1 ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
+      long long s;
+      if (in1) {
+        s = i - (cx(q) + sy * cy(q) + sz * cz(q));
+      } else if (bounded) {
+        const bool inside = (unsigned)(x - cx(q)) < (unsigned)p.nx && (unsigned)(y - cy(q)) < (unsigned)p.ny &&
+                            (unsigned)(z - cz(q)) < (unsigned)p.nz;
+        s = inside ? i - (cx(q) + sy * cy(q) + sz * cz(q)) : -1;
+      } else {
+        s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
+      }
       uint8_t ks = kind_at(v.flags, s);
       if (srcs) srcs[q] = (int)s;
       if (is_fluid(ks)) {

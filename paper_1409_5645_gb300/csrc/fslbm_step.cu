@@ -238,7 +238,7 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
         if (ok) {
           R cn = R(cx(pq)) * n[0] + R(cy(pq)) * n[1] + R(cz(pq)) * n[2];
           if (cn > R(0)) {
-            dl = d / cn;
+            dl = qdiv(d, cn);
             dl = dl < R(p.delta_min) ? R(p.delta_min) : (dl > R(1) ? R(1) : dl);
           }
         }
@@ -270,11 +270,11 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
 }
 
 // the geometry of cells within 3 of a face, out of line so that the
-// interior path of k_geom stays compact
-template <class R>
+// interior path of k_geom stays compact (bounded: no periodic axis)
+template <class R, bool BOUNDED>
 __device__ __noinline__ void geometry_edge(const Par& p, const uint8_t* __restrict__ flags,
                                            const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
-  geometry<R, false>(p, flags, phin, x, y, z, phic, G);
+  geometry<R, BOUNDED ? 2 : 0>(p, flags, phin, x, y, z, phic, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,12 +297,13 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
     R o[5];
     if (in3) {
       Geo<R> G;  // (in registers)
-      geometry<R, true>(p, v.flags, v.phin, x, y, z, phic, G);
+      geometry<R, 1>(p, v.flags, v.phin, x, y, z, phic, G);
       o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
       o[3] = G.d; o[4] = G.kap;
     } else {
       Geo<R> G;  // (in local memory: passed out of line)
-      geometry_edge<R>(p, v.flags, v.phin, x, y, z, phic, G);
+      if (!p.px && !p.py && !p.pz) geometry_edge<R, true>(p, v.flags, v.phin, x, y, z, phic, G);
+      else geometry_edge<R, false>(p, v.flags, v.phin, x, y, z, phic, G);
       o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
       o[3] = G.d; o[4] = G.kap;
     }
