@@ -535,7 +535,7 @@ extern "C" int fslbm_counters(fslbm_t* h, long long out[5]) {
   out[1] = c[7];
   out[2] = c[3];
   out[3] = c[4];
-  out[4] = c[0];
+  out[4] = c[0] + c[6];
   return rc;
 }
 

@@ -119,13 +119,14 @@ struct View {
   R* phout;
   const double* wd;  // wall link fractions (FP64 in every form)
   // lists and counters
-  int* ilist;   // interface cells of this step
+  int* ilist;   // interface cells of this step: interior from the front, edge cells from the back
   int* flist;   // fill
   int* elist;   // empty
   int* nglist;  // new from gas
   int* nllist;  // new from liquid
   int* rlist;   // excess receivers
-  int* cnt;     // [0] ilist [1] flist [2] elist [3] ng [4] nl [5] rl [7] emptied; [8] all conversions since set; [9] fluid segments
+  int* cnt;     // [0] ilist front [6] ilist back [1] flist [2] elist [3] ng [4] nl [5] rl [7] emptied;
+                // [8] all conversions since set; [9] fluid segments
   int cap;
   double* share;
   R* geo;            // interface geometry per list entry: [5][cap] n0, n1, n2, d, kappa (n = 0: none)

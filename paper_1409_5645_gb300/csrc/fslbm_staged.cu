@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     const long long i = rowstart + x;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
-    warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
+    append_iface(p, v, k == IFC, (int)i, x, y, z);
     R f[19];
     const bool fast = k == LIQ && !(fl & NEARB) && x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 &&
                       z < p.nz - 1;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
     const long long i = rowstart + x;
     const uint8_t fl = in ? (uint8_t)(sl[19 * 32] >> (8 * (int)(i & 3))) : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
-    warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
+    append_iface(p, v, k == IFC, (int)i, x, y, z);
     R f[19];
     const bool fast = k == LIQ && !(fl & NEARB) && x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 &&
                       z < p.nz - 1;

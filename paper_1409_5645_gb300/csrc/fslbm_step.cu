@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
     const long long i = (long long)sd.w + lane;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
-    warp_append(k == IFC, (int)i, v.ilist, &v.cnt[0], v.cap, v.err);
+    append_iface(p, v, k == IFC, (int)i, x, y, z);
     const size_t N = (size_t)p.N;
     R f[19];
     // Fast path: every source is a fluid cell at a plain offset, or lies beyond
@@ -286,14 +286,16 @@ template <int P>
 __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
   pdl_begin();
   using R = typename Form<P>::R;
-  const int count = min(*((volatile int*)&v.cnt[0]), v.cap);
+  const int n_in = min(*((volatile int*)&v.cnt[0]), v.cap), n_edge = min(*((volatile int*)&v.cnt[6]), v.cap);
+  const int count = min(n_in + n_edge, v.cap);
   const size_t cap = (size_t)v.cap;
   for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < count; li += gridDim.x * blockDim.x) {
-    const long long i = v.ilist[li];
+    const bool in3 = li < n_in;  // interior cells at the front, edge cells at the back
+    const int pos = in3 ? li : v.cap - 1 - (li - n_in);
+    const long long i = v.ilist[pos];
     int x, y, z;
     coords(p, i, x, y, z);
     const R phic = v.phin[i];
-    const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
     R o[5];
     if (in3) {
       Geo<R> G;  // (in registers)
@@ -308,14 +310,15 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
       o[3] = G.d; o[4] = G.kap;
     }
 #pragma unroll
-    for (int k = 0; k < 5; ++k) v.geo[k * cap + li] = o[k];
+    for (int k = 0; k < 5; ++k) v.geo[k * cap + pos] = o[k];
   }
 }
 
 template <int P>
 __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int part_base) {
   pdl_begin();
-  const int count = min(*((volatile int*)&v.cnt[0]), v.cap);
+  const int n_in = min(*((volatile int*)&v.cnt[0]), v.cap), n_edge = min(*((volatile int*)&v.cnt[6]), v.cap);
+  const int count = min(n_in + n_edge, v.cap);
   const int stride = gridDim.x * blockDim.x;
   const int rounds = (count + stride - 1) / stride;
   double msum = 0.0;
@@ -325,13 +328,14 @@ __global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P
     bool fill = false, empty = false;
     int icell = 0;
     if (act) {
-      const long long i = v.ilist[li];
+      const bool in3 = li < n_in;  // interior cells at the front, edge cells at the back
+      const int pos = in3 ? li : v.cap - 1 - (li - n_in);
+      const long long i = v.ilist[pos];
       icell = (int)i;
       int x, y, z;
       coords(p, i, x, y, z);
-      const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
-      msum += in3 ? iface_cell<P, true>(p, v, li, i, x, y, z, fill, empty)
-                  : iface_cell<P, false>(p, v, li, i, x, y, z, fill, empty);
+      msum += in3 ? iface_cell<P, true>(p, v, pos, i, x, y, z, fill, empty)
+                  : iface_cell<P, false>(p, v, pos, i, x, y, z, fill, empty);
     }
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);
