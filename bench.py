@@ -38,9 +38,9 @@ DIMS = (512, 256, 256)
 COL = (128, 192)
 TAU, MAGIC = 0.53, 0.005
 # kernels of one step: k_reset, k_segments, k_bulk, k_geom (FSL or surface
-# tension only), k_iface, 2 x k_reduce, 7 conversion kernels
+# tension only), k_iface, 2 x k_reduce, 5 conversion kernels
 def kernels_per_step(rule, sigma=0.0):
-    return 13 + (1 if (rule != 0 or sigma != 0.0) else 0)
+    return 11 + (1 if (rule != 0 or sigma != 0.0) else 0)
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 

@@ -16,7 +16,8 @@
 //   recv     each receiver gathers the shares of its converting neighbours in q
 //            order (deterministic, no floating-point atomics)
 //   final    F -> liquid, E -> gas, new cells -> interface, marks cleared
-// The result does not depend on list order.
+// newg and empty run in one launch, newl and share in another (each pair is
+// independent): five launches.  The result does not depend on list order.
 #include "fslbm_dev.cuh"
 #include "fslbm_kernels.h"
 
@@ -91,8 +92,7 @@ __global__ void __launch_bounds__(256) k_fill(Par p, View<P> v) {
 // one warp per new cell: lane l (1..18) reads neighbour l's populations; the
 // means are summed in neighbour order; lane q builds and collides population q
 template <int P>
-__global__ void __launch_bounds__(256) k_newg(Par p, View<P> v) {
-  pdl_begin();
+__device__ __forceinline__ void do_newg(const Par& p, const View<P>& v) {
   using R = typename Form<P>::R;
   const unsigned FULL = 0xffffffffu;
   const size_t N = (size_t)p.N;
@@ -164,8 +164,7 @@ __global__ void __launch_bounds__(256) k_newg(Par p, View<P> v) {
 
 // one warp per empty cell still marked, lane q (1..18) takes link q
 template <int P>
-__global__ void __launch_bounds__(256) k_empty(Par p, View<P> v) {
-  pdl_begin();
+__device__ __forceinline__ void do_empty(const Par& p, const View<P>& v) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -191,8 +190,7 @@ __global__ void __launch_bounds__(256) k_empty(Par p, View<P> v) {
 
 // liquid cells turned interface next to an emptied cell: m = rho, phi = m/rho
 template <int P>
-__global__ void k_newl(Par p, View<P> v) {
-  pdl_begin();
+__device__ __forceinline__ void do_newl(const Par& p, const View<P>& v) {
   using R = typename Form<P>::R;
   int nl = min(load_count(&v.cnt[4]), v.cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x) {
@@ -207,8 +205,7 @@ __global__ void k_newl(Par p, View<P> v) {
 // one warp per fill / empty cell: lane q (1..18) tests neighbour q as a
 // receiver; lane 0 computes the share (rho summed in q order, as a thread would)
 template <int P>
-__global__ void __launch_bounds__(256) k_share(Par p, View<P> v) {
-  pdl_begin();
+__device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -251,6 +248,22 @@ __global__ void __launch_bounds__(256) k_share(Par p, View<P> v) {
     }
     push(first, v.rlist, &v.cnt[5], v.cap, (int)j, v.err);
   }
+}
+
+// new cells from gas and the empty list are independent once the fill list is
+// processed, and so are new cells from liquid and the excess shares once the
+// empty list is: two launches instead of four
+template <int P>
+__global__ void __launch_bounds__(256) k_newg_empty(Par p, View<P> v) {
+  pdl_begin();
+  do_newg<P>(p, v);
+  do_empty<P>(p, v);
+}
+template <int P>
+__global__ void __launch_bounds__(256) k_newl_share(Par p, View<P> v) {
+  pdl_begin();
+  do_newl<P>(p, v);
+  do_share<P>(p, v);
 }
 
 // one thread per receiver (the lists are long late in a run): gathers the
@@ -335,7 +348,7 @@ __global__ void k_final(Par p, View<P> v) {
 
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks) {
-  void (*ks[7])(Par, View<P>) = {k_fill<P>, k_newg<P>, k_empty<P>, k_newl<P>, k_share<P>, k_recv<P>, k_final<P>};
+  void (*ks[5])(Par, View<P>) = {k_fill<P>, k_newg_empty<P>, k_newl_share<P>, k_recv<P>, k_final<P>};
   for (auto k : ks)
     if (launch_k(k, list_blocks, 256, 0, st, p, v)) return 1;
   return 0;
