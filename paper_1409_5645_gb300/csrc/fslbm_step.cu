@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, (P == P64 ? 1 : 6)) k_iface(Par p, View<P> v, int part_base) {
+__global__ void __launch_bounds__(128, (P == P64 ? 3 : 5)) k_iface(Par p, View<P> v, int part_base) {
   pdl_begin();
   const int n_in = min(*((volatile int*)&v.cnt[0]), v.cap), n_edge = min(*((volatile int*)&v.cnt[6]), v.cap);
   const int count = min(n_in + n_edge, v.cap);
