@@ -303,6 +303,7 @@ __global__ void k_final(Par p, View<P> v) {
   int total = nf + ne + ng + nl + nr;
   // running total of conversions since the state was set (never reset per step)
   if (blockIdx.x == 0 && threadIdx.x == 0 && nf + ng + nl) atomicAdd(&v.cnt[8], nf + ng + nl);
+  int emptied = 0;  // cells this thread turned to gas (counted once per warp below)
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     int kk = k;
     if (kk < nf) {
@@ -318,8 +319,7 @@ __global__ void k_final(Par p, View<P> v) {
         v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | GAS);
         v.phout[i] = R(0);
         v.mark[i] = 0;
-        atomicAdd(&v.cnt[7], 1);
-        atomicAdd(&v.cnt[8], 1);
+        ++emptied;
       }
       continue;
     }
@@ -339,6 +339,12 @@ __global__ void k_final(Par p, View<P> v) {
     }
     kk -= nl;
     v.mark[v.rlist[kk]] = 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emptied += __shfl_down_sync(0xffffffffu, emptied, o);
+  if ((threadIdx.x & 31) == 0 && emptied) {
+    atomicAdd(&v.cnt[7], emptied);
+    atomicAdd(&v.cnt[8], emptied);
   }
 }
 
