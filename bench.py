@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation workload")
+    ap.add_argument("--save-state", default=None, metavar="PREFIX",
+                    help="run --save-after steps of the workload (first form), save the state, exit")
+    ap.add_argument("--save-after", type=int, default=8000)
+    ap.add_argument("--load-state", default=None, metavar="PREFIX",
+                    help="time the first form from a state saved by --save-state (a late phase of the run)")
     ap.add_argument("--small", action="store_true", help="development size (128 x 64 x 64)")
     ap.add_argument("--dims", default=None, help="nx,ny,nz of a scaled dam break (profiling)")
     ap.add_argument("--tau", type=float, default=TAU)
@@ -203,15 +208,40 @@ def count_kinds(lat):
     return int(np.count_nonzero(fl == 1)), int(np.count_nonzero(fl == 2))
 
 
-def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False):
+def save_state(lat, prefix):
+    """Post-collision state of a lattice to prefix_{flags,f,m,phi}.npy (f as
+    float32: the FP32 form's own values)."""
+    import numpy as np
+    from paper_1409_5645_gb300 import fslbm
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = lat.get(fslbm.FIELD_FLAGS | fslbm.FIELD_F | fslbm.FIELD_MASS | fslbm.FIELD_PHI, device=dev)
+    np.save(prefix + "_flags.npy", st["flags"].cpu().numpy())
+    np.save(prefix + "_f.npy", st["f"].float().cpu().numpy())
+    np.save(prefix + "_m.npy", st["m"].cpu().numpy())
+    np.save(prefix + "_phi.npy", st["phi"].cpu().numpy())
+
+
+def load_state(lat, prefix, dev):
+    import numpy as np
+    import torch
+    t = {k: torch.from_numpy(np.load(prefix + "_" + k + ".npy")).to(dev) for k in ("flags", "f", "m", "phi")}
+    lat.set_state_post(t["flags"], t["f"].double(), t["m"], t["phi"])
+    del t
+
+
+def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False, state=None):
     import torch
     from paper_1409_5645_gb300 import fslbm
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     lat = fslbm.Lattice(case["dims"], case["params"], precision=form, stream=stream.cuda_stream)
-    t = {k: torch.from_numpy(case[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
-    lat.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
-    del t
+    if state:
+        load_state(lat, state, dev)
+    else:
+        t = {k: torch.from_numpy(case[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
+        lat.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
+        del t
     lat.step(warmup)
     lat.sync()
     M0, _ = lat.total_mass()
@@ -316,8 +346,21 @@ def main():
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     case = make_case(args)
     N = int(case["flags"].size)
+    if args.save_state:
+        from paper_1409_5645_gb300 import fslbm
+        dev = torch.device("cuda", local_rank)
+        lat = fslbm.Lattice(case["dims"], case["params"], precision=forms[0])
+        t = {k: torch.from_numpy(case[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
+        lat.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
+        del t
+        lat.step(args.save_after)
+        lat.sync()
+        save_state(lat, args.save_state)
+        print(json.dumps({"saved": args.save_state, "steps": args.save_after, "counters": lat.counters()}))
+        return 0
 
-    head = run_form(case, forms[0], args.steps, args.warmup, ws, rank, local_rank, clocks=True)
+    head = run_form(case, forms[0], args.steps, args.warmup, ws, rank, local_rank, clocks=True,
+                    state=args.load_state)
     ms_max = max_over_ranks(head["ms"], ws, torch.device("cuda", local_rank))
     value = ws * N * args.steps / (ms_max / 1e3) / 1e6
 
@@ -340,7 +383,8 @@ def main():
                    "dims": list(dims_for(args)), "rule": "FSL" if args.rule else "FSK", "tau": args.tau,
                    "magic": args.magic, "g": 1e-5,
                    "precision": forms[0], "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (populations %.1f GB)" % (N * 2 * 19 * s / 1e9)},
+                   "l2": "inputs larger than L2 (populations %.1f GB)" % (N * 2 * 19 * s / 1e9),
+                   "start": ("saved state " + args.load_state) if args.load_state else "initial column"},
         "mflups_active": round(ws * (head["n_liquid"] + head["n_interface"]) * args.steps
                                / (ms_max / 1e3) / 1e6, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

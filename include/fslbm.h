@@ -203,10 +203,11 @@ int fslbm_counters(fslbm_t *h, long long out[5]);
 int fslbm_timing(fslbm_t *h, int on);
 
 /* Average device time per step, in milliseconds, of each kernel group over
- * the steps taken with timing on: ms[0] bulk stream-collide (k_bulk),
- * ms[1] interface cells (k_iface), ms[2] mass-balance reduction, ms[3] the
- * conversion kernels; *steps receives the number of timed steps.
- * Synchronises. */
+ * the steps taken with timing on: ms[0] the bulk stream-collide kernel alone,
+ * ms[1] the interface kernels (geometry and interface cells), ms[2] the
+ * mass-balance reduction, ms[3] the conversion kernels (the counter reset and
+ * the fluid-segment scan are in no group); *steps receives the number of
+ * timed steps.  Synchronises. */
 int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
 
 /* ---- Differentiation: hand-written adjoint -------------------------------

@@ -388,7 +388,6 @@ template <int P>
 static int step_t(fslbm* h) {
   View<P> v = make_view<P>(h);
   if (launch_reset(h->cnt, h->st)) return 1;
-  if (mark_event(h, 0)) return 1;
   if (launch_step_kernels<P>(h->par, v, h->st, h->bulk_blocks, h->iface_blocks, h->seglist, h->cnt + 9,
                              h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr))
     return 1;
@@ -403,9 +402,9 @@ static int step_t(fslbm* h) {
   return 0;
 }
 
-// called between k_bulk and k_iface when timing is on
+// called around the bulk kernel when timing is on (events 0 and 1)
 namespace fsl {
-int fslbm_mark_between(void* hv) { return mark_event((fslbm*)hv, 1); }
+int fslbm_mark(void* hv, int k) { return mark_event((fslbm*)hv, k); }
 }  // namespace fsl
 
 extern "C" int fslbm_timing(fslbm_t* h, int on) {

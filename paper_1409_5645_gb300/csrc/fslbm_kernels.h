@@ -59,8 +59,8 @@ template <int P>
 int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
                       const int* segcount);
 
-// records the handle's between-kernel timing event (host side, fslbm_api.cu)
-int fslbm_mark_between(void* handle);
+// records timing event k of the handle's current step (host side, fslbm_api.cu)
+int fslbm_mark(void* handle, int k);
 
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks);

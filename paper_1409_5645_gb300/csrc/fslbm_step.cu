@@ -377,6 +377,7 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
                         const CUtensorMap* tmap) {
   const long long nseg = (long long)((p.nx + 31) / 32) * p.ny * p.nz;
   if (launch_k(k_segments, (unsigned)((nseg + 255) / 256), 256, 0, st, p, v.flags, seglist, segcount)) return 1;
+  if (timing_handle && fslbm_mark(timing_handle, 0)) return 1;  // the bulk group times the bulk kernel alone
   bool launched = false;
   if constexpr (P != P64) {
     if (bulk_mode == BULK_TMA && tmap) {
@@ -389,7 +390,7 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
   }
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
     return 1;
-  if (timing_handle && fslbm_mark_between(timing_handle)) return 1;
+  if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
   if ((p.rule != 0 || p.sigma != 0.0) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v)) return 1;
   // the interface partials follow the bulk warps' ones
   if (launch_k(k_iface<P>, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) return 1;
