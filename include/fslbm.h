@@ -123,6 +123,10 @@ typedef struct {
                          it recovers them by inverting the collision from the stored populations
                          (exact in FP64, limited by the storage precision in FP32/FP16) */
   double delta_min;   /* lower clamp of the free-surface link fraction, default 0 */
+  int stress;         /* 1: the boundary shear-rate term D c_a c_b S^b_ab of Eq. bterm on every
+                         rebuilt gas link (D of Table 1; S extrapolated from the cell's own
+                         non-equilibrium part, its normal-tangential components set to zero in
+                         the interface basis, Eq. bstress / Eq. proj2); 0 (default): D = 0 */
   int bulk_loads;     /* fslbm_loads: how the bulk kernel of FP32/FP16 lattices reaches the
                          pulled values (FP64 always loads them plainly); same results every way */
   int precision;      /* fslbm_precision */
@@ -216,7 +220,7 @@ int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
  * is included) through nsteps time steps to an objective J, at fixed cell
  * flags: every discrete decision of the forward pass (flags, the height-
  * function or plane-fit branch, the dominant axis, clamps of delta) is held.
- * Supported: rho_0 = 1, sigma = 0, and no cell conversion inside the window
+ * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), and no cell conversion inside the window
  * (FSLBM_ERR_STATE otherwise).  Parameters: nu = (tau - 1/2)/3 with the magic
  * parameter Lambda held fixed, g, and the initial fill levels phi0 of
  * interface cells (m0 = phi0 rho0). */

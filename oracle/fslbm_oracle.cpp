@@ -124,6 +124,8 @@ struct Params {
   int freeze;        // 1 = fixed flags and fill levels (no mass exchange, no conversion)
   int cleanup;       // bit 1: no gas neighbour -> fill; bit 2: no fluid neighbour -> empty
   double delta_min;  // lower clamp of the free-surface link fraction (0: FSL needs delta >= 0)
+  int stress;        // 1: boundary shear-rate term D c_a c_b S^b_ab of Eq. bterm (Table 1's D, S^b per
+                     //    Eq. bstress); 0: D = 0
 };
 
 template <class T>
@@ -645,15 +647,57 @@ struct Sim {
     T eb = e_plus(pq, rb, ub, rho0(rb));
     T ftp = ft[(size_t)pq * NN + i];
     long up = nbq(i, pq, -1);  // x_b - c_p
-    if (p.rule == 0 || !fluid(type(up))) return T(-1.0) * ftp + T(2.0) * eb;
+    if (p.rule == 0 || !fluid(type(up))) {
+      T fq = T(-1.0) * ftp + T(2.0) * eb;
+      if (p.stress) fq = fq + stress_term(i, pq, 2.0);
+      return fq;
+    }
     T n[3] = {gn[3 * i], gn[3 * i + 1], gn[3 * i + 2]};
     T dl = link_delta(pq, n, gd[i], gok[i] != 0);
     T a0 = T(0.5) - dl;
     T ab0 = T(0.5);
     T a1 = dl - T(1.0);
     T C = lam_p * (T(0.5) + dl) - T(2.0) * lam_p;
-    return a0 * ftp + ab0 * ft[(size_t)q * NN + i] + a1 * ft[(size_t)pq * NN + up] +
+    T fq = a0 * ftp + ab0 * ft[(size_t)q * NN + i] + a1 * ft[(size_t)pq * NN + up] +
            C * nplus[(size_t)pq * NN + i] + eb;
+    if (p.stress) fq = fq + stress_term(i, pq, 1.0);
+    return fq;
+  }
+
+  // Boundary shear-rate term of Eq. bterm for the gas link p of interface
+  // cell i: D c_p,a c_p,b S^b_ab with D = -alpha_+ Lambda_+ w_p / c_s^2
+  // (Table 1: alpha_+ = 2 FSK, 1 FSL; Lambda_+ = tau - 1/2).  S is extrapolated
+  // from the cell's own non-equilibrium part (the leading order of Eq. nqp,
+  // incompressible: sum_q c_qa c_qb n_q^+ = (2 c_s^2 / lambda_+) S_ab), and
+  // S^b is S with its normal-tangential components set to zero in the basis of
+  // the interface normal n (Eq. proj2 through Eq. bstress), the others kept:
+  //   S^b = S - (S n) n^T - n (S n)^T + 2 (n.S.n) n n^T.
+  // Without a normal, S^b = S.
+  T stress_term(long i, int pq, double alpha) const {
+    const long NN = N;
+    T S[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) S[a][b] = T(0);
+    for (int q = 1; q < Q; ++q) {
+      const T np = nplus[(size_t)q * NN + i];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[a][b] += T(CV[q][a] * CV[q][b]) * np;
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) S[a][b] = T(1.5) * lam_p * S[a][b];
+    if (gok[i]) {
+      const T n[3] = {gn[3 * i], gn[3 * i + 1], gn[3 * i + 2]};
+      T Sn[3];
+      for (int a = 0; a < 3; ++a) Sn[a] = S[a][0] * n[0] + S[a][1] * n[1] + S[a][2] * n[2];
+      const T snn = n[0] * Sn[0] + n[1] * Sn[1] + n[2] * Sn[2];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[a][b] = S[a][b] - Sn[a] * n[b] - n[a] * Sn[b] + T(2.0) * snn * n[a] * n[b];
+    }
+    T ccS = T(0);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) ccS += T(CV[pq][a] * CV[pq][b]) * S[a][b];
+    const double Lp = p.tau - 0.5;
+    return T(-alpha * Lp * 3.0 * w[pq]) * ccS;
   }
 
   // Cell conversions after the mass update (reading of Koerner et al. /

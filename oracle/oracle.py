@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int),
                 ("compressible", C.c_int), ("linear_eq", C.c_int), ("eps", C.c_double),
                 ("periodic", C.c_int * 3), ("zshift", C.c_int), ("freeze", C.c_int),
-                ("cleanup", C.c_int), ("delta_min", C.c_double)]
+                ("cleanup", C.c_int), ("delta_min", C.c_double), ("stress", C.c_int)]
 
 
 def lib():
@@ -108,6 +108,7 @@ def make_params(dims, p) -> Params:
     P.freeze = int(p["freeze"])
     P.cleanup = int(p.get("cleanup", 3))
     P.delta_min = p["delta_min"]
+    P.stress = int(p.get("stress", 0))
     return P
 
 

@@ -62,7 +62,7 @@ def uniform(seed: int, count: int, amp: float, offset: int = 0) -> np.ndarray:
 def default_params(**kw) -> dict:
     p = dict(tau=0.8, magic=3.0 / 16.0, g=(0.0, 0.0, 0.0), rho_G=1.0, sigma=0.0,
              rule=1, compressible=0, linear_eq=0, eps=1e-3,
-             periodic=(0, 0, 0), zshift=0, freeze=0, cleanup=3, delta_min=0.0)
+             periodic=(0, 0, 0), zshift=0, freeze=0, cleanup=3, delta_min=0.0, stress=0)
     p.update(kw)
     return p
 

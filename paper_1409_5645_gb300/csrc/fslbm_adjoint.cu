@@ -638,6 +638,7 @@ extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objectiv
   if (!h || nsteps < 1 || K < 1 || (objective != 0 && objective != 1)) return FSLBM_ERR_ARG;
   if (h->par.compressible) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs rho_0 = 1");
   if (h->par.sigma != 0.0) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs sigma = 0");
+  if (h->par.stress) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs D = 0 (no boundary shear term)");
   fslbm_free_adjoint(h);
   AdjointState* A = new AdjointState();
   h->adj = A;

@@ -142,6 +142,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   p.linear_eq = q.linear_eq != 0;
   p.freeze = q.freeze != 0;
   p.cleanup = q.cleanup;
+  p.stress = q.stress != 0;
+  p.tau_m_half = q.tau - 0.5;
   p.has_wd = 0;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;

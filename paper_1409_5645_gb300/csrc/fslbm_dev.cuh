@@ -103,6 +103,8 @@ struct Par {
   double g[3];
   double rho_G, sigma, eps, delta_min;
   int rule, compressible, linear_eq, freeze, cleanup;
+  int stress;              // boundary shear-rate term of Eq. bterm (D != 0)
+  double tau_m_half;       // Lambda_+ = tau - 1/2
   int has_wd;
 };
 

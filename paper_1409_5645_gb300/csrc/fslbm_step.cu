@@ -208,9 +208,10 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
   }
   if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
   if (gasm) {
-    // the plane and curvature of k_geom (FSK without surface tension needs neither)
+    // the plane and curvature of k_geom (FSK without surface tension or the
+    // boundary shear term needs neither)
     R n[3] = {R(0), R(0), R(0)}, d = R(0), kap = R(0);
-    if (p.rule != 0 || p.sigma != 0.0) {
+    if (p.rule != 0 || p.sigma != 0.0 || p.stress) {
       const size_t cap = (size_t)v.cap;
       n[0] = v.geo[li];
       n[1] = v.geo[cap + li];
@@ -225,14 +226,50 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     const R r0t = p.compressible ? rt : R(1);
     const R usq = utx * utx + uty * uty + utz * utz;
     const R lp = R(p.lam_p);
+    // boundary shear rate S^b of Eq. bterm (stress mode): S from the cell's
+    // own non-equilibrium part, sum_q c_qa c_qb n_q^+ = (2 c_s^2 / lambda_+) S_ab
+    // (leading order of Eq. nqp), with its normal-tangential components set to
+    // zero in the basis of the normal (Eq. proj2 through Eq. bstress):
+    // S^b = S - (S n) n^T - n (S n)^T + 2 (n.S.n) n n^T
+    R Sb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};  // xx yy zz xy xz yz
+    if (p.stress) {
+#pragma unroll
+      for (int q = 1; q < 19; q += 2) {  // each pair once: n_q^+ = n_qbar^+
+        const R et = eplus_q<R>(p, q, rt, r0t, utx, uty, utz, usq);
+        const R np2 = R(2) * (R(0.5) * (own[q] + own[q + 1]) - et) * R(p.inv_1plp);
+        Sb[0] += R(cx(q) * cx(q)) * np2; Sb[1] += R(cy(q) * cy(q)) * np2; Sb[2] += R(cz(q) * cz(q)) * np2;
+        Sb[3] += R(cx(q) * cy(q)) * np2; Sb[4] += R(cx(q) * cz(q)) * np2; Sb[5] += R(cy(q) * cz(q)) * np2;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Sb[k] *= R(1.5) * lp;
+      const R Sn0 = Sb[0] * n[0] + Sb[3] * n[1] + Sb[4] * n[2];
+      const R Sn1 = Sb[3] * n[0] + Sb[1] * n[1] + Sb[5] * n[2];
+      const R Sn2 = Sb[4] * n[0] + Sb[5] * n[1] + Sb[2] * n[2];
+      const R snn = n[0] * Sn0 + n[1] * Sn1 + n[2] * Sn2;
+      Sb[0] += R(2) * (snn * n[0] * n[0] - Sn0 * n[0]);
+      Sb[1] += R(2) * (snn * n[1] * n[1] - Sn1 * n[1]);
+      Sb[2] += R(2) * (snn * n[2] * n[2] - Sn2 * n[2]);
+      Sb[3] += R(2) * snn * n[0] * n[1] - Sn0 * n[1] - n[0] * Sn1;
+      Sb[4] += R(2) * snn * n[0] * n[2] - Sn0 * n[2] - n[0] * Sn2;
+      Sb[5] += R(2) * snn * n[1] * n[2] - Sn1 * n[2] - n[1] * Sn2;
+    }
+    const R Dk = R(-3.0 * (p.tau_m_half));  // D = -alpha_+ Lambda_+ w_p / c_s^2, without alpha_+ w_p
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
       if (!(gasm & (1u << q))) continue;
       const int pq = inv(q);  // boundary link: x + c_p is gas, missing f_pbar = f_q
       R eb = eplus_q<R>(p, pq, rb, r0b, utx, uty, utz, usq);
       bool up_fluid = !((wallm | gasm) & (1u << pq));
+      // D c_p.S^b.c_p / alpha_+ (Eq. bterm, Table 1)
+      R dterm = R(0);
+      if (p.stress) {
+        const R cSc = R(cx(pq) * cx(pq)) * Sb[0] + R(cy(pq) * cy(pq)) * Sb[1] + R(cz(pq) * cz(pq)) * Sb[2] +
+                      R(2 * cx(pq) * cy(pq)) * Sb[3] + R(2 * cx(pq) * cz(pq)) * Sb[4] +
+                      R(2 * cy(pq) * cz(pq)) * Sb[5];
+        dterm = Dk * wq<R>(pq) * cSc;
+      }
       if (p.rule == 0 || !up_fluid) {
-        f[q] = -own[pq] + R(2) * eb;  // FSK, Eq. koerner
+        f[q] = -own[pq] + R(2) * eb + R(2) * dterm;  // FSK, Eq. koerner (alpha_+ = 2)
       } else {
         R dl = R(0.5);
         if (ok) {
@@ -245,7 +282,7 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
         R et = eplus_q<R>(p, pq, rt, r0t, utx, uty, utz, usq);
         R nplus = (R(0.5) * (own[pq] + own[q]) - et) * R(p.inv_1plp);
         R C = lp * (R(0.5) + dl) - R(2) * lp;
-        f[q] = (R(0.5) - dl) * own[pq] + R(0.5) * own[q] + (dl - R(1)) * f[pq] + C * nplus + eb;
+        f[q] = (R(0.5) - dl) * own[pq] + R(0.5) * own[q] + (dl - R(1)) * f[pq] + C * nplus + eb + dterm;
       }
     }
   }
@@ -391,7 +428,7 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
     return 1;
   if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
-  if ((p.rule != 0 || p.sigma != 0.0) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v)) return 1;
+  if ((p.rule != 0 || p.sigma != 0.0 || p.stress) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v)) return 1;
   // the interface partials follow the bulk warps' ones
   if (launch_k(k_iface<P>, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) return 1;
   return (int)cudaGetLastError();

@@ -38,7 +38,7 @@ class Params(C.Structure):
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int), ("compressible", C.c_int),
                 ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
                 ("freeze", C.c_int), ("cleanup", C.c_int), ("keep_f0", C.c_int), ("delta_min", C.c_double),
-                ("bulk_loads", C.c_int), ("precision", C.c_int),
+                ("stress", C.c_int), ("bulk_loads", C.c_int), ("precision", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -146,6 +146,7 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.cleanup = int(params.get("cleanup", P.cleanup))
     P.keep_f0 = int(params.get("keep_f0", 0))
     P.delta_min = params.get("delta_min", P.delta_min)
+    P.stress = int(params.get("stress", 0))
     P.bulk_loads = LOADS[params.get("bulk_loads", "plain")]
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream

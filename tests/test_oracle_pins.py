@@ -449,3 +449,84 @@ def test_tangent_linear_matches_central_differences():
     pm[k] -= h
     fd = (J_fd(phi=pp) - J_fd(phi=pm)) / (2 * h)
     assert t_phi == pytest.approx(fd, rel=2e-3)
+
+
+def _extensional_state(a=1e-3, dims=(12, 12, 10), h_if=5, fill=0.6, tau=0.8):
+    """Steady linear extensional flow u = (a x', -a y', 0) under a flat free
+    surface (interface layer z = h_if, normal along z, so the normal-tangential
+    shear rates vanish and S = diag(a, -a, 0)).  With the linear equilibrium and
+    no force the Chapman-Enskog solution (Eq. ce / Eq. nqp, Eq. nqm) terminates:
+    f_q = w_q rho + 3 w_q c_q.u + (3 w_q / lambda_+) c_q.G.c_q, an exact fixed
+    point of the bulk update."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    i = np.arange(N)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    flags = np.where(z < h_if, cases.LIQUID, np.where(z == h_if, cases.INTERFACE, cases.GAS)).astype(np.uint8)
+    phi = np.where(z == h_if, fill, 0.0)
+    xc, yc = (nx - 1) / 2, (ny - 1) / 2
+    u = np.stack([a * (x - xc), -a * (y - yc), np.zeros(N)], axis=1)
+    G = np.diag([a, -a, 0.0])
+    lam_p = -1.0 / tau
+    c = cases.LINKS.astype(np.float64)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    cu = u @ c.T                                       # (N, 19)
+    cGc = np.einsum("qa,ab,qb->q", c, G, c)            # (19,)
+    f = (w[None, :] * (1.0 + 3.0 * cu) + (3.0 * w * cGc / lam_p)[None, :]).T.copy()
+    params = cases.default_params(tau=tau, rule=1, linear_eq=1, freeze=1, periodic=(0, 0, 0))
+    return dims, params, flags, f, phi, (x, y, z)
+
+
+@pytest.mark.parametrize("rule", [1, 0])
+def test_stress_term_exact_for_linear_extensional_flow(rule):
+    """With the boundary shear-rate term (Eq. bterm, D of Table 1, S^b from
+    Eq. bstress) the free-surface closure reproduces the steady linear flow
+    exactly; with D = 0 the tangential shear rates are forced to zero and the
+    rebuilt populations are off by D c.S.c (checked against its value)."""
+    dims, params, flags, f, phi, (x, y, z) = _extensional_state()
+    params["rule"] = rule
+    nx, ny, nz = dims
+    inner = (flags == cases.INTERFACE) & (x >= 2) & (x < nx - 2) & (y >= 2) & (y < ny - 2)
+    errs = {}
+    for stress in (1, 0):
+        o = Oracle(dims, dict(params, stress=stress))
+        o.set_state(flags, f, phi)
+        o.step(1)
+        f1 = o.get(F_PRE)
+        errs[stress] = np.abs(f1[:, inner] - f[:, inner]).max()
+    assert errs[1] < 1e-14, errs
+    # D = 0: the error on a gas link p is -D c_p.S.c_p = alpha_+ (tau - 1/2) 3 w_p a (c_px^2 - c_py^2);
+    # the gas links of a surface with normal z are (+-1, 0, 1) and (0, +-1, 1), w_p = 1/36
+    alpha = 1.0 if rule == 1 else 2.0
+    expect = alpha * (0.8 - 0.5) * 3.0 / 36.0 * 1e-3
+    assert errs[0] == pytest.approx(expect, rel=1e-6), (errs, expect)
+
+
+def test_stress_term_projection_zeroes_normal_tangential_shear():
+    """A shear u_x = b z' under the flat surface (S_xz = b/2) violates the
+    tangential condition Eq. proj2; the boundary term keeps S^b_xz = 0 (Eq.
+    bstress), so the rebuilt population on a gas link (c_x, 0, 1) differs from
+    the steady field by D c.(S^b - S).c = 6 alpha_+ Lambda_+ w c_x S_xz."""
+    b = 1e-3
+    dims, params, flags, _, phi, (x, y, z) = _extensional_state()
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    u = np.stack([b * (z - 2.0), np.zeros(N), np.zeros(N)], axis=1)
+    G = np.zeros((3, 3)); G[2, 0] = b                    # d_z u_x
+    c = cases.LINKS.astype(np.float64)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    f = (w[None, :] * (1.0 + 3.0 * (u @ c.T)) + (3.0 * w * np.einsum("qa,ab,qb->q", c, G, c) / (-1.0 / 0.8))[None, :]).T.copy()
+    o = Oracle(dims, dict(params, stress=1))
+    o.set_state(flags, f, phi)
+    o.step(1)
+    f1 = o.get(F_PRE)
+    inner = (flags == cases.INTERFACE) & (x >= 2) & (x < nx - 2) & (y >= 2) & (y < ny - 2)
+    Lp = 0.8 - 0.5
+    for q in range(1, 19):
+        cq = cases.LINKS[q]
+        if cq[2] != -1:          # populations arriving from the gas above: c_q = -c_p with c_p,z = +1
+            continue
+        cp = -cq
+        d = f1[q, inner] - f[q, inner]
+        expect = 6.0 * 1.0 * Lp * w[q] * cp[0] * (b / 2.0)
+        assert np.allclose(d, expect, rtol=1e-9, atol=1e-15), (q, d[:3], expect)
