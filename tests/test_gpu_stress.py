@@ -43,7 +43,7 @@ def _extensional(a=1e-3, dims=(40, 40, 12), h_if=6, fill=0.6, tau=0.8):
     return dims, params, flags, np.ascontiguousarray(f), phi, (x, y, z)
 
 
-@pytest.mark.parametrize("precision,tol", [("f64", 1e-14), ("f32", 2e-7)])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-14), ("f32", 1e-6)])
 def test_stress_exact_for_linear_extensional_flow(precision, tol):
     """Steady u = (a x', -a y', 0) under a flat surface is a fixed point of the
     step with the boundary shear term (checked on the interface layer away
