@@ -126,7 +126,12 @@ typedef struct {
   int stress;         /* 1: the boundary shear-rate term D c_a c_b S^b_ab of Eq. bterm on every
                          rebuilt gas link (D of Table 1; S extrapolated from the cell's own
                          non-equilibrium part, its normal-tangential components set to zero in
-                         the interface basis, Eq. bstress / Eq. proj2); 0 (default): D = 0 */
+                         the interface basis, Eq. bstress / Eq. proj2); 2: the same term with the
+                         prescribed S^b of shear_b (Sec. 6, linear Couette flows); 0 (default):
+                         D = 0 */
+  double shear_b[6];  /* prescribed S^b for stress = 2: xx, yy, zz, xy, xz, yz */
+  double wall_u[3];   /* velocity of every wall: half-way bounce-back links get
+                         + 6 w_q (c_q.u_w) (rho_0 = 1; not with compressible, not on CLI links) */
   int bulk_loads;     /* fslbm_loads: how the bulk kernel of FP32/FP16 lattices reaches the
                          pulled values (FP64 always loads them plainly); same results every way */
   int precision;      /* fslbm_precision */

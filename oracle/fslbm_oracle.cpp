@@ -125,7 +125,10 @@ struct Params {
   int cleanup;       // bit 1: no gas neighbour -> fill; bit 2: no fluid neighbour -> empty
   double delta_min;  // lower clamp of the free-surface link fraction (0: FSL needs delta >= 0)
   int stress;        // 1: boundary shear-rate term D c_a c_b S^b_ab of Eq. bterm (Table 1's D, S^b per
-                     //    Eq. bstress); 0: D = 0
+                     //    Eq. bstress); 2: the same term with the prescribed S^b below (Sec. 6,
+                     //    linear Couette flows); 0: D = 0
+  double shear_b[6]; // prescribed S^b: xx, yy, zz, xy, xz, yz (stress = 2)
+  double wall_u[3];  // velocity of every wall (half-way bounce-back links; rho_0 = 1)
 };
 
 template <class T>
@@ -618,7 +621,13 @@ struct Sim {
     const long NN = N;
     int pq = opp[q];
     T bb = ft[(size_t)pq * NN + i];
-    if (wdelta.empty()) return bb;
+    if (wdelta.empty()) {
+      // a moving wall adds -2 w_p rho_0 (c_p.u_w)/c_s^2 = 6 w_q (c_q.u_w) for the
+      // link arriving from it (c_q = -c_p), rho_0 = 1
+      const double cu = CV[q][0] * p.wall_u[0] + CV[q][1] * p.wall_u[1] + CV[q][2] * p.wall_u[2];
+      if (cu != 0.0) bb = bb + T(6.0 * w[q] * cu);
+      return bb;
+    }
     double dw = wdelta[(size_t)pq * NN + i];
     if (!(dw >= 0.0)) return bb;
     long up = nbq(i, pq, -1);  // x - c_p
@@ -676,6 +685,14 @@ struct Sim {
   T stress_term(long i, int pq, double alpha) const {
     const long NN = N;
     T S[3][3];
+    if (p.stress == 2) {  // prescribed S^b
+      const double* s6 = p.shear_b;
+      const double Sp[3][3] = {{s6[0], s6[3], s6[4]}, {s6[3], s6[1], s6[5]}, {s6[4], s6[5], s6[2]}};
+      T ccS = T(0);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) ccS += T(CV[pq][a] * CV[pq][b] * Sp[a][b]);
+      return T(-alpha * (p.tau - 0.5) * 3.0 * w[pq]) * ccS;
+    }
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) S[a][b] = T(0);
     for (int q = 1; q < Q; ++q) {

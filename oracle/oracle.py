@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int),
                 ("compressible", C.c_int), ("linear_eq", C.c_int), ("eps", C.c_double),
                 ("periodic", C.c_int * 3), ("zshift", C.c_int), ("freeze", C.c_int),
-                ("cleanup", C.c_int), ("delta_min", C.c_double), ("stress", C.c_int)]
+                ("cleanup", C.c_int), ("delta_min", C.c_double), ("stress", C.c_int),
+                ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3)]
 
 
 def lib():
@@ -109,6 +110,10 @@ def make_params(dims, p) -> Params:
     P.cleanup = int(p.get("cleanup", 3))
     P.delta_min = p["delta_min"]
     P.stress = int(p.get("stress", 0))
+    for k, v in enumerate(p.get("shear_b", (0.0,) * 6)):
+        P.shear_b[k] = float(v)
+    for k, v in enumerate(p.get("wall_u", (0.0,) * 3)):
+        P.wall_u[k] = float(v)
     return P
 
 

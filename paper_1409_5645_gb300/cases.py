@@ -315,3 +315,51 @@ def adjoint_film(**kw) -> Case:
     args = dict(nx=8, ny=4, nz=64, h=40.0)
     args.update(kw)
     return film(**args)
+
+
+def plate_flow(h=8, tau=1.0, rule=0, u_wall=1e-3, magic=0.25, headroom=3, **kw) -> Case:
+    """Plate-driven planar flow (Sec. 6, transient): x, y periodic, the wall at
+    the bottom face moves along x with u_wall, a flat free surface h cells
+    above it (interface layer z = h - 1 with fill 1, frozen), at rest at t = 0.
+    (The paper puts the surface below and the wall above; the mirror image.)"""
+    nx, ny, nz = 2, 2, h + headroom
+    dims = (nx, ny, nz)
+    N = nx * ny * nz
+    z = np.arange(N) // (nx * ny)
+    phi = np.where(z < h, 1.0, 0.0)
+    params = default_params(tau=tau, magic=magic, rule=rule, periodic=(1, 1, 0), freeze=1,
+                            wall_u=(u_wall, 0.0, 0.0))
+    params.update(kw)
+    flags = np.where(z < h - 1, LIQUID, np.where(z == h - 1, INTERFACE, GAS)).astype(np.uint8)
+    return Case(dims=dims, params=params, flags=flags, rho=np.ones(N), u=np.zeros((N, 3)),
+                phi=np.where(flags == INTERFACE, 1.0, 0.0), noise=None, wall_delta=None, h=h, u_wall=u_wall)
+
+
+def plate_flow_exact(zc, t, h, nu, u_wall, terms=400):
+    """Fourier series of the plate-driven flow (the paper's transient formula):
+    u / u_wall = 1 - sum_k 4 (-1)^k / ((2k+1) pi) exp(-(2k+1)^2 pi^2 nu t / (4 h^2))
+    cos((2k+1) pi s / (2h)), s the distance from the free surface."""
+    s = h - np.asarray(zc, dtype=np.float64)
+    out = np.ones_like(s)
+    for k in range(terms):
+        m = 2 * k + 1
+        out -= 4.0 * (-1) ** k / (m * math.pi) * math.exp(-(m * math.pi) ** 2 * nu * t / (4.0 * h * h)) * \
+            np.cos(m * math.pi * s / (2.0 * h))
+    return u_wall * out
+
+
+def couette(h=8, tau=1.1, rule=1, shear=1e-3, headroom=3, **kw) -> Case:
+    """Linear Couette flow driven by a prescribed shear rate at the free surface
+    (Sec. 6): x, y periodic, resting bounce-back wall at the bottom face, flat
+    surface h cells above (interface layer z = h - 1, fill 1, frozen), S^b_xz =
+    shear prescribed, at rest at t = 0; steady u_x = 2 shear (z + 1/2)."""
+    nx, ny, nz = 2, 2, h + headroom
+    dims = (nx, ny, nz)
+    N = nx * ny * nz
+    z = np.arange(N) // (nx * ny)
+    params = default_params(tau=tau, rule=rule, periodic=(1, 1, 0), freeze=1, stress=2,
+                            shear_b=(0.0, 0.0, 0.0, 0.0, shear, 0.0))
+    params.update(kw)
+    flags = np.where(z < h - 1, LIQUID, np.where(z == h - 1, INTERFACE, GAS)).astype(np.uint8)
+    return Case(dims=dims, params=params, flags=flags, rho=np.ones(N), u=np.zeros((N, 3)),
+                phi=np.where(flags == INTERFACE, 1.0, 0.0), noise=None, wall_delta=None, h=h, shear=shear)

@@ -104,6 +104,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   if (N >= (1LL << 31)) return FSLBM_ERR_ARG;
   if (q.precision == FSLBM_F16 && q.compressible) return FSLBM_ERR_ARG;
   if (q.bulk_loads < FSLBM_LOADS_PLAIN || q.bulk_loads > FSLBM_LOADS_TMA) return FSLBM_ERR_ARG;
+  if (q.stress < 0 || q.stress > 2) return FSLBM_ERR_ARG;
+  if (q.compressible && (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0)) return FSLBM_ERR_ARG;
 
   fslbm* h = (fslbm*)calloc(1, sizeof(fslbm));
   if (!h) return FSLBM_ERR_OOM;
@@ -142,8 +144,11 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   p.linear_eq = q.linear_eq != 0;
   p.freeze = q.freeze != 0;
   p.cleanup = q.cleanup;
-  p.stress = q.stress != 0;
+  p.stress = q.stress;
   p.tau_m_half = q.tau - 0.5;
+  for (int k = 0; k < 6; ++k) p.shear_b[k] = q.shear_b[k];
+  for (int a = 0; a < 3; ++a) p.wall_u[a] = q.wall_u[a];
+  p.has_uw = (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0) ? 1 : 0;
   p.has_wd = 0;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;

@@ -103,8 +103,11 @@ struct Par {
   double g[3];
   double rho_G, sigma, eps, delta_min;
   int rule, compressible, linear_eq, freeze, cleanup;
-  int stress;              // boundary shear-rate term of Eq. bterm (D != 0)
+  int stress;              // boundary shear-rate term of Eq. bterm: 0 off, 1 extrapolated S^b, 2 prescribed
   double tau_m_half;       // Lambda_+ = tau - 1/2
+  double shear_b[6];       // prescribed S^b (xx yy zz xy xz yz)
+  double wall_u[3];        // wall velocity
+  int has_uw;              // a wall velocity is set
   int has_wd;
 };
 

@@ -133,6 +133,10 @@ __device__ __forceinline__ void wall_links(const Par& p, const View<P>& v, long 
         R kap = (R(1) - R(2) * dw) / (R(1) + R(2) * dw);
         val = val + kap * (f[pq] - own[q]);
       }
+    } else if (p.has_uw) {
+      // moving wall (half-way bounce-back): + 6 w_q rho_0 (c_q.u_w), rho_0 = 1
+      val = val + R(6) * wq<R>(q) *
+                      (R(cx(q)) * R(p.wall_u[0]) + R(cy(q)) * R(p.wall_u[1]) + R(cz(q)) * R(p.wall_u[2]));
     }
     f[q] = val;
   }

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
                az1 = z == p.nz - 1;
     const bool onface = ax0 || ax1 || ay0 || ay1 || az0 || az1;
     const bool fast = k == LIQ &&
-                      (p.has_wd ? !(fl & NEARB) && !onface
+                      ((p.has_wd || p.has_uw) ? !(fl & NEARB) && !onface
                                 : !(fl & NEARW) && !((ax0 || ax1) && p.px) && !((ay0 || ay1) && p.py) &&
                                       !((az0 || az1) && p.pz));
     const bool face_warp = __any_sync(0xffffffffu, fast && onface);
@@ -232,7 +232,10 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     // zero in the basis of the normal (Eq. proj2 through Eq. bstress):
     // S^b = S - (S n) n^T - n (S n)^T + 2 (n.S.n) n n^T
     R Sb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};  // xx yy zz xy xz yz
-    if (p.stress) {
+    if (p.stress == 2) {  // prescribed S^b
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Sb[k] = R(p.shear_b[k]);
+    } else if (p.stress) {
 #pragma unroll
       for (int q = 1; q < 19; q += 2) {  // each pair once: n_q^+ = n_qbar^+
         const R et = eplus_q<R>(p, q, rt, r0t, utx, uty, utz, usq);

@@ -38,7 +38,8 @@ class Params(C.Structure):
                 ("rho_G", C.c_double), ("sigma", C.c_double), ("rule", C.c_int), ("compressible", C.c_int),
                 ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
                 ("freeze", C.c_int), ("cleanup", C.c_int), ("keep_f0", C.c_int), ("delta_min", C.c_double),
-                ("stress", C.c_int), ("bulk_loads", C.c_int), ("precision", C.c_int),
+                ("stress", C.c_int), ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
+                ("bulk_loads", C.c_int), ("precision", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -147,6 +148,10 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.keep_f0 = int(params.get("keep_f0", 0))
     P.delta_min = params.get("delta_min", P.delta_min)
     P.stress = int(params.get("stress", 0))
+    for k, val in enumerate(params.get("shear_b", (0.0,) * 6)):
+        P.shear_b[k] = float(val)
+    for k, val in enumerate(params.get("wall_u", (0.0,) * 3)):
+        P.wall_u[k] = float(val)
     P.bulk_loads = LOADS[params.get("bulk_loads", "plain")]
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream
