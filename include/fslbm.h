@@ -225,7 +225,7 @@ int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
  * is included) through nsteps time steps to an objective J, at fixed cell
  * flags: every discrete decision of the forward pass (flags, the height-
  * function or plane-fit branch, the dominant axis, clamps of delta) is held.
- * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), and no cell conversion inside the window
+ * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), resting walls (wall_u = 0), and no cell conversion inside the window
  * (FSLBM_ERR_STATE otherwise).  Parameters: nu = (tau - 1/2)/3 with the magic
  * parameter Lambda held fixed, g, and the initial fill levels phi0 of
  * interface cells (m0 = phi0 rho0). */
