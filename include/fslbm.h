@@ -132,6 +132,13 @@ typedef struct {
   double shear_b[6];  /* prescribed S^b for stress = 2: xx, yy, zz, xy, xz, yz */
   double wall_u[3];   /* velocity of every wall: half-way bounce-back links get
                          + 6 w_q (c_q.u_w) (rho_0 = 1; not with compressible, not on CLI links) */
+  int ub_extrap;      /* u_b in e^+(rho_b, u_b) of the FSL closure (Eq. closure, Table 1): 0
+                         (default) the interface node's own velocity u(x_b) (first order, the
+                         next-neighbour value of Sec. 6's breaking dam); 1 its linear extrapolation
+                         along the link to the surface point x_w = x_b + delta c_p,
+                         u(x_b) + delta (u(x_b) - u(x_b - c_p)) (second order; with the non-linear
+                         e^+ a linear flow along a surface that is not lattice-aligned needs it,
+                         Sec. 6).  FSK links, and FSL links that fall back to FSK, keep u(x_b). */
   int bulk_loads;     /* fslbm_loads: how the bulk kernel of FP32/FP16 lattices reaches the
                          pulled values (FP64 always loads them plainly); same results every way */
   int precision;      /* fslbm_precision */
@@ -225,7 +232,8 @@ int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
  * is included) through nsteps time steps to an objective J, at fixed cell
  * flags: every discrete decision of the forward pass (flags, the height-
  * function or plane-fit branch, the dominant axis, clamps of delta) is held.
- * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), resting walls (wall_u = 0), and no cell conversion inside the window
+ * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), resting walls (wall_u = 0), u_b = u(x_b)
+ * (ub_extrap = 0), and no cell conversion inside the window
  * (FSLBM_ERR_STATE otherwise).  Parameters: nu = (tau - 1/2)/3 with the magic
  * parameter Lambda held fixed, g, and the initial fill levels phi0 of
  * interface cells (m0 = phi0 rho0). */

@@ -129,6 +129,7 @@ struct Params {
                      //    linear Couette flows); 0: D = 0
   double shear_b[6]; // prescribed S^b: xx, yy, zz, xy, xz, yz (stress = 2)
   double wall_u[3];  // velocity of every wall (half-way bounce-back links; rho_0 = 1)
+  int ub_extrap;     // 1: FSL takes u_b at the surface point x_b + delta c_p (linear along the link)
 };
 
 template <class T>
@@ -645,7 +646,8 @@ struct Sim {
   //           + C n_p^+(x_b),  C = lambda_+ (1/2 + delta) - 2 lambda_+,
   //           + alpha_+ e_p^+(rho_b, u_b),  alpha_+ = 1
   // rho_b = rho_G + 3 sigma kappa (Laplace pressure in place of P_b, Sec. 2.3),
-  // u_b = u(x_b, t) (next-neighbour extrapolation, Sec. 4.5).  FSL falls back
+  // u_b = u(x_b, t) (next-neighbour extrapolation, Sec. 4.5; with ub_extrap the
+  // FSL links take its linear extrapolation to x_w).  FSL falls back
   // to FSK on a link whose upstream node x_b - c_p is not liquid/interface.
   T free_surface_closure(long i, int q) const {
     const long NN = N;
@@ -663,6 +665,14 @@ struct Sim {
     }
     T n[3] = {gn[3 * i], gn[3 * i + 1], gn[3 * i + 2]};
     T dl = link_delta(pq, n, gd[i], gok[i] != 0);
+    if (p.ub_extrap) {
+      // u_b at the surface point x_w = x_b + delta c_p, linear in the values at
+      // x_b and x_b - c_p along the link (the boundary velocity of Eq. koerner,
+      // extrapolated from the nodes)
+      T uw[3];
+      for (int a = 0; a < 3; ++a) uw[a] = ub[a] + dl * (ub[a] - u_t[3 * up + a]);
+      eb = e_plus(pq, rb, uw, rho0(rb));
+    }
     T a0 = T(0.5) - dl;
     T ab0 = T(0.5);
     T a1 = dl - T(1.0);

@@ -49,7 +49,8 @@ class Params(C.Structure):
                 ("compressible", C.c_int), ("linear_eq", C.c_int), ("eps", C.c_double),
                 ("periodic", C.c_int * 3), ("zshift", C.c_int), ("freeze", C.c_int),
                 ("cleanup", C.c_int), ("delta_min", C.c_double), ("stress", C.c_int),
-                ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3)]
+                ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
+                ("ub_extrap", C.c_int)]
 
 
 def lib():
@@ -114,6 +115,7 @@ def make_params(dims, p) -> Params:
         P.shear_b[k] = float(v)
     for k, v in enumerate(p.get("wall_u", (0.0,) * 3)):
         P.wall_u[k] = float(v)
+    P.ub_extrap = int(p.get("ub_extrap", 0))
     return P
 
 

@@ -242,6 +242,58 @@ def inclined_film(h=8, tau=0.8, rule=1, magic=0.25, wall_offset=0.1, peak=None,
                 ncoord=ncoord, t_hat=t_hat)
 
 
+def skew_couette(h=8, slope=0.25, period=1, shear=1e-3, tau=1.1, rule=1, magic=0.25,
+                 wall_offset=0.1, headroom=4, init_exact=True, **kw) -> Case:
+    """Linear Couette flow in a channel inclined with slope dz/dx (Sec. 6,
+    rotated Couette flow): ny = 1, period nx = period/slope with a z-shift of
+    ``period`` on the x wrap; wall plane z = slope x + wall_offset (WALL cells
+    below it, CLI link fractions from the exact plane); free surface at
+    vertical height h above the wall plane, exact cut fill levels, frozen;
+    the surface shear rate du_t/dn = shear is prescribed through
+    S^b = shear/2 (t n^T + n t^T) (stress = 2); steady u = shear d t with d the
+    distance from the wall plane and t the unit tangent (1, 0, slope)/L."""
+    nx = int(round(period / slope))
+    assert abs(nx * slope - period) < 1e-12, "period / slope must be an integer"
+    nz = h + period + headroom
+    dims = (nx, 1, nz)
+    N = nx * nz
+    i = np.arange(N)
+    x = (i % nx) + 0.5
+    z = (i // nx) + 0.5
+    L = math.sqrt(1.0 + slope * slope)
+    zw = slope * x + wall_offset
+    solid = z < zw
+    k = z - 0.5
+    zs0 = slope * (x - 0.5) + wall_offset + h - k
+    phi = np.where(solid, 0.0, _clamped_linear_mean(zs0, zs0 + slope))
+    t_hat = np.array([1.0, 0.0, slope]) / L
+    n_hat = np.array([-slope, 0.0, 1.0]) / L
+    Sb = 0.5 * shear * (np.outer(t_hat, n_hat) + np.outer(n_hat, t_hat))
+    params = default_params(tau=tau, magic=magic, rule=rule, periodic=(1, 1, 0), zshift=period,
+                            freeze=1, stress=2,
+                            shear_b=(Sb[0, 0], Sb[1, 1], Sb[2, 2], Sb[0, 1], Sb[0, 2], Sb[1, 2]))
+    params.update(kw)
+    flags = classify(dims, params["periodic"], params["zshift"], phi, solid=solid, sharp=True)
+    wd = np.full((19, N), -1.0)
+    fluid = (flags == LIQUID) | (flags == INTERFACE)
+    for q in range(1, 19):
+        c = LINKS[q]
+        j = _neighbour_index(dims, params["periodic"], params["zshift"], i, c)
+        hit = fluid & ((j < 0) | (flags[np.maximum(j, 0)] == WALL))
+        denom = slope * c[0] - c[2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = (z - slope * x - wall_offset) / denom
+        good = hit & (denom > 0)
+        wd[q, good] = s[good]
+    d = (z - zw) / L
+    u_exact = np.where(fluid, shear * d, 0.0)[:, None] * t_hat[None, :]
+    keep = (flags == INTERFACE) | (flags == GAS)
+    return Case(dims=dims, params=params, flags=flags, rho=np.ones(N),
+                u=u_exact.copy() if init_exact else np.zeros((N, 3)),
+                phi=np.where(keep, phi, 0.0), noise=None, wall_delta=wd.reshape(-1),
+                h=h, shear=shear, u_exact=u_exact, d=d, t_hat=t_hat)
+
+
 def standing_wave(n=128, depth=64.0, amp=2.0, tau=0.55, g=2e-5, sigma=1e-4,
                   phi_noise=1e-4, seed=SEED, quad=8, rule=1, **kw) -> Case:
     """Standing gravity-capillary wave in an n^3 box with walls on all faces:

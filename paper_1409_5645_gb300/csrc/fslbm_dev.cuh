@@ -109,6 +109,7 @@ struct Par {
   double wall_u[3];        // wall velocity
   int has_uw;              // a wall velocity is set
   int has_wd;
+  int ub_extrap;           // FSL: u_b extrapolated along the link to the surface point
 };
 
 template <int P>

@@ -178,7 +178,32 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
 // closures, collision, store, fill/empty marks); returns its mass m.  IN:
 // every cell within 3 of it lies inside the lattice, so all stencil offsets
 // are plain (the hot path, kept apart from the face and wrap logic).
-template <int P, bool IN>
+// Velocity of a fluid cell from its stored post-collision populations
+// (sum_q c_q f~_q = rho_0 U + F, u = U + F/(2 rho_0)); only the FSL closure
+// with u_b extrapolated along the link calls it (the extended k_iface instance).
+template <class R>
+struct Vel3 {
+  R x, y, z;
+};
+template <int P>
+__device__ __forceinline__ Vel3<typename Form<P>::R> cell_velocity(const typename Form<P>::S* __restrict__ fin,
+                                                                 size_t N, size_t s, int compressible, double gx,
+                                                                 double gy, double gz) {
+  using R = typename Form<P>::R;
+  R r = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    const R fq = ldq<P>(fin, (size_t)q * N + s, q);
+    r += fq;
+    if (cx(q)) jx += R(cx(q)) * fq;
+    if (cy(q)) jy += R(cy(q)) * fq;
+    if (cz(q)) jz += R(cz(q)) * fq;
+  }
+  const R ir0 = compressible ? R(1) / r : R(1);
+  return Vel3<R>{jx * ir0 - R(0.5) * R(gx), jy * ir0 - R(0.5) * R(gy), jz * ir0 - R(0.5) * R(gz)};
+}
+
+template <int P, bool IN, bool EXT>
 __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int li, long long i, int x, int y,
                                              int z, bool& fill, bool& empty) {
   using R = typename Form<P>::R;
@@ -211,7 +236,7 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     // the plane and curvature of k_geom (FSK without surface tension or the
     // boundary shear term needs neither)
     R n[3] = {R(0), R(0), R(0)}, d = R(0), kap = R(0);
-    if (p.rule != 0 || p.sigma != 0.0 || p.stress) {
+    if (p.rule != 0 || p.sigma != 0.0 || (EXT && p.stress)) {
       const size_t cap = (size_t)v.cap;
       n[0] = v.geo[li];
       n[1] = v.geo[cap + li];
@@ -232,10 +257,10 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     // zero in the basis of the normal (Eq. proj2 through Eq. bstress):
     // S^b = S - (S n) n^T - n (S n)^T + 2 (n.S.n) n n^T
     R Sb[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};  // xx yy zz xy xz yz
-    if (p.stress == 2) {  // prescribed S^b
+    if (EXT && p.stress == 2) {  // prescribed S^b
 #pragma unroll
       for (int k = 0; k < 6; ++k) Sb[k] = R(p.shear_b[k]);
-    } else if (p.stress) {
+    } else if (EXT && p.stress) {
 #pragma unroll
       for (int q = 1; q < 19; q += 2) {  // each pair once: n_q^+ = n_qbar^+
         const R et = eplus_q<R>(p, q, rt, r0t, utx, uty, utz, usq);
@@ -265,7 +290,7 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
       bool up_fluid = !((wallm | gasm) & (1u << pq));
       // D c_p.S^b.c_p / alpha_+ (Eq. bterm, Table 1)
       R dterm = R(0);
-      if (p.stress) {
+      if (EXT && p.stress) {
         const R cSc = R(cx(pq) * cx(pq)) * Sb[0] + R(cy(pq) * cy(pq)) * Sb[1] + R(cz(pq) * cz(pq)) * Sb[2] +
                       R(2 * cx(pq) * cy(pq)) * Sb[3] + R(2 * cx(pq) * cz(pq)) * Sb[4] +
                       R(2 * cy(pq) * cz(pq)) * Sb[5];
@@ -281,6 +306,14 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
             dl = qdiv(d, cn);
             dl = dl < R(p.delta_min) ? R(p.delta_min) : (dl > R(1) ? R(1) : dl);
           }
+        }
+        if (EXT && p.ub_extrap) {
+          // u_b at the surface point x_b + delta c_p, linear along the link
+          // through u(x_b) and u(x_b - c_p)
+          const long long su = IN ? i - (cx(pq) + sy * cy(pq) + sz * cz(pq)) : (long long)srcs[pq];
+          const Vel3<R> uu = cell_velocity<P>(v.fin, N, (size_t)su, p.compressible, p.g[0], p.g[1], p.g[2]);
+          const R wx = utx + dl * (utx - uu.x), wy = uty + dl * (uty - uu.y), wz = utz + dl * (utz - uu.z);
+          eb = eplus_q<R>(p, pq, rb, r0b, wx, wy, wz, wx * wx + wy * wy + wz * wz);
         }
         R et = eplus_q<R>(p, pq, rt, r0t, utx, uty, utz, usq);
         R nplus = (R(0.5) * (own[pq] + own[q]) - et) * R(p.inv_1plp);
@@ -354,7 +387,9 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
   }
 }
 
-template <int P>
+// EXT: the instance with the boundary shear-rate term and the extrapolated
+// u_b (separate, so that the default instance carries none of their code)
+template <int P, bool EXT>
 __global__ void __launch_bounds__(128, (P == P64 ? 3 : 5)) k_iface(Par p, View<P> v, int part_base) {
   pdl_begin();
   const int n_in = min(*((volatile int*)&v.cnt[0]), v.cap), n_edge = min(*((volatile int*)&v.cnt[6]), v.cap);
@@ -374,8 +409,8 @@ __global__ void __launch_bounds__(128, (P == P64 ? 3 : 5)) k_iface(Par p, View<P
       icell = (int)i;
       int x, y, z;
       coords(p, i, x, y, z);
-      msum += in3 ? iface_cell<P, true>(p, v, pos, i, x, y, z, fill, empty)
-                  : iface_cell<P, false>(p, v, pos, i, x, y, z, fill, empty);
+      msum += in3 ? iface_cell<P, true, EXT>(p, v, pos, i, x, y, z, fill, empty)
+                  : iface_cell<P, false, EXT>(p, v, pos, i, x, y, z, fill, empty);
     }
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);
@@ -433,7 +468,9 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
   if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
   if ((p.rule != 0 || p.sigma != 0.0 || p.stress) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v)) return 1;
   // the interface partials follow the bulk warps' ones
-  if (launch_k(k_iface<P>, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) return 1;
+  if (launch_k((p.stress || p.ub_extrap) ? k_iface<P, true> : k_iface<P, false>, iface_blocks, 128, 0, st, p, v,
+               bulk_blocks * 4))
+    return 1;
   return (int)cudaGetLastError();
 }
 

@@ -585,3 +585,66 @@ def test_couette_prescribed_shear_exact():
     o = Oracle.from_case(c)
     o.step(2000)
     assert np.abs(o.get(VEL)).max() < 1e-15
+
+
+def _skew_couette_error(h, shear, linear_eq, ub_extrap, tau=1.1, tol=1e-12, chunk=500, max_steps=200000):
+    """Relative L2 error of the steady skew Couette flow (run from the exact
+    velocity until the relative change per 500 steps is below tol)."""
+    c = cases.skew_couette(h=h, shear=shear, tau=tau, linear_eq=linear_eq, ub_extrap=ub_extrap)
+    o = Oracle.from_case(c)
+    fl = c["flags"]
+    fluid = (fl == cases.LIQUID) | (fl == cases.INTERFACE)
+    prev = o.get(VEL)[fluid]
+    for _ in range(max_steps // chunk):
+        assert o.step(chunk) == 0
+        u = o.get(VEL)[fluid]
+        change = np.sqrt(((u - prev) ** 2).sum() / (u ** 2).sum())
+        prev = u
+        if change < tol:
+            break
+    ex = c["u_exact"][fluid]
+    return np.sqrt(((u - ex) ** 2).sum() / (ex ** 2).sum())
+
+
+def test_skew_couette_linear_equilibrium_exact():
+    """Couette flow in a channel with slope 1/4 (Sec. 6, rotated linear
+    flow): CLI wall below, free surface above with the surface shear rate
+    prescribed through S^b = s/2 (t n^T + n t^T) (stress = 2, FSL); with the
+    linear e^+ the steady profile u = s d t is recovered to round-off, whichever
+    u_b the closure takes (u_b enters only the non-linear part of e^+)."""
+    for h in (8, 16):
+        for xu in (0, 1):
+            e = _skew_couette_error(h, 1e-3, 1, xu)
+            assert e < 1e-10, (h, xu, e)
+
+
+def test_skew_couette_nonlinear_order_needs_extrapolated_ub():
+    """The same flow with the non-linear e^+ at a fixed Reynolds number (shear
+    rate ~ 1/h^2 at fixed tau, h = 8, 16, 32): with u_b extrapolated along the
+    link to the surface point x_b + delta c_p the error falls at second order
+    (Sec. 6); with the node's own velocity the surface shear rate is off by a
+    fraction proportional to the surface velocity and the order drops to one."""
+    hs = (8, 16, 32)
+    ex = np.array([_skew_couette_error(h, 1e-3 * (8.0 / h) ** 2, 0, 1) for h in hs])
+    node = np.array([_skew_couette_error(h, 1e-3 * (8.0 / h) ** 2, 0, 0) for h in hs])
+    o_ex = np.log2(ex[:-1] / ex[1:])
+    o_node = np.log2(node[:-1] / node[1:])
+    assert np.all(o_ex > 1.9), (ex, o_ex)
+    assert np.all((o_node > 0.9) & (o_node < 1.15)), (node, o_node)
+    assert ex[0] < 2e-5 and node[0] > 5e-4
+
+
+def test_aligned_couette_exact_with_extrapolated_ub():
+    """The aligned Couette flow stays exact with u_b extrapolated along the
+    link (non-linear and linear e^+)."""
+    for linear in (0, 1):
+        c = cases.couette(h=8, linear_eq=linear, ub_extrap=1)
+        o = Oracle.from_case(c)
+        o.step(8000)
+        u = o.get(VEL)[:, 0]
+        nx, ny = c["dims"][0], c["dims"][1]
+        z = np.arange(c.N) // (nx * ny)
+        fluid = (c["flags"] == cases.LIQUID) | (c["flags"] == cases.INTERFACE)
+        ue = 2.0 * c["shear"] * (z + 0.5)
+        err = np.abs(u[fluid] - ue[fluid]).max() / np.abs(ue[fluid]).max()
+        assert err < 1e-10, (linear, err)
