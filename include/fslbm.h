@@ -139,6 +139,17 @@ typedef struct {
                          u(x_b) + delta (u(x_b) - u(x_b - c_p)) (second order; with the non-linear
                          e^+ a linear flow along a surface that is not lattice-aligned needs it,
                          Sec. 6).  FSK links, and FSL links that fall back to FSK, keep u(x_b). */
+  int recon_nc;       /* 1: an interface cell also rebuilds, with the rule's closure, every link p
+                         toward a liquid/interface node whose direction points to the gas side of
+                         the surface, n.c_p > 1e-6 with n the unit normal of the plane fit
+                         (the reconstruction along the normal of Koerner et al., whose tracking
+                         Sec. 4.4 and Sec. 6 follow); 0 (default): only the links to gas cells */
+  int excess_split;   /* excess mass of a filled or emptied cell: 0 (default) split equally over
+                         its receivers; 1 split in proportion to the weights along the fill-level
+                         normal n = -grad phi (central differences of the fill levels after the
+                         mass exchange): n.c_q > 0 for a filled cell, -n.c_q > 0 for an emptied
+                         one (Thuerey's distribution, whose tracking Sec. 4.4 follows); equal
+                         split where no receiver has a positive weight (sum below 1e-12) */
   int bulk_loads;     /* fslbm_loads: how the bulk kernel of FP32/FP16 lattices reaches the
                          pulled values (FP64 always loads them plainly); same results every way */
   int precision;      /* fslbm_precision */
@@ -233,7 +244,7 @@ int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
  * flags: every discrete decision of the forward pass (flags, the height-
  * function or plane-fit branch, the dominant axis, clamps of delta) is held.
  * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), resting walls (wall_u = 0), u_b = u(x_b)
- * (ub_extrap = 0), and no cell conversion inside the window
+ * (ub_extrap = 0), gas links only (recon_nc = 0), and no cell conversion inside the window
  * (FSLBM_ERR_STATE otherwise).  Parameters: nu = (tau - 1/2)/3 with the magic
  * parameter Lambda held fixed, g, and the initial fill levels phi0 of
  * interface cells (m0 = phi0 rho0). */

@@ -130,6 +130,9 @@ struct Params {
   double shear_b[6]; // prescribed S^b: xx, yy, zz, xy, xz, yz (stress = 2)
   double wall_u[3];  // velocity of every wall (half-way bounce-back links; rho_0 = 1)
   int ub_extrap;     // 1: FSL takes u_b at the surface point x_b + delta c_p (linear along the link)
+  int recon_nc;      // 1: interface cells also rebuild links p with n.c_p > 0 toward a fluid node
+                     //    (Koerner et al.'s reconstruction along the normal, Sec. 4.4 citation)
+  int excess_split;  // 1: excess mass split with weights along the fill-level normal (Thuerey)
 };
 
 template <class T>
@@ -562,7 +565,7 @@ struct Sim {
         uint8_t ts = type(src);
         if (q == 0) { fn[i] = ft[i]; continue; }
         if (fluid(ts)) {
-          fn[(size_t)q * NN + i] = ft[(size_t)q * NN + src];
+          fn[(size_t)q * NN + i] = normal_link(i, q) ? free_surface_closure(i, q) : ft[(size_t)q * NN + src];
         } else if (ts == WALL) {
           fn[(size_t)q * NN + i] = wall_closure(i, q);
         } else {  // gas source
@@ -611,6 +614,19 @@ struct Sim {
     ++t;
     if (st != OK && status == OK) status = st;
     return st;
+  }
+
+  // Koerner et al.'s extra reconstruction (recon_nc): at an interface cell
+  // with a surface normal n (pointing into the gas), the population f_q whose
+  // source x - c_q = x + c_p is a fluid node is rebuilt by the free-surface
+  // closure as well when n.c_p > 0, i.e. when the link points to the gas side
+  // of the surface.  A margin of 1e-6 keeps links that are tangent to the
+  // surface (n.c_p = 0 up to rounding) out of the set.
+  bool normal_link(long i, int q) const {
+    if (!p.recon_nc || flag[i] != IFC || !gok[i]) return false;
+    const int pq = opp[q];
+    const double cn = CV[pq][0] * val(gn[3 * i]) + CV[pq][1] * val(gn[3 * i + 1]) + CV[pq][2] * val(gn[3 * i + 2]);
+    return cn > 1e-6;
   }
 
   // Wall closure for population q at fluid cell i whose source x - c_q is a
@@ -727,6 +743,35 @@ struct Sim {
     return T(-alpha * Lp * 3.0 * w[pq]) * ccS;
   }
 
+  // Normal of the fill level for the weighted excess split (Thuerey's
+  // distribution along the interface normal): n = -grad phi by central
+  // differences, n_a = (phi(x - e_a) - phi(x + e_a)) / 2, pointing into the
+  // gas, from the fill levels after the mass exchange: liquid 1, gas 0,
+  // interface m / rho, and the cell's own value across a wall or a face.
+  double phi_star(long j, double own, const std::vector<T>& rho1) const {
+    if (j < 0) return own;
+    switch (flag[j]) {
+      case LIQ: return 1.0;
+      case GAS: return 0.0;
+      case IFC: return val(m[j]) / val(rho1[j]);
+      default: return own;
+    }
+  }
+  void fill_normal(long i, const std::vector<T>& rho1, double* n) const {
+    const double own = val(m[i]) / val(rho1[i]);
+    for (int a = 0; a < 3; ++a) {
+      const int qp = 1 + 2 * a, qm = 2 + 2 * a;  // +e_a and -e_a
+      n[a] = 0.5 * (phi_star(nbq(i, qm, 1), own, rho1) - phi_star(nbq(i, qp, 1), own, rho1));
+    }
+  }
+  // Weight of the neighbour x + c_q in the split of a converting cell: a
+  // filled cell pushes its excess toward the gas (n.c_q > 0), an emptied cell
+  // draws its deficit from the liquid side (n.c_q < 0).
+  static double split_weight(const double* n, int q, bool filled) {
+    const double d = CV[q][0] * n[0] + CV[q][1] * n[1] + CV[q][2] * n[2];
+    return filled ? (d > 0.0 ? d : 0.0) : (d < 0.0 ? -d : 0.0);
+  }
+
   // Cell conversions after the mass update (reading of Koerner et al. /
   // Thuerey as cited in Sec. 4.4; the paper gives no details):
   //  F = {interface : m > (1+eps) rho, or no gas neighbour (cleanup bit 1)},
@@ -736,7 +781,9 @@ struct Sim {
   //     their liquid/interface neighbours (q order), m = 0;
   //  3. liquid neighbours of the remaining E become interface with m = rho;
   //  4. excess (F: m - rho, E: m) is split equally over the neighbours that are
-  //     interface after 2-3 and not converting; no receiver -> lost ledger;
+  //     interface after 2-3 and not converting (excess_split 1: in proportion
+  //     to split_weight along the fill-level normal, equally where no receiver
+  //     lies on the weighted side); no receiver -> lost ledger;
   //  5. F -> liquid (m = rho), E -> gas (m = 0), new cells -> interface.
   void convert(std::vector<T>& rho1) {
     const long NN = N;
@@ -812,14 +859,24 @@ struct Sim {
       return flag[j] == IFC && !isF[j] && !isE[j];
     };
     std::vector<T> share(NN, T(0));
+    std::vector<uint8_t> weighted(NN, 0);
+    std::vector<double> nf;  // fill-level normals of the converting cells (weighted split)
+    if (p.excess_split) nf.assign((size_t)3 * NN, 0.0);
     for (long i = 0; i < NN; ++i) {
       if (!isF[i] && !isE[i]) continue;
       T ex = isF[i] ? T(m[i] - rho1[i]) : m[i];
       int nr = 0;
       for (int q = 1; q < Q; ++q)
         if (receiver(nbq(i, q, 1))) ++nr;
-      if (nr == 0) lost += ex;
-      else share[i] = ex / T((double)nr);
+      if (nr == 0) { lost += ex; continue; }
+      if (p.excess_split) {
+        fill_normal(i, rho1, &nf[3 * i]);
+        double V = 0.0;  // sum of the receivers' weights, in q order
+        for (int q = 1; q < Q; ++q)
+          if (receiver(nbq(i, q, 1))) V += split_weight(&nf[3 * i], q, isF[i] != 0);
+        if (V > 1e-12) { share[i] = ex / T(V); weighted[i] = 1; continue; }
+      }
+      share[i] = ex / T((double)nr);  // equal split (also where no receiver lies along the normal)
     }
     for (long j = 0; j < NN; ++j) {
       if (!receiver(j)) continue;
@@ -827,7 +884,12 @@ struct Sim {
       bool any = false;
       for (int q = 1; q < Q; ++q) {
         long i = nbq(j, q, 1);
-        if (i >= 0 && (isF[i] || isE[i])) { acc += share[i]; any = true; }
+        if (i >= 0 && (isF[i] || isE[i])) {
+          // the link from i to j is opp[q]
+          if (weighted[i]) acc += share[i] * T(split_weight(&nf[3 * i], opp[q], isF[i] != 0));
+          else acc += share[i];
+          any = true;
+        }
       }
       if (any) m[j] = m[j] + acc;
     }

@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("periodic", C.c_int * 3), ("zshift", C.c_int), ("freeze", C.c_int),
                 ("cleanup", C.c_int), ("delta_min", C.c_double), ("stress", C.c_int),
                 ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
-                ("ub_extrap", C.c_int)]
+                ("ub_extrap", C.c_int), ("recon_nc", C.c_int),
+                ("excess_split", C.c_int)]
 
 
 def lib():
@@ -116,6 +117,8 @@ def make_params(dims, p) -> Params:
     for k, v in enumerate(p.get("wall_u", (0.0,) * 3)):
         P.wall_u[k] = float(v)
     P.ub_extrap = int(p.get("ub_extrap", 0))
+    P.recon_nc = int(p.get("recon_nc", 0))
+    P.excess_split = int(p.get("excess_split", 0))
     return P
 
 

@@ -641,6 +641,7 @@ extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objectiv
   if (h->par.stress) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs D = 0 (no boundary shear term)");
   if (h->par.has_uw) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs resting walls");
   if (h->par.ub_extrap) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs u_b = u(x_b) (ub_extrap = 0)");
+  if (h->par.recon_nc) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs the gas links only (recon_nc = 0)");
   fslbm_free_adjoint(h);
   AdjointState* A = new AdjointState();
   h->adj = A;

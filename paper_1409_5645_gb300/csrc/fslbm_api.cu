@@ -106,6 +106,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   if (q.bulk_loads < FSLBM_LOADS_PLAIN || q.bulk_loads > FSLBM_LOADS_TMA) return FSLBM_ERR_ARG;
   if (q.stress < 0 || q.stress > 2) return FSLBM_ERR_ARG;
   if (q.ub_extrap < 0 || q.ub_extrap > 1) return FSLBM_ERR_ARG;
+  if (q.recon_nc < 0 || q.recon_nc > 1) return FSLBM_ERR_ARG;
+  if (q.excess_split < 0 || q.excess_split > 1) return FSLBM_ERR_ARG;
   if (q.compressible && (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0)) return FSLBM_ERR_ARG;
 
   fslbm* h = (fslbm*)calloc(1, sizeof(fslbm));
@@ -152,6 +154,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   p.has_uw = (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0) ? 1 : 0;
   p.has_wd = 0;
   p.ub_extrap = q.ub_extrap;
+  p.recon_nc = q.recon_nc;
+  p.excess_split = q.excess_split;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;

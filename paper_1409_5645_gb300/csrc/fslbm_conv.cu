@@ -202,6 +202,36 @@ __device__ __forceinline__ void do_newl(const Par& p, const View<P>& v) {
   }
 }
 
+// Fill-level normal of a converting cell for the weighted excess split
+// (Thuerey's distribution along the interface normal): n = -grad phi by
+// central differences, n_a = (phi(x - e_a) - phi(x + e_a)) / 2, pointing into
+// the gas, from the fill levels after the mass exchange (liquid 1, gas 0,
+// interface m/rho as k_iface stored it, the cell's own value across a wall or
+// a face).  The flags are those of time t until k_final.
+template <int P>
+__device__ __forceinline__ double phi_star(const Par& p, const View<P>& v, long long j, double own) {
+  if (j < 0) return own;
+  const uint8_t k = v.flags[j] & KIND;
+  return k == LIQ ? 1.0 : (k == GAS ? 0.0 : (k == IFC ? (double)v.phout[j] : own));
+}
+template <int P>
+__device__ __forceinline__ void fill_normal(const Par& p, const View<P>& v, long long i, double (&n)[3]) {
+  int x, y, z;
+  coords(p, i, x, y, z);
+  const double own = (double)v.phout[i];
+  n[0] = 0.5 * (phi_star<P>(p, v, nbr(p, x, y, z, -1, 0, 0), own) - phi_star<P>(p, v, nbr(p, x, y, z, 1, 0, 0), own));
+  n[1] = 0.5 * (phi_star<P>(p, v, nbr(p, x, y, z, 0, -1, 0), own) - phi_star<P>(p, v, nbr(p, x, y, z, 0, 1, 0), own));
+  n[2] = 0.5 * (phi_star<P>(p, v, nbr(p, x, y, z, 0, 0, -1), own) - phi_star<P>(p, v, nbr(p, x, y, z, 0, 0, 1), own));
+}
+// weight of the neighbour along c (components -1, 0, 1, so the products are
+// exact and the sum is the same in any contraction): a filled cell pushes its
+// excess toward the gas (n.c > 0), an emptied cell draws its deficit from the
+// liquid side (n.c < 0)
+__device__ __forceinline__ double split_weight(const double (&n)[3], int ax, int ay, int az, bool filled) {
+  const double d = (double)ax * n[0] + (double)ay * n[1] + (double)az * n[2];
+  return filled ? (d > 0.0 ? d : 0.0) : (d < 0.0 ? -d : 0.0);
+}
+
 // one warp per fill / empty cell: lane q (1..18) tests neighbour q as a
 // receiver; lane 0 computes the share (rho summed in q order, as a thread would)
 template <int P>
@@ -229,6 +259,14 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
       }
     }
     const unsigned rm = __ballot_sync(FULL, recv);
+    // weighted split: the receivers' weights summed in q order on lane 0
+    double V = 0.0;
+    if (p.excess_split && rm) {
+      double n[3];
+      fill_normal<P>(p, v, i, n);  // (every lane: the same few loads)
+      const double w = recv ? split_weight(n, cx(q), cy(q), cz(q), isF) : 0.0;
+      for (int s = 1; s < 19; ++s) V += __shfl_sync(FULL, w, s);
+    }
     if (lane == 0) {
       const double rho = (double)rho_out<P>(p, v, i);
       const double ex = isF ? v.m[i] - rho : v.m[i];
@@ -236,8 +274,11 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
       if (nr == 0) {
         atomicAdd(v.lost, ex);
         v.share[i] = 0.0;
+      } else if (V > 1e-12) {
+        v.share[i] = ex / V;
+        v.mark[i] = (uint8_t)(v.mark[i] | MK_WSPLIT);
       } else {
-        v.share[i] = ex / (double)nr;
+        v.share[i] = ex / (double)nr;  // equal split (also where no receiver lies along the normal)
       }
       v.m[i] = isF ? rho : 0.0;
     }
@@ -284,12 +325,25 @@ __global__ void __launch_bounds__(256) k_recv(Par p, View<P> v) {
     for (int q = 1; q < 19; ++q) {
       const long long j = in1 ? yj + (cx(q) + sy * cy(q) + sz * cz(q)) : nbr(p, x, y, z, cx(q), cy(q), cz(q));
       if (j < 0) continue;
-      if (v.mark[j] & (MK_FILL | MK_EMPTY)) acc += v.share[j];
+      const uint8_t mk = v.mark[j];
+      if (mk & (MK_FILL | MK_EMPTY)) {
+        if (mk & MK_WSPLIT) {  // the link from j to this receiver is -c_q
+          double n[3];
+          fill_normal<P>(p, v, j, n);
+          acc += v.share[j] * split_weight(n, -cx(q), -cy(q), -cz(q), (mk & MK_FILL) != 0);
+        } else {
+          acc += v.share[j];
+        }
+      }
     }
     const double mm = v.m[yj] + acc;
     v.m[yj] = mm;
-    const R r = rho_out<P>(p, v, yj);
-    v.phout[yj] = (R)(mm / (double)r);
+    // (the weighted split reads the fill levels of interface cells here, so
+    // its receivers take their new fill level in k_final)
+    if (!p.excess_split) {
+      const R r = rho_out<P>(p, v, yj);
+      v.phout[yj] = (R)(mm / (double)r);
+    }
   }
 }
 
@@ -338,7 +392,9 @@ __global__ void k_final(Par p, View<P> v) {
       continue;
     }
     kk -= nl;
-    v.mark[v.rlist[kk]] = 0;
+    const long long r = v.rlist[kk];
+    v.mark[r] = 0;
+    if (p.excess_split) v.phout[r] = (R)(v.m[r] / (double)rho_out<P>(p, v, r));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) emptied += __shfl_down_sync(0xffffffffu, emptied, o);

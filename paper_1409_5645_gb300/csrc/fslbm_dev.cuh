@@ -42,7 +42,7 @@ __host__ __device__ constexpr R wq(int q) {
 // static bits beside the kind: NEARB a neighbour is a wall (a WALL cell or
 // beyond a non-periodic face); NEARW a neighbour is a WALL cell of the lattice
 enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16, NEARW = 32, STATIC_BITS = 48 };
-enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16 };
+enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_WSPLIT = 32 };
 enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8 };
 
 // ---------------------------------------------------------------------------
@@ -110,6 +110,8 @@ struct Par {
   int has_uw;              // a wall velocity is set
   int has_wd;
   int ub_extrap;           // FSL: u_b extrapolated along the link to the surface point
+  int recon_nc;            // interface cells also rebuild the links with n.c_p > 0
+  int excess_split;        // 1: excess split along the fill-level normal
 };
 
 template <int P>

@@ -232,11 +232,11 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     }
   }
   if (wallm) wall_links<P>(p, v, i, wallm, gasm, own, f);
-  if (gasm) {
-    // the plane and curvature of k_geom (FSK without surface tension or the
-    // boundary shear term needs neither)
+  if (gasm || (EXT && p.recon_nc)) {
+    // the plane and curvature of k_geom (FSK without surface tension, the
+    // boundary shear term or the normal links needs neither)
     R n[3] = {R(0), R(0), R(0)}, d = R(0), kap = R(0);
-    if (p.rule != 0 || p.sigma != 0.0 || (EXT && p.stress)) {
+    if (p.rule != 0 || p.sigma != 0.0 || (EXT && (p.stress || p.recon_nc))) {
       const size_t cap = (size_t)v.cap;
       n[0] = v.geo[li];
       n[1] = v.geo[cap + li];
@@ -245,6 +245,20 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
       kap = v.geo[4 * cap + li];
     }
     const bool ok = true;  // no normal is stored as n = 0: c.n > 0 fails and delta stays 1/2
+    // links to rebuild: the gas links, and with recon_nc the links p toward a
+    // fluid node with n.c_p > 0 (Koerner et al.'s reconstruction along the
+    // normal; margin 1e-6 for links tangent to the surface)
+    unsigned rmask = gasm;
+    R pulled[19];  // the pulled values, kept apart from the rebuilt ones
+    if (EXT && p.recon_nc) {
+#pragma unroll
+      for (int q = 1; q < 19; ++q) {
+        pulled[q] = f[q];
+        const int pq = inv(q);
+        const R cn = R(cx(pq)) * n[0] + R(cy(pq)) * n[1] + R(cz(pq)) * n[2];
+        if (!((wallm | gasm) & (1u << q)) && cn > R(1e-6)) rmask |= 1u << q;
+      }
+    }
     R rb = R(p.rho_G);
     if (p.sigma != 0.0) rb = rb + R(3.0 * p.sigma) * kap;
     const R r0b = p.compressible ? rb : R(1);
@@ -284,8 +298,8 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     const R Dk = R(-3.0 * (p.tau_m_half));  // D = -alpha_+ Lambda_+ w_p / c_s^2, without alpha_+ w_p
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
-      if (!(gasm & (1u << q))) continue;
-      const int pq = inv(q);  // boundary link: x + c_p is gas, missing f_pbar = f_q
+      if (!(rmask & (1u << q))) continue;
+      const int pq = inv(q);  // boundary link: x + c_p is gas (or a normal link), rebuilt f_pbar = f_q
       R eb = eplus_q<R>(p, pq, rb, r0b, utx, uty, utz, usq);
       bool up_fluid = !((wallm | gasm) & (1u << pq));
       // D c_p.S^b.c_p / alpha_+ (Eq. bterm, Table 1)
@@ -318,7 +332,8 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
         R et = eplus_q<R>(p, pq, rt, r0t, utx, uty, utz, usq);
         R nplus = (R(0.5) * (own[pq] + own[q]) - et) * R(p.inv_1plp);
         R C = lp * (R(0.5) + dl) - R(2) * lp;
-        f[q] = (R(0.5) - dl) * own[pq] + R(0.5) * own[q] + (dl - R(1)) * f[pq] + C * nplus + eb + dterm;
+        const R fup = (EXT && p.recon_nc) ? pulled[pq] : f[pq];  // f~_p(x_b - c_p)
+        f[q] = (R(0.5) - dl) * own[pq] + R(0.5) * own[q] + (dl - R(1)) * fup + C * nplus + eb + dterm;
       }
     }
   }
@@ -387,10 +402,11 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
   }
 }
 
-// EXT: the instance with the boundary shear-rate term and the extrapolated
-// u_b (separate, so that the default instance carries none of their code)
+// EXT: the instance with the boundary shear-rate term, the extrapolated u_b
+// and the normal links (separate, so that the default instance carries none
+// of their code)
 template <int P, bool EXT>
-__global__ void __launch_bounds__(128, (P == P64 ? 3 : 5)) k_iface(Par p, View<P> v, int part_base) {
+__global__ void __launch_bounds__(128, (EXT ? 2 : (P == P64 ? 3 : 5))) k_iface(Par p, View<P> v, int part_base) {
   pdl_begin();
   const int n_in = min(*((volatile int*)&v.cnt[0]), v.cap), n_edge = min(*((volatile int*)&v.cnt[6]), v.cap);
   const int count = min(n_in + n_edge, v.cap);
@@ -466,9 +482,10 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
     return 1;
   if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
-  if ((p.rule != 0 || p.sigma != 0.0 || p.stress) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v)) return 1;
+  if ((p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc) && launch_k(k_geom<P>, iface_blocks, 128, 0, st, p, v))
+    return 1;
   // the interface partials follow the bulk warps' ones
-  if (launch_k((p.stress || p.ub_extrap) ? k_iface<P, true> : k_iface<P, false>, iface_blocks, 128, 0, st, p, v,
+  if (launch_k((p.stress || p.ub_extrap || p.recon_nc) ? k_iface<P, true> : k_iface<P, false>, iface_blocks, 128, 0, st, p, v,
                bulk_blocks * 4))
     return 1;
   return (int)cudaGetLastError();

@@ -39,7 +39,8 @@ class Params(C.Structure):
                 ("linear_eq", C.c_int), ("eps", C.c_double), ("periodic", C.c_int * 3), ("zshift", C.c_int),
                 ("freeze", C.c_int), ("cleanup", C.c_int), ("keep_f0", C.c_int), ("delta_min", C.c_double),
                 ("stress", C.c_int), ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
-                ("ub_extrap", C.c_int), ("bulk_loads", C.c_int), ("precision", C.c_int),
+                ("ub_extrap", C.c_int), ("recon_nc", C.c_int), ("excess_split", C.c_int),
+                ("bulk_loads", C.c_int), ("precision", C.c_int),
                 ("stream", C.c_void_p)]
 
 
@@ -153,6 +154,8 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     for k, val in enumerate(params.get("wall_u", (0.0,) * 3)):
         P.wall_u[k] = float(val)
     P.ub_extrap = int(params.get("ub_extrap", 0))
+    P.recon_nc = int(params.get("recon_nc", 0))
+    P.excess_split = int(params.get("excess_split", 0))
     P.bulk_loads = LOADS[params.get("bulk_loads", "plain")]
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream

@@ -1,0 +1,58 @@
+"""Interface-tracking variants of the works the paper's tracking follows
+(Sec. 4.4, Sec. 6) on the CUDA path, against the oracle: the reconstruction of
+the links along the surface normal (recon_nc) and the excess split along the
+fill-level normal (excess_split)."""
+import pytest
+
+from gpu_util import run_parity
+from paper_1409_5645_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_dam_break_parity_normal_links(rule):
+    """Dam break with conversions, interior and edge interface cells."""
+    c = cases.dam_break(nx=24, ny=12, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=rule, recon_nc=1)
+    _, _, conv = run_parity(c, 120, every=1)
+    assert conv[0] + conv[1] > 0 and conv[2] + conv[3] > 0
+
+
+def test_inclined_film_parity_normal_links():
+    """Tilted frozen surface (shifted wrap, CLI wall): the normal links are
+    rebuilt on every interface cell."""
+    run_parity(cases.inclined_film(h=8, rule=1, recon_nc=1), 300, every=30)
+
+
+def test_wave_parity_normal_links_with_all_options():
+    """Capillary wave with the shear term, the extrapolated u_b and the normal
+    links together."""
+    c = cases.standing_wave(n=24, depth=12.0, amp=1.5, tau=0.6, g=1e-4, sigma=5e-3, phi_noise=1e-4,
+                            stress=1, ub_extrap=1, recon_nc=1)
+    run_parity(c, 60, every=1)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_dam_break_parity_weighted_split(rule):
+    c = cases.dam_break(nx=24, ny=12, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=rule, excess_split=1)
+    _, _, conv = run_parity(c, 150, every=1)
+    assert conv[0] > 0 and conv[1] > 0
+
+
+@pytest.mark.parametrize("phi_c", [1.05, -0.05])
+def test_single_conversion_parity_weighted_split(phi_c):
+    """One cell fills (or empties) under a flat surface: the weighted split
+    sends its excess across the surface only."""
+    c = cases.film(nx=4, ny=4, nz=16, h=8.5, gx=0.0, noise_amp=0.0, excess_split=1)
+    c["phi"][1 + 4 * (2 + 4 * 8)] = phi_c
+    _, _, conv = run_parity(c, 20, every=1)
+    assert conv[0] + conv[1] >= 1
+
+
+def test_dam_break_parity_all_tracking_variants():
+    """Dam break of a ragged size with the normal links, the weighted split,
+    the extrapolated u_b and the shear term together."""
+    c = cases.dam_break(nx=21, ny=11, nz=17, col_x=7, col_z=12, tau=0.62, g=2e-4, rule=1,
+                        recon_nc=1, excess_split=1, ub_extrap=1, stress=1)
+    _, _, conv = run_parity(c, 150, every=1)
+    assert conv[0] > 0 and conv[1] > 0

@@ -648,3 +648,140 @@ def test_aligned_couette_exact_with_extrapolated_ub():
         ue = 2.0 * c["shear"] * (z + 0.5)
         err = np.abs(u[fluid] - ue[fluid]).max() / np.abs(ue[fluid]).max()
         assert err < 1e-10, (linear, err)
+
+
+# --------------------------------------------------------------------------
+# Koerner et al.'s reconstruction along the normal (recon_nc)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rule", ["FSK", "FSL"])
+def test_normal_links_rebuilt_exactly_where_the_plane_says(rule):
+    """Inclined film (slope 1/2, frozen surface, exact plane with unit normal
+    (-1, 0, 2)/sqrt5 into the gas): with recon_nc every interface cell
+    rebuilds, besides its gas links, exactly the links p toward fluid nodes
+    with n.c_p > 0 of the exact plane (links tangent to it, n.c_p = 0, stay
+    streamed), each with the rule's closure of Table 1; all other links are
+    streamed unchanged."""
+    c = cases.inclined_film(h=8, rule=1 if rule == "FSL" else 0, recon_nc=1, init_exact=True)
+    o = Oracle.from_case(c)
+    dims, N = c["dims"], c.N
+    per, zs = c["params"]["periodic"], c["params"]["zshift"]
+    f0 = o.get(F_PRE)
+    ft = o.get(F_POST)
+    u0 = o.get(VEL)
+    nrm, dpl, _, _, gok = o.geometry()
+    lp = -1.0 / c["params"]["tau"]
+    o.step(1)
+    f1 = o.get(F_PRE)
+    flags = c["flags"]
+    n_exact = np.array([-1.0, 0.0, 2.0]) / math.sqrt(5.0)
+    idx = np.arange(N)
+    nb = {p: cases._neighbour_index(dims, per, zs, idx, cases.LINKS[p]) for p in range(1, 19)}
+    rebuilt = streamed = 0
+    for i in np.where(flags == cases.INTERFACE)[0]:
+        assert gok[i] and np.allclose(nrm[i], n_exact, atol=1e-12)
+        rho = f0[:, i].sum()
+        nplus = 0.5 * (f0[:, i] + f0[OPP, i]) - _eplus(rho, u0[i])
+        eb = _eplus(c["params"]["rho_G"], u0[i])
+        for p in range(1, 19):
+            q = OPP[p]
+            j = nb[p][i]  # x + c_p, the source of f_q
+            if j < 0 or flags[j] == cases.WALL:
+                continue
+            normal = flags[j] != cases.GAS and CQ[p] @ n_exact > 1e-9
+            if flags[j] == cases.GAS or normal:
+                cn = CQ[p] @ nrm[i]
+                delta = min(max(dpl[i] / cn, 0.0), 1.0) if cn > 0 else 0.5
+                up = nb[q][i]  # x - c_p
+                r = rule if (up >= 0 and flags[up] in (cases.LIQUID, cases.INTERFACE)) else "FSK"
+                a0, ab0, a1, ap, C = coeffs(r, delta, lp)
+                expect = a0 * ft[p, i] + ab0 * ft[q, i] + ap * eb[p] + C * nplus[p]
+                if a1 != 0.0:
+                    expect += a1 * ft[p, up]
+                assert f1[q, i] == pytest.approx(expect, rel=0, abs=1e-14), (i, p)
+                rebuilt += normal
+            else:
+                assert f1[q, i] == ft[q, j], (i, p)
+                streamed += 1
+    assert rebuilt > 0 and streamed > 0
+
+
+def test_normal_links_change_nothing_on_a_flat_surface():
+    """On a lattice-aligned surface every link with n.c_p > 0 already points
+    to a gas cell: recon_nc gives the same run bit for bit (film, 200 steps)."""
+    runs = []
+    for rn in (0, 1):
+        c = cases.film(nx=4, ny=4, nz=16, h=9.0, recon_nc=rn, freeze=1)
+        o = Oracle.from_case(c)
+        o.step(200)
+        runs.append(o.get(F_POST))
+    assert np.array_equal(runs[0], runs[1])
+
+
+# --------------------------------------------------------------------------
+# Thuerey's excess split along the fill-level normal (excess_split)
+# --------------------------------------------------------------------------
+def _one_converting_cell(phi_c, split):
+    """Film 4x4x16 at rest, surface at z = 8.5 (interface layer z = 8 with
+    fill 1/2), no gravity, no noise; the interface cell (1, 2, 8) starts at
+    fill phi_c so that it fills (phi_c > 1 + eps) or empties (phi_c < 0) in
+    the first step.  Returns the state after one step, the cell index and
+    the lattice dims."""
+    c = cases.film(nx=4, ny=4, nz=16, h=8.5, gx=0.0, noise_amp=0.0, excess_split=split)
+    nx, ny = 4, 4
+    i = 1 + nx * (2 + ny * 8)
+    assert c["flags"][i] == cases.INTERFACE
+    c["phi"][i] = phi_c
+    o = Oracle.from_case(c)
+    M0, L0 = o.total_mass()
+    assert o.step(1) == 0
+    M1, L1 = o.total_mass()
+    assert abs((M1 + L1) - (M0 + L0)) < 1e-12 * M0
+    return o.get(2), i, c
+
+
+@pytest.mark.parametrize("phi_c,side", [(1.05, +1), (-0.05, -1)])
+def test_weighted_excess_goes_along_the_normal(phi_c, side):
+    """A cell that fills under a flat surface (fill-level normal +z) gives
+    its excess only to the five receivers above it, in equal parts; one that
+    empties takes its deficit only from the five below.  Against the equal
+    split over all 13 receivers (5 across, 8 in the layer), each cell in the
+    layer receives -ex/13 less and each cell across ex/5 - ex/13 more, so the
+    two changes stand in the ratio -8/5, and the changes sum to zero."""
+    m_eq, i, c = _one_converting_cell(phi_c, 0)
+    m_w, _, _ = _one_converting_cell(phi_c, 1)
+    nx, ny, _ = c["dims"]
+    diff = m_w - m_eq
+    x0, y0, z0 = 1, 2, 8
+    layer, across = [], []
+    for p in range(1, 19):
+        cx_, cy_, cz_ = cases.LINKS[p]
+        j = (x0 + cx_) % nx + nx * ((y0 + cy_) % ny + ny * (z0 + cz_))
+        if cz_ == 0:
+            layer.append(diff[j])
+        elif cz_ == side:
+            across.append(diff[j])
+    layer, across = np.array(layer), np.array(across)
+    assert len(layer) == 8 and len(across) == 5
+    assert np.ptp(layer) < 1e-15 and np.ptp(across) < 1e-15
+    assert abs(layer[0]) > 1e-4
+    assert across[0] / layer[0] == pytest.approx(-8.0 / 5.0, rel=1e-12)
+    others = np.delete(diff, [i] + [
+        (x0 + int(cq[0])) % nx + nx * ((y0 + int(cq[1])) % ny + ny * (z0 + int(cq[2]))) for cq in cases.LINKS[1:]])
+    assert np.abs(others).max() < 1e-15
+    assert abs(diff.sum()) < 1e-15
+
+
+def test_mass_ledger_exact_with_weighted_split():
+    """The mass ledger (total + lost) is exact through conversions with the
+    weighted split (dam break with conversions, both rules)."""
+    for rule in (0, 1):
+        c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=rule, excess_split=1)
+        o = Oracle.from_case(c)
+        M0, L0 = o.total_mass()
+        conv = np.zeros(4)
+        for _ in range(150):
+            assert o.step(1) == 0
+            conv += np.array(o.counters()[0])
+        M1, L1 = o.total_mass()
+        assert conv[0] > 0 and conv[1] > 0
+        assert abs((M1 + L1) - (M0 + L0)) < 1e-12 * M0
