@@ -39,8 +39,6 @@ COL = (128, 192)
 TAU, MAGIC = 0.53, 0.005
 # kernels of one step: k_reset, k_segments, k_bulk, k_geom (FSL or surface
 # tension only), k_iface, 2 x k_reduce, 5 conversion kernels
-def kernels_per_step(rule, sigma=0.0):
-    return 11 + (1 if (rule != 0 or sigma != 0.0) else 0)
 STORE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 
 
@@ -266,7 +264,8 @@ def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False, stat
     nliq1, nifc1 = count_kinds(lat)
     out = dict(ms=ms, steps=steps, groups_ms=groups, timed_steps=nt, mass0=M0, mass1=M1, lost=lost,
                n_liquid=(nliq0 + nliq1) / 2, n_interface=(nifc0 + nifc1) / 2, clocks=clk,
-               device_bytes=lat.device_bytes, t_end=lat.time, bulk_loads=lat.bulk_loads)
+               device_bytes=lat.device_bytes, t_end=lat.time, bulk_loads=lat.bulk_loads,
+               launches_per_step=lat.launches_per_step)
     lat.close()
     torch.cuda.synchronize(dev)
     return out
@@ -398,7 +397,7 @@ def main():
                                "reduce": round(head["groups_ms"][2], 5), "conversions": round(head["groups_ms"][3], 5)},
         "cells": {"total": N, "liquid_avg": head["n_liquid"], "interface_avg": head["n_interface"]},
         "mass_drift_rel": (head["mass1"] - head["mass0"]) / head["mass0"],
-        "gpu_launches": kernels_per_step(args.rule) * args.steps,
+        "gpu_launches": head["launches_per_step"] * args.steps,
         "clocks": head["clocks"],
     }
     # the other precision forms on the same workload

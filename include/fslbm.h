@@ -310,6 +310,15 @@ long long fslbm_time(const fslbm_t *h);
  * NULL).  An implementation property with no counterpart in the paper. */
 int fslbm_bulk_loads(const fslbm_t *h);
 
+/* Kernel launches one fslbm_step time step makes on this handle (the
+ * per-step reset, segment list, bulk, interface geometry where the rule,
+ * surface tension, the shear term or the normal links need it, interface,
+ * the two-level mass reduction, and the conversions: one cooperative launch
+ * where the device allows it, else five; none with frozen flags), or
+ * FSLBM_ERR_ARG for NULL.  An implementation property with no counterpart in
+ * the paper. */
+int fslbm_launches_per_step(const fslbm_t *h);
+
 /* Bytes of device memory held by the handle. */
 size_t fslbm_device_bytes(const fslbm_t *h);
 

@@ -164,6 +164,18 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   h->bulk_blocks = 152 * (h->prec == FSLBM_F64 ? 4 : 8);
   h->iface_blocks = 152 * 16;  // one thread per interface cell up to 311 296 cells per round
   h->list_blocks = 152 * 8;  // 8 warps each: one warp per listed cell, 9728 cells per round
+  {
+    // the five conversion stages as one cooperative launch, two resident
+    // blocks per SM, where the device allows it; else five launches
+    int dev = 0, coop = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = h->prec == FSLBM_F64   ? convert_blocks_per_sm<P64>()
+                       : h->prec == FSLBM_F32 ? convert_blocks_per_sm<P32>()
+                                              : convert_blocks_per_sm<P16>();
+    h->coop_blocks = (coop && per_sm > 0 && sms > 0) ? sms * (per_sm < 2 ? per_sm : 2) : 0;
+  }
   h->red_blocks = 152;
   h->nparts = (h->bulk_blocks + h->iface_blocks) * 4;  // one partial per bulk and per interface warp
   if (h->nparts < 4096) h->nparts = 4096;
@@ -238,6 +250,14 @@ extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
   return h->bulk_mode == BULK_TMA ? FSLBM_LOADS_TMA : (h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC : FSLBM_LOADS_PLAIN);
 }
 
+extern "C" int fslbm_launches_per_step(const fslbm_t* h) {
+  if (!h) return FSLBM_ERR_ARG;
+  const Par& p = h->par;
+  const int geom = (p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc) ? 1 : 0;
+  const int conv = p.freeze ? 0 : (h->coop_blocks > 0 ? 1 : 5);
+  return 6 + geom + conv;  // reset, segments, bulk, interface, reduce x2
+}
+
 extern "C" void fslbm_destroy(fslbm_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
@@ -275,6 +295,7 @@ static int read_err(fslbm* h) {
   if (e & ERRB_UNSTABLE) return fail(h, FSLBM_ERR_UNSTABLE, "non-finite or non-positive density");
   if (e & ERRB_OVERFLOW) return fail(h, FSLBM_ERR_OVERFLOW, "conversion list overflow");
   if (e & ERRB_TMA) return fail(h, FSLBM_ERR_TIMEOUT, "staged loads of the bulk kernel failed (bounded wait expired)");
+  if (e & ERRB_SYNC) return fail(h, FSLBM_ERR_TIMEOUT, "grid barrier of the conversion kernel expired");
   return FSLBM_OK;
 }
 
@@ -409,7 +430,7 @@ static int step_t(fslbm* h) {
                     h->step_mass, h->st))
     return 1;
   if (mark_event(h, 3)) return 1;
-  if (!h->par.freeze && launch_conversions<P>(h->par, v, h->st, h->list_blocks)) return 1;
+  if (!h->par.freeze && launch_conversions<P>(h->par, v, h->st, h->list_blocks, h->coop_blocks)) return 1;
   if (mark_event(h, 4)) return 1;
   if (h->timing) h->timed_steps += 1;
   return 0;

@@ -16,8 +16,11 @@
 //   recv     each receiver gathers the shares of its converting neighbours in q
 //            order (deterministic, no floating-point atomics)
 //   final    F -> liquid, E -> gas, new cells -> interface, marks cleared
-// newg and empty run in one launch, newl and share in another (each pair is
-// independent): five launches.  The result does not depend on list order.
+// newg and empty run together, newl and share together (each pair is
+// independent).  The five stages run as one cooperative launch (k_convert,
+// two resident blocks per SM, grid barriers between the stages) where the
+// device allows it, else as five launches.  The result does not depend on
+// list order.
 #include "fslbm_dev.cuh"
 #include "fslbm_kernels.h"
 
@@ -62,8 +65,7 @@ __device__ __forceinline__ typename Form<P>::R rho_out(const Par& p, const View<
 
 // one warp per fill cell, lane q (1..18) takes link q
 template <int P>
-__global__ void __launch_bounds__(256) k_fill(Par p, View<P> v) {
-  pdl_begin();
+__device__ __forceinline__ void do_fill(const Par& p, const View<P>& v) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -87,6 +89,11 @@ __global__ void __launch_bounds__(256) k_fill(Par p, View<P> v) {
     }
     push(won, v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
   }
+}
+template <int P>
+__global__ void __launch_bounds__(256) k_fill(Par p, View<P> v) {
+  pdl_begin();
+  do_fill<P>(p, v);
 }
 
 // one warp per new cell: lane l (1..18) reads neighbour l's populations; the
@@ -310,8 +317,7 @@ __global__ void __launch_bounds__(256) k_newl_share(Par p, View<P> v) {
 // one thread per receiver (the lists are long late in a run): gathers the
 // shares of its converting neighbours in q order (deterministic)
 template <int P>
-__global__ void __launch_bounds__(256) k_recv(Par p, View<P> v) {
-  pdl_begin();
+__device__ __forceinline__ void do_recv(const Par& p, const View<P>& v) {
   using R = typename Form<P>::R;
   const int nr = min(load_count(&v.cnt[5]), v.cap);
   const long long sy = p.nx, sz = (long long)p.nx * p.ny;
@@ -348,8 +354,13 @@ __global__ void __launch_bounds__(256) k_recv(Par p, View<P> v) {
 }
 
 template <int P>
-__global__ void k_final(Par p, View<P> v) {
+__global__ void __launch_bounds__(256) k_recv(Par p, View<P> v) {
   pdl_begin();
+  do_recv<P>(p, v);
+}
+
+template <int P>
+__device__ __forceinline__ void do_final(const Par& p, const View<P>& v) {
   using R = typename Form<P>::R;
   int nf = min(load_count(&v.cnt[1]), v.cap), ne = min(load_count(&v.cnt[2]), v.cap);
   int ng = min(load_count(&v.cnt[3]), v.cap), nl = min(load_count(&v.cnt[4]), v.cap);
@@ -404,20 +415,93 @@ __global__ void k_final(Par p, View<P> v) {
   }
 }
 
+template <int P>
+__global__ void __launch_bounds__(256) k_final(Par p, View<P> v) {
+  pdl_begin();
+  do_final<P>(p, v);
+}
+
 // removed E cells keep a zero mark; receivers, new cells and F/E cells are
 // cleared above.  E cells that left E in k_fill carry no mark bits besides a
 // possible RECV (cleared through the receiver list).
 
+// Grid-wide barrier of the fused conversion kernel (a cooperative launch, so
+// every block is resident): thread 0 of each block arrives on the per-step
+// counter cnt[10] and waits until the blocks of this phase have arrived.  The
+// wait is bounded (about a second); on expiry it records ERRB_SYNC and goes
+// on, the step's result is then invalid and the host reports the error.
+__device__ __forceinline__ void grid_sync(unsigned* ctr, unsigned target, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    unsigned spins = 0;
+    while (*((volatile unsigned*)ctr) < target) {
+      if (++spins > (1u << 20)) {
+        atomicOr(err, ERRB_SYNC);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// the five conversion stages in one launch, separated by grid barriers
 template <int P>
-int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks) {
+__global__ void __launch_bounds__(256) k_convert(Par p, View<P> v) {
+  pdl_begin();
+  unsigned* ctr = (unsigned*)&v.cnt[10];
+  const unsigned nb = gridDim.x;
+  do_fill<P>(p, v);
+  grid_sync(ctr, nb, v.err);
+  do_newg<P>(p, v);
+  do_empty<P>(p, v);
+  grid_sync(ctr, 2 * nb, v.err);
+  do_newl<P>(p, v);
+  do_share<P>(p, v);
+  grid_sync(ctr, 3 * nb, v.err);
+  do_recv<P>(p, v);
+  grid_sync(ctr, 4 * nb, v.err);
+  do_final<P>(p, v);
+}
+
+// resident blocks of k_convert per SM (0: the fused kernel cannot be used)
+template <int P>
+int convert_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_convert<P>, 256, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+// coop_blocks > 0: the fused cooperative kernel on that many blocks (all
+// resident); else five launches of list_blocks
+template <int P>
+int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks) {
+  if (coop_blocks > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(coop_blocks);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, k_convert<P>, p, v);
+  }
   void (*ks[5])(Par, View<P>) = {k_fill<P>, k_newg_empty<P>, k_newl_share<P>, k_recv<P>, k_final<P>};
   for (auto k : ks)
     if (launch_k(k, list_blocks, 256, 0, st, p, v)) return 1;
   return 0;
 }
 
-template int launch_conversions<P64>(const Par&, const View<P64>&, cudaStream_t, int);
-template int launch_conversions<P32>(const Par&, const View<P32>&, cudaStream_t, int);
-template int launch_conversions<P16>(const Par&, const View<P16>&, cudaStream_t, int);
+template int launch_conversions<P64>(const Par&, const View<P64>&, cudaStream_t, int, int);
+template int launch_conversions<P32>(const Par&, const View<P32>&, cudaStream_t, int, int);
+template int launch_conversions<P16>(const Par&, const View<P16>&, cudaStream_t, int, int);
+template int convert_blocks_per_sm<P64>();
+template int convert_blocks_per_sm<P32>();
+template int convert_blocks_per_sm<P16>();
 
 }  // namespace fsl

@@ -43,7 +43,7 @@ __host__ __device__ constexpr R wq(int q) {
 // beyond a non-periodic face); NEARW a neighbour is a WALL cell of the lattice
 enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16, NEARW = 32, STATIC_BITS = 48 };
 enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_WSPLIT = 32 };
-enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8 };
+enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8, ERRB_SYNC = 16 };
 
 // ---------------------------------------------------------------------------
 // Precision forms
@@ -134,7 +134,7 @@ struct View {
   int* nllist;  // new from liquid
   int* rlist;   // excess receivers
   int* cnt;     // [0] ilist front [6] ilist back [1] flist [2] elist [3] ng [4] nl [5] rl [7] emptied;
-                // [8] all conversions since set; [9] fluid segments
+                // [8] all conversions since set; [9] fluid segments; [10] grid barrier of k_convert
   int cap;
   double* share;
   R* geo;            // interface geometry per list entry: [5][cap] n0, n1, n2, d, kappa (n = 0: none)

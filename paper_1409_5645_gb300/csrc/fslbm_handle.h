@@ -33,6 +33,7 @@ struct fslbm {
   double* partials;
   long long nparts;
   int bulk_blocks, iface_blocks, list_blocks, red_blocks;
+  int coop_blocks;  // blocks of the fused cooperative conversion kernel (0: five launches)
   double* red;
   double* lost;
   int* err;

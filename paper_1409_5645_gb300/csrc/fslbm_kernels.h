@@ -63,7 +63,10 @@ int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_
 int fslbm_mark(void* handle, int k);
 
 template <int P>
-int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks);
+int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks);
+// resident blocks per SM of the fused conversion kernel (0: not usable)
+template <int P>
+int convert_blocks_per_sm();
 
 int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, const double* add, double* out,
                   cudaStream_t st);

@@ -357,10 +357,11 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
   return mm;
 }
 
-// the geometry of cells within 3 of a face, out of line so that the
-// interior path of k_geom stays compact (bounded: no periodic axis)
+// the geometry of cells within 3 of a face (bounded: no periodic axis);
+// inlined, so that its Geo stays in registers (an out-of-line call measured
+// slower: the edge warps set the kernel's tail)
 template <class R, bool BOUNDED>
-__device__ __noinline__ void geometry_edge(const Par& p, const uint8_t* __restrict__ flags,
+__device__ __forceinline__ void geometry_edge(const Par& p, const uint8_t* __restrict__ flags,
                                            const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
   geometry<R, BOUNDED ? 2 : 0>(p, flags, phin, x, y, z, phic, G);
 }
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
       o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
       o[3] = G.d; o[4] = G.kap;
     } else {
-      Geo<R> G;  // (in local memory: passed out of line)
+      Geo<R> G;
       if (!p.px && !p.py && !p.pz) geometry_edge<R, true>(p, v.flags, v.phin, x, y, z, phic, G);
       else geometry_edge<R, false>(p, v.flags, v.phin, x, y, z, phic, G);
       o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
@@ -493,7 +494,7 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
 
 __global__ void k_reset(int* cnt) {
   pdl_begin();
-  if (threadIdx.x < 10 && threadIdx.x != 8) cnt[threadIdx.x] = 0;
+  if (threadIdx.x < 11 && threadIdx.x != 8) cnt[threadIdx.x] = 0;
 }
 
 int launch_reset(int* cnt, cudaStream_t st) { return launch_k(k_reset, 1, 32, 0, st, cnt); }

@@ -80,6 +80,8 @@ def lib():
             L.fslbm_time.restype = C.c_longlong
             L.fslbm_bulk_loads.argtypes = [vp]
             L.fslbm_bulk_loads.restype = C.c_int
+            L.fslbm_launches_per_step.argtypes = [vp]
+            L.fslbm_launches_per_step.restype = C.c_int
             L.fslbm_device_bytes.argtypes = [vp]
             L.fslbm_device_bytes.restype = C.c_size_t
             L.fslbm_last_error.argtypes = [vp]
@@ -304,6 +306,11 @@ class Lattice:
         """How the bulk kernel reaches its pulled values: 'async' (cp.async into
         shared memory), 'plain' (global loads) or 'tma' (tensor-map row copies)."""
         return {v: k for k, v in LOADS.items()}[self.L.fslbm_bulk_loads(self.h)]
+
+    @property
+    def launches_per_step(self) -> int:
+        """Kernel launches one time step makes on this lattice."""
+        return int(self.L.fslbm_launches_per_step(self.h))
 
     @property
     def device_bytes(self) -> int:
