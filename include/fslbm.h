@@ -68,7 +68,8 @@ enum fslbm_status {
   FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
   FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
-  FSLBM_ERR_TIMEOUT = -7,  /* a bounded device-side wait expired (staged loads of the bulk kernel) */
+  FSLBM_ERR_TIMEOUT = -7,  /* a bounded device-side wait expired (staged loads of the bulk kernel, the
+                              grid barrier of the conversion kernel) */
   FSLBM_ERR_TOO_LARGE = -8 /* beyond the fixed scratch of fslbm_mass_balance_noalloc */
 };
 
@@ -318,6 +319,18 @@ int fslbm_bulk_loads(const fslbm_t *h);
  * FSLBM_ERR_ARG for NULL.  An implementation property with no counterpart in
  * the paper. */
 int fslbm_launches_per_step(const fslbm_t *h);
+
+/* Self-check of the grid barrier between the conversion stages: one
+ * cooperative launch of it (two resident blocks per SM) on `stream` (NULL =
+ * legacy default).  expire = 0: the barrier completes; expire = 1: it waits
+ * for one block more than exists, so its bounded wait runs out after about a
+ * second and records the expiry, the way a barrier that never completes ends
+ * in a step.  Returns FSLBM_OK when it completed, FSLBM_ERR_TIMEOUT when it
+ * expired, FSLBM_ERR_CUDA when the device refuses the cooperative launch,
+ * FSLBM_ERR_ARG for another expire.  Synchronises the stream; the context
+ * stays usable either way.  An implementation property with no counterpart
+ * in the paper. */
+int fslbm_check_grid_barrier(int expire, void *stream);
 
 /* Bytes of device memory held by the handle. */
 size_t fslbm_device_bytes(const fslbm_t *h);

@@ -250,6 +250,28 @@ extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
   return h->bulk_mode == BULK_TMA ? FSLBM_LOADS_TMA : (h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC : FSLBM_LOADS_PLAIN);
 }
 
+extern "C" int fslbm_check_grid_barrier(int expire, void* stream) {
+  if (expire < 0 || expire > 1) return FSLBM_ERR_ARG;
+  int dev = 0, coop = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FSLBM_ERR_CUDA;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop || sms <= 0) return FSLBM_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* buf = nullptr;  // [0] barrier counter, [1] error bits
+  if (cudaMalloc(&buf, 2 * sizeof(int)) != cudaSuccess) return FSLBM_ERR_OOM;
+  int rc = FSLBM_OK, host[2] = {0, 0};
+  if (cudaMemsetAsync(buf, 0, 2 * sizeof(int), st) != cudaSuccess ||
+      launch_barrier_check((unsigned*)buf, buf + 1, sms * 2, (unsigned)expire, st) != cudaSuccess ||
+      cudaMemcpyAsync(host, buf, sizeof host, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    rc = FSLBM_ERR_CUDA;
+  else if (host[1] & ERRB_SYNC)
+    rc = FSLBM_ERR_TIMEOUT;
+  cudaFree(buf);
+  return rc;
+}
+
 extern "C" int fslbm_launches_per_step(const fslbm_t* h) {
   if (!h) return FSLBM_ERR_ARG;
   const Par& p = h->par;

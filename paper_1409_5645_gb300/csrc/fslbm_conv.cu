@@ -467,6 +467,25 @@ __global__ void __launch_bounds__(256) k_convert(Par p, View<P> v) {
   do_final<P>(p, v);
 }
 
+// self-check of the barrier: one grid_sync waiting for `extra` blocks more
+// than the grid has (extra = 1: nothing completes it, the bounded wait runs out)
+__global__ void __launch_bounds__(256) k_barrier_check(unsigned* ctr, unsigned extra, int* err) {
+  grid_sync(ctr, gridDim.x + extra, err);
+}
+
+int launch_barrier_check(unsigned* ctr, int* err, int blocks, unsigned extra, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_barrier_check, ctr, extra, err);
+}
+
 // resident blocks of k_convert per SM (0: the fused kernel cannot be used)
 template <int P>
 int convert_blocks_per_sm() {

@@ -64,6 +64,9 @@ int fslbm_mark(void* handle, int k);
 
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks);
+// one cooperative launch of the conversion kernel's grid barrier on `blocks`
+// blocks, waiting for `extra` blocks more than exist (self-check)
+int launch_barrier_check(unsigned* ctr, int* err, int blocks, unsigned extra, cudaStream_t st);
 // resident blocks per SM of the fused conversion kernel (0: not usable)
 template <int P>
 int convert_blocks_per_sm();

@@ -82,6 +82,8 @@ def lib():
             L.fslbm_bulk_loads.restype = C.c_int
             L.fslbm_launches_per_step.argtypes = [vp]
             L.fslbm_launches_per_step.restype = C.c_int
+            L.fslbm_check_grid_barrier.argtypes = [ip, vp]
+            L.fslbm_check_grid_barrier.restype = C.c_int
             L.fslbm_device_bytes.argtypes = [vp]
             L.fslbm_device_bytes.restype = C.c_size_t
             L.fslbm_last_error.argtypes = [vp]
@@ -90,6 +92,18 @@ def lib():
             L.fslbm_destroy.restype = None
             _lib = L
     return _lib
+
+
+def check_grid_barrier(expire: bool, stream=None) -> str:
+    """Self-check of the conversion kernel's grid barrier (one cooperative
+    launch): 'ok' when it completed, 'timeout' when its bounded wait ran out
+    (expire=True makes it wait for a block that does not exist)."""
+    rc = lib().fslbm_check_grid_barrier(1 if expire else 0, stream)
+    if rc == 0:
+        return "ok"
+    if rc == -7:
+        return "timeout"
+    raise FslbmError(rc, "grid barrier self-check")
 
 
 def _is_torch_cuda(a) -> bool:

@@ -56,3 +56,18 @@ def test_dam_break_parity_all_tracking_variants():
                         recon_nc=1, excess_split=1, ub_extrap=1, stress=1)
     _, _, conv = run_parity(c, 150, every=1)
     assert conv[0] > 0 and conv[1] > 0
+
+
+def test_grid_barrier_bounded_wait():
+    """The grid barrier between the conversion stages completes, and when
+    nothing completes it (it waits for one block more than exist) its bounded
+    wait runs out with FSLBM_ERR_TIMEOUT instead of hanging; the context stays
+    usable and a lattice steps normally afterwards."""
+    import time
+    from paper_1409_5645_gb300 import fslbm
+    assert fslbm.check_grid_barrier(False) == "ok"
+    t0 = time.time()
+    assert fslbm.check_grid_barrier(True) == "timeout"
+    assert time.time() - t0 < 10.0
+    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1)
+    run_parity(c, 40, every=10)
