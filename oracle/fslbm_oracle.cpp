@@ -1,5 +1,5 @@
-// fslbm_oracle.cpp -- plain, slow, single-threaded FP64 CPU oracle of one
-// free-surface lattice Boltzmann (FSLBM) time step on D3Q19.
+// fslbm_oracle.cpp -- plain, slow FP64 CPU oracle of one free-surface
+// lattice Boltzmann (FSLBM) time step on D3Q19.
 //
 // TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, calls or
 // includes this file; only the test-suite, the smoke check and the CPU
@@ -30,13 +30,20 @@
 // sorting) taken on the value part.
 //
 // Build: g++ -O2 -ffp-contract=off -shared -fPIC (no fused multiply-add, so
-// each operation is one IEEE rounding in source order).
+// each operation is one IEEE rounding in source order).  The same source
+// built with -fopenmp (liborc_omp.so, for the all-core CPU timing only) runs
+// the per-cell loops of stages 1-4 over threads; each iteration writes only
+// its own cell, every sum keeps its order, and the conversions stay serial,
+// so both builds give the same bits.
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace orc {
 
@@ -489,6 +496,7 @@ struct Sim {
 
   // 1. geometry at time t
   void stage_geometry() {
+#pragma omp parallel for schedule(dynamic, 4096)
     for (long i = 0; i < N; ++i) {
       if (flag[i] != IFC) continue;
       T n[3], d, k;
@@ -504,6 +512,7 @@ struct Sim {
     clear_scratch();
     stage_geometry();
     // 2. collision at time t (Eq. lbe2)
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < NN; ++i) {
       if (!fluid(flag[i])) continue;
       T fq[Q], out[Q], np[Q], rho, u[3];
@@ -528,6 +537,7 @@ struct Sim {
     const long NN = N;
     clear_scratch();
     stage_geometry();
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < NN; ++i) {
       if (!fluid(flag[i])) continue;
       T r = T(0), j[3] = {T(0), T(0), T(0)};
@@ -558,6 +568,8 @@ struct Sim {
 
     // 3. pull streaming (Eq. lbe1) with closures for the missing populations
     std::vector<T> fn((size_t)Q * NN, T(0));
+    int bad_state = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(| : bad_state)
     for (long i = 0; i < NN; ++i) {
       if (!fluid(flag[i])) continue;
       for (int q = 0; q < Q; ++q) {
@@ -569,15 +581,17 @@ struct Sim {
         } else if (ts == WALL) {
           fn[(size_t)q * NN + i] = wall_closure(i, q);
         } else {  // gas source
-          if (flag[i] != IFC) { st = ERR_STATE; fn[(size_t)q * NN + i] = ft[(size_t)opp[q] * NN + i]; continue; }
+          if (flag[i] != IFC) { bad_state = 1; fn[(size_t)q * NN + i] = ft[(size_t)opp[q] * NN + i]; continue; }
           fn[(size_t)q * NN + i] = free_surface_closure(i, q);
         }
       }
     }
+    if (bad_state) st = ERR_STATE;
 
     // 4. mass exchange (non-frozen), Sec. 2.3 advection of phi
     std::vector<T> mn = m;
     if (!p.freeze) {
+#pragma omp parallel for schedule(dynamic, 4096)
       for (long i = 0; i < NN; ++i) {
         if (flag[i] != IFC) continue;
         T dm = T(0);
@@ -596,18 +610,22 @@ struct Sim {
 
     // density at t+1 and instability check
     std::vector<T> rho1(NN, T(0));
+    int unstable = 0;
+#pragma omp parallel for schedule(static) reduction(| : unstable)
     for (long i = 0; i < NN; ++i) {
       if (!fluid(flag[i])) continue;
       T r = T(0);
       for (int q = 0; q < Q; ++q) r += f[(size_t)q * NN + i];
       rho1[i] = r;
-      if (!(val(r) > 0.0) || !std::isfinite(val(r))) st = (st == OK ? ERR_UNSTABLE : st);
+      if (!(val(r) > 0.0) || !std::isfinite(val(r))) unstable = 1;
     }
+    if (unstable && st == OK) st = ERR_UNSTABLE;
 
     // 5. conversions (non-frozen)
     cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
     if (!p.freeze) {
       convert(rho1);
+#pragma omp parallel for schedule(static)
       for (long i = 0; i < NN; ++i)
         if (flag[i] == IFC) phi[i] = m[i] / rho1[i];
     }
@@ -1035,6 +1053,18 @@ extern "C" int orc_step_from_post(void* hv, const uint8_t* flags, const double* 
   s->lost = 0.0;
   int r = s->step_from_post(ft);
   return r;
+}
+
+// Threads of the OpenMP build (n > 0 sets them); returns the count in use,
+// 1 for the plain build.
+extern "C" int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 extern "C" int orc_step(void* hv, int n) {

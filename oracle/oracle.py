@@ -17,29 +17,33 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fslbm_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liborc_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 F_PRE, F_POST, MASS, PHI, RHO, VEL = 0, 1, 2, 3, 4, 5
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no FMA contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction); ``omp=True`` builds
+    the OpenMP variant of the same source (all-core CPU timing only)."""
     os.makedirs(_BUILD, exist_ok=True)
-    stamp = os.path.join(_BUILD, "STAMP")
+    path = _LIB_OMP_PATH if omp else _LIB_PATH
+    stamp = os.path.join(_BUILD, "STAMP_omp" if omp else "STAMP")
     try:
         same_machine = open(stamp).read().strip() == platform.machine()
     except OSError:
         same_machine = False
-    if (force or not same_machine or not os.path.exists(_LIB_PATH)
-            or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC",
-                               _SRC, "-o", tmp])
-        os.replace(tmp, _LIB_PATH)
+    if (force or not same_machine or not os.path.exists(path)
+            or os.path.getmtime(path) < os.path.getmtime(_SRC)):
+        tmp = path + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC"]
+                              + (["-fopenmp"] if omp else []) + [_SRC, "-o", tmp])
+        os.replace(tmp, path)
         with open(stamp, "w") as fh:
             fh.write(platform.machine())
-    return _LIB_PATH
+    return path
 
 
 class Params(C.Structure):
@@ -54,11 +58,11 @@ class Params(C.Structure):
                 ("excess_split", C.c_int)]
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if (_lib_omp if omp else _lib) is None:
+            L = C.CDLL(build(omp=omp))
             vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
             u8p = C.POINTER(C.c_uint8)
             L.orc_create.restype = vp
@@ -79,8 +83,18 @@ def lib():
             L.orc_counters.argtypes = [vp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
             L.orc_seed.argtypes = [vp, C.c_double, dp, dp]
             L.orc_step_from_post.argtypes = [vp, u8p, dp, dp, dp]
-            _lib = L
-    return _lib
+            L.orc_threads.restype = C.c_int
+            L.orc_threads.argtypes = [ip]
+            if omp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if omp else _lib
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build (n > 0 sets them); returns the count in use."""
+    return int(lib(omp=True).orc_threads(int(n)))
 
 
 def _dp(a):
@@ -123,10 +137,11 @@ def make_params(dims, p) -> Params:
 
 
 class Oracle:
-    """One lattice in the oracle.  ``dual=True`` carries one tangent."""
+    """One lattice in the oracle.  ``dual=True`` carries one tangent;
+    ``omp=True`` runs it on the OpenMP build (same results)."""
 
-    def __init__(self, dims, params, dual: bool = False):
-        self.L = lib()
+    def __init__(self, dims, params, dual: bool = False, omp: bool = False):
+        self.L = lib(omp)
         self.dims = tuple(int(v) for v in dims)
         self.N = int(np.prod(self.dims))
         self.params = dict(params)
@@ -137,10 +152,10 @@ class Oracle:
         self.dual = dual
 
     @classmethod
-    def from_case(cls, case, dual: bool = False, **override):
+    def from_case(cls, case, dual: bool = False, omp: bool = False, **override):
         p = dict(case["params"])
         p.update(override)
-        o = cls(case["dims"], p, dual=dual)
+        o = cls(case["dims"], p, dual=dual, omp=omp)
         o.init(case)
         return o
 

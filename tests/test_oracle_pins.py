@@ -785,3 +785,22 @@ def test_mass_ledger_exact_with_weighted_split():
         M1, L1 = o.total_mass()
         assert conv[0] > 0 and conv[1] > 0
         assert abs((M1 + L1) - (M0 + L0)) < 1e-12 * M0
+
+
+def test_openmp_build_gives_the_same_bits():
+    """The OpenMP build of the oracle (used only to time it on all cores)
+    gives bit for bit the results of the plain build: dam break with
+    conversions and a capillary wave with the shear term and all tracking
+    variants."""
+    from oracle import oracle as orc
+    orc.threads(4)
+    for c in (cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1),
+              cases.standing_wave(n=16, depth=8.0, amp=1.0, tau=0.6, g=1e-4, sigma=5e-3, phi_noise=1e-4,
+                                  stress=1, ub_extrap=1, recon_nc=1, excess_split=1)):
+        a = Oracle.from_case(c)
+        b = Oracle.from_case(c, omp=True)
+        assert a.step(60) == 0 and b.step(60) == 0
+        for fid in (F_POST, 2, PHI):
+            assert np.array_equal(a.get(fid), b.get(fid))
+        assert np.array_equal(a.flags(), b.flags())
+        assert a.total_mass() == b.total_mass()
