@@ -250,6 +250,9 @@ extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
   return h->bulk_mode == BULK_TMA ? FSLBM_LOADS_TMA : (h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC : FSLBM_LOADS_PLAIN);
 }
 
+// the step's mass reduction runs inside the cooperative conversion kernel
+static bool fold_reduce(const fslbm* h) { return !h->par.freeze && h->coop_blocks >= h->red_blocks; }
+
 extern "C" int fslbm_check_grid_barrier(int expire, void* stream) {
   if (expire < 0 || expire > 1) return FSLBM_ERR_ARG;
   int dev = 0, coop = 0, sms = 0;
@@ -277,7 +280,8 @@ extern "C" int fslbm_launches_per_step(const fslbm_t* h) {
   const Par& p = h->par;
   const int geom = (p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc) ? 1 : 0;
   const int conv = p.freeze ? 0 : (h->coop_blocks > 0 ? 1 : 5);
-  return 6 + geom + conv;  // reset, segments, bulk, interface, reduce x2
+  const int reduce = fold_reduce(h) ? 0 : 2;
+  return 4 + geom + reduce + conv;  // reset, segments, bulk, interface
 }
 
 extern "C" void fslbm_destroy(fslbm_t* h) {
@@ -448,11 +452,23 @@ static int step_t(fslbm* h) {
                              h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr))
     return 1;
   if (mark_event(h, 2)) return 1;
-  if (launch_reduce(h->partials, (long long)(h->bulk_blocks + h->iface_blocks) * 4, h->red, h->red_blocks, h->lost,
-                    h->step_mass, h->st))
+  // the mass reduction rides in the cooperative conversion kernel where that runs
+  MassReduce mr = {};
+  const long long nparts = (long long)(h->bulk_blocks + h->iface_blocks) * 4;
+  if (fold_reduce(h)) {
+    mr.in = h->partials;
+    mr.n = nparts;
+    mr.chunk = (nparts + h->red_blocks - 1) / h->red_blocks;
+    if (mr.chunk < 1) mr.chunk = 1;
+    mr.nb = (int)((nparts + mr.chunk - 1) / mr.chunk);
+    mr.tmp = h->red;
+    mr.add = h->lost;
+    mr.out = h->step_mass;
+  } else if (launch_reduce(h->partials, nparts, h->red, h->red_blocks, h->lost, h->step_mass, h->st)) {
     return 1;
+  }
   if (mark_event(h, 3)) return 1;
-  if (!h->par.freeze && launch_conversions<P>(h->par, v, h->st, h->list_blocks, h->coop_blocks)) return 1;
+  if (!h->par.freeze && launch_conversions<P>(h->par, v, h->st, h->list_blocks, h->coop_blocks, mr)) return 1;
   if (mark_event(h, 4)) return 1;
   if (h->timing) h->timed_steps += 1;
   return 0;

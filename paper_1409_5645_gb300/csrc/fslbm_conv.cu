@@ -448,14 +448,25 @@ __device__ __forceinline__ void grid_sync(unsigned* ctr, unsigned target, int* e
   __syncthreads();
 }
 
-// the five conversion stages in one launch, separated by grid barriers
+// the five conversion stages in one launch, separated by grid barriers; the
+// step's two-level mass reduction rides along in the first two stages (the
+// same chunks and order as the stand-alone reduction, before any excess
+// reaches the lost ledger)
 template <int P>
-__global__ void __launch_bounds__(256) k_convert(Par p, View<P> v) {
+__global__ void __launch_bounds__(256) k_convert(Par p, View<P> v, MassReduce mr) {
   pdl_begin();
   unsigned* ctr = (unsigned*)&v.cnt[10];
   const unsigned nb = gridDim.x;
+  if ((int)blockIdx.x < mr.nb) {
+    const double t = block_chunk_sum(mr.in, mr.n, mr.chunk, blockIdx.x);
+    if (threadIdx.x == 0) mr.tmp[blockIdx.x] = t;
+  }
   do_fill<P>(p, v);
   grid_sync(ctr, nb, v.err);
+  if (mr.nb > 0 && blockIdx.x == 0) {
+    const double t = block_chunk_sum(mr.tmp, mr.nb, mr.nb, 0);
+    if (threadIdx.x == 0) *mr.out = t + *mr.add;
+  }
   do_newg<P>(p, v);
   do_empty<P>(p, v);
   grid_sync(ctr, 2 * nb, v.err);
@@ -497,7 +508,8 @@ int convert_blocks_per_sm() {
 // coop_blocks > 0: the fused cooperative kernel on that many blocks (all
 // resident); else five launches of list_blocks
 template <int P>
-int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks) {
+int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks,
+                       const MassReduce& mr) {
   if (coop_blocks > 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(coop_blocks);
@@ -508,7 +520,8 @@ int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return (int)cudaLaunchKernelEx(&cfg, k_convert<P>, p, v);
+    if (mr.nb > coop_blocks) return (int)cudaErrorInvalidValue;
+    return (int)cudaLaunchKernelEx(&cfg, k_convert<P>, p, v, mr);
   }
   void (*ks[5])(Par, View<P>) = {k_fill<P>, k_newg_empty<P>, k_newl_share<P>, k_recv<P>, k_final<P>};
   for (auto k : ks)
@@ -516,9 +529,9 @@ int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list
   return 0;
 }
 
-template int launch_conversions<P64>(const Par&, const View<P64>&, cudaStream_t, int, int);
-template int launch_conversions<P32>(const Par&, const View<P32>&, cudaStream_t, int, int);
-template int launch_conversions<P16>(const Par&, const View<P16>&, cudaStream_t, int, int);
+template int launch_conversions<P64>(const Par&, const View<P64>&, cudaStream_t, int, int, const MassReduce&);
+template int launch_conversions<P32>(const Par&, const View<P32>&, cudaStream_t, int, int, const MassReduce&);
+template int launch_conversions<P16>(const Par&, const View<P16>&, cudaStream_t, int, int, const MassReduce&);
 template int convert_blocks_per_sm<P64>();
 template int convert_blocks_per_sm<P32>();
 template int convert_blocks_per_sm<P16>();

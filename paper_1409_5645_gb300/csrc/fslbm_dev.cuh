@@ -651,4 +651,35 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
   }
 }
 
+// Fixed-order sum of chunk b of in[0, n) by the calling block of 256 threads:
+// strided per-thread sums, warp shuffles, the eight warp sums in a fixed
+// tree.  Every thread of the block must call it; the result is on thread 0.
+__device__ __forceinline__ double block_chunk_sum(const double* __restrict__ in, long long n, long long chunk,
+                                                  long long b) {
+  __shared__ double red[8];
+  const long long lo = b * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  double s = 0.0;
+  for (long long k = lo + threadIdx.x; k < hi; k += blockDim.x) s += in[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  const double t = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+  __syncthreads();  // red is reused by the next call
+  return t;
+}
+
+// The step's mass reduction when the conversion kernel carries it: nb chunks
+// of `chunk` partials summed into tmp, then tmp summed into *out (+ *add, the
+// lost ledger).  nb = 0: the reduction runs on its own.
+struct MassReduce {
+  const double* in;
+  long long n, chunk;
+  int nb;
+  double* tmp;
+  const double* add;
+  double* out;
+};
+
 }  // namespace fsl

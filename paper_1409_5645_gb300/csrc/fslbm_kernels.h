@@ -63,7 +63,8 @@ int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_
 int fslbm_mark(void* handle, int k);
 
 template <int P>
-int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks);
+int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks,
+                       const MassReduce& mr);
 // one cooperative launch of the conversion kernel's grid barrier on `blocks`
 // blocks, waiting for `extra` blocks more than exist (self-check)
 int launch_barrier_check(unsigned* ctr, int* err, int blocks, unsigned extra, cudaStream_t st);

@@ -444,17 +444,8 @@ __global__ void __launch_bounds__(128, (EXT ? 2 : (P == P64 ? 3 : 5))) k_iface(P
 __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ in, long long n, long long chunk,
                                                 double* __restrict__ out, const double* add, double* final_out) {
   pdl_begin();
-  __shared__ double red[8];
-  long long lo = (long long)blockIdx.x * chunk;
-  long long hi = lo + chunk < n ? lo + chunk : n;
-  double s = 0.0;
-  for (long long k = lo + threadIdx.x; k < hi; k += blockDim.x) s += in[k];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
+  const double t = block_chunk_sum(in, n, chunk, blockIdx.x);
   if (threadIdx.x == 0) {
-    double t = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
     out[blockIdx.x] = t;
     if (final_out) *final_out = t + (add ? *add : 0.0);
   }

@@ -71,3 +71,23 @@ def test_grid_barrier_bounded_wait():
     assert time.time() - t0 < 10.0
     c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1)
     run_parity(c, 40, every=10)
+
+
+@pytest.mark.parametrize("freeze", [0, 1])
+def test_step_mass_equals_recount(freeze):
+    """The mass reduced inside each step (by the cooperative conversion kernel,
+    or by the stand-alone reduction with frozen flags) equals the full recount
+    after the step, whose conversions conserve it (FP64, dam break with
+    conversions; inclined film with a frozen interface)."""
+    from paper_1409_5645_gb300 import fslbm
+    if freeze:
+        c = cases.inclined_film(h=8, rule=1)
+    else:
+        c = cases.dam_break(nx=24, ny=12, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1)
+    g = fslbm.Lattice.from_case(c, precision="f64")
+    for _ in range(60):
+        g.step(1)
+        ms = g.step_mass()
+        M, _ = g.total_mass()
+        assert abs(ms - M) <= 1e-12 * M, (ms, M)
+    g.close()
