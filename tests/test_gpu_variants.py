@@ -91,3 +91,45 @@ def test_step_mass_equals_recount(freeze):
         M, _ = g.total_mass()
         assert abs(ms - M) <= 1e-12 * M, (ms, M)
     g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("f32", 2e-3), ("f16", 2e-2)])
+def test_reduced_precision_with_all_options(precision, tol):
+    """The extended interface kernel in the FP32 and FP16-storage forms (shear
+    term, extrapolated u_b, normal links, weighted split): 300 steps of a dam
+    break stay finite, keep the mass ledger, convert cells, and stay near the
+    FP64 run (mean fill-level difference, share of cells of another kind)."""
+    from paper_1409_5645_gb300 import fslbm
+    c = cases.dam_break(nx=32, ny=12, nz=20, col_x=10, col_z=14, tau=0.6, g=2e-4, rule=1,
+                        stress=1, ub_extrap=1, recon_nc=1, excess_split=1)
+    out = {}
+    for prec in ("f64", precision):
+        g = fslbm.Lattice.from_case(c, precision=prec)
+        M0, _ = g.total_mass()
+        conv = np.zeros(4)
+        for _ in range(30):
+            g.step(10)
+            conv += np.array(g.counters()[:4])
+        M1, _ = g.total_mass()
+        st = g.get(fslbm.FIELD_PHI | fslbm.FIELD_FLAGS)
+        out[prec] = (M0, M1, conv, st["phi"], st["flags"])
+        g.close()
+    M0, M1, conv, phi, fl = out[precision]
+    assert np.isfinite(phi).all() and conv[0] + conv[1] > 0
+    assert abs(M1 - M0) / M0 < tol
+    assert np.mean(np.abs(phi - out["f64"][3])) < 0.02
+    assert np.mean(fl != out["f64"][4]) < 0.02
+
+
+def test_launches_per_step():
+    """The launch count a step reports: reset, segments, bulk, interface,
+    the geometry kernel where the rule needs it, and the conversions with the
+    mass reduction in one cooperative launch (two reduction launches and no
+    conversions with frozen flags)."""
+    from paper_1409_5645_gb300 import fslbm
+    film = cases.film(nx=4, ny=4, nz=16, h=9.0)
+    expect = {(1, 0): 6, (0, 0): 5, (1, 1): 7, (0, 1): 6}
+    for (rule, freeze), n in expect.items():
+        g = fslbm.Lattice(film["dims"], dict(film["params"], rule=rule, freeze=freeze))
+        assert g.launches_per_step == n, (rule, freeze, g.launches_per_step)
+        g.close()
