@@ -468,7 +468,19 @@ static int step_t(fslbm* h) {
     return 1;
   }
   if (mark_event(h, 3)) return 1;
-  if (!h->par.freeze && launch_conversions<P>(h->par, v, h->st, h->list_blocks, h->coop_blocks, mr)) return 1;
+  if (!h->par.freeze) {
+    int rc = launch_conversions<P>(h->par, v, h->st, h->list_blocks, h->coop_blocks, mr);
+    if (rc == (int)cudaErrorCooperativeLaunchTooLarge && h->coop_blocks > 0) {
+      // the device cannot hold the cooperative grid now (e.g. shared with
+      // other work): five launches and the stand-alone reduction from here on
+      cudaGetLastError();
+      h->coop_blocks = 0;
+      if (mr.nb > 0 && launch_reduce(h->partials, nparts, h->red, h->red_blocks, h->lost, h->step_mass, h->st))
+        return 1;
+      rc = launch_conversions<P>(h->par, v, h->st, h->list_blocks, 0, MassReduce{});
+    }
+    if (rc) return 1;
+  }
   if (mark_event(h, 4)) return 1;
   if (h->timing) h->timed_steps += 1;
   return 0;
