@@ -1,7 +1,10 @@
 """Interface-tracking variants of the works the paper's tracking follows
 (Sec. 4.4, Sec. 6) on the CUDA path, against the oracle: the reconstruction of
 the links along the surface normal (recon_nc) and the excess split along the
-fill-level normal (excess_split)."""
+fill-level normal (excess_split); the grid barrier of the conversion kernel,
+the step's mass reduction and launch count, and the extended interface kernel
+in the reduced-precision forms."""
+import numpy as np
 import pytest
 
 from gpu_util import run_parity
