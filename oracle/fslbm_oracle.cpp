@@ -462,10 +462,78 @@ struct Sim {
         kappa = T(-1.0) * num / (q2 * sqrt(q2));
       }
     } else {
+      // curvature only: heights along the other axes, by decreasing |n_a|,
+      // where the columns along the dominant one are not closed
+      if (p.sigma != 0.0) {
+        int ax[2] = {(a + 1) % 3, (a + 2) % 3};
+        if (std::fabs(val(n[ax[1]])) > std::fabs(val(n[ax[0]]))) std::swap(ax[0], ax[1]);
+        bool got = false;
+        for (int t = 0; t < 2 && !got; ++t) got = height_curvature(i, ax[t], val(n[ax[t]]) > 0 ? 1 : -1, kappa);
+        if (!got) kappa = normal_divergence(i, n);
+      }
       T len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
       for (int k = 0; k < 3; ++k) n[k] = n[k] / len;
       d = plic_offset(n, phi_of(i));
     }
+  }
+
+  // Curvature as the divergence of the unit Parker-Youngs normal by central
+  // differences over the six face neighbours; a neighbour without a normal
+  // takes the cell's own (n0, not normalised on entry).
+  T normal_divergence(long i, const T n0[3]) const {
+    T l0 = sqrt(n0[0] * n0[0] + n0[1] * n0[1] + n0[2] * n0[2]);
+    T k = T(0);
+    for (int a = 0; a < 3; ++a) {
+      T comp[2];
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        int o[3] = {0, 0, 0};
+        o[a] = sgn ? 1 : -1;
+        long j = nbr(i, o[0], o[1], o[2]);
+        T nj[3] = {n0[0], n0[1], n0[2]};
+        T lj = l0;
+        if (j >= 0 && type(j) != WALL) {
+          T m[3];
+          normal_py(j, m);
+          T lm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+          if (val(lm) > 1e-12) { nj[0] = m[0]; nj[1] = m[1]; nj[2] = m[2]; lj = lm; }
+        }
+        comp[sgn] = nj[a] / lj;
+      }
+      k += T(0.5) * (comp[1] - comp[0]);
+    }
+    return k;
+  }
+
+  // Curvature from the heights over 3x3 columns of 7 cells along axis a,
+  // gas side s; false (kappa untouched) where a column is not closed.
+  bool height_curvature(long i, int a, int s, T& kappa) const {
+    const int b = (a == 0) ? 1 : 0;
+    const int c = (a == 2) ? 1 : 2;
+    T H[3][3];
+    for (int ib = -1; ib <= 1; ++ib)
+      for (int ic = -1; ic <= 1; ++ic) {
+        T sum = T(0);
+        for (int k = -3; k <= 3; ++k) {
+          int o[3] = {0, 0, 0};
+          o[a] = k; o[b] = ib; o[c] = ic;
+          long j = nbr(i, o[0], o[1], o[2]);
+          uint8_t ty = type(j);
+          if (ty == WALL) return false;
+          if (k == -3 * s && ty != LIQ) return false;
+          if (k == 3 * s && ty != GAS) return false;
+          sum += phi_of(j);
+        }
+        H[ib + 1][ic + 1] = sum;
+      }
+    T Hb = T(0.5) * (H[2][1] - H[0][1]);
+    T Hc = T(0.5) * (H[1][2] - H[1][0]);
+    T Hbb = H[2][1] - T(2.0) * H[1][1] + H[0][1];
+    T Hcc = H[1][2] - T(2.0) * H[1][1] + H[1][0];
+    T Hbc = T(0.25) * (H[2][2] - H[2][0] - H[0][2] + H[0][0]);
+    T q2 = T(1.0) + Hb * Hb + Hc * Hc;
+    T num = Hbb * (T(1.0) + Hc * Hc) + Hcc * (T(1.0) + Hb * Hb) - T(2.0) * Hb * Hc * Hbc;
+    kappa = T(-1.0) * num / (q2 * sqrt(q2));
+    return true;
   }
 
   // Link fraction along c_q for a gas link: x_w = x_b + delta c_q lies on the

@@ -294,6 +294,35 @@ def skew_couette(h=8, slope=0.25, period=1, shear=1e-3, tau=1.1, rule=1, magic=0
                 h=h, shear=shear, u_exact=u_exact, d=d, t_hat=t_hat)
 
 
+def droplet(n=24, R=6.0, centre=None, sigma=1e-3, tau=0.8, rule=1, sub=16, **kw) -> Case:
+    """Spherical liquid droplet of radius R at rest in gas (fully periodic
+    n^3 box, no gravity), frozen interface, surface tension sigma: the static
+    Laplace test (Sec. 2.3, Laplace pressure).  Fill levels are the liquid
+    fraction of each cell, sampled on sub^3 points (cells away from the
+    surface are exactly 0 or 1)."""
+    dims = (n, n, n)
+    N = n ** 3
+    if centre is None:
+        centre = (n / 2 + 0.13, n / 2 - 0.21, n / 2 + 0.07)  # off the lattice symmetry
+    i = np.arange(N)
+    x, y, z = i % n + 0.5, (i // n) % n + 0.5, i // (n * n) + 0.5
+    r = np.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2)
+    phi = np.where(r < R, 1.0, 0.0)
+    near = np.abs(r - R) < 1.0
+    o = (np.arange(sub) + 0.5) / sub - 0.5
+    ox, oy, oz = np.meshgrid(o, o, o, indexing="ij")
+    ox, oy, oz = ox.ravel(), oy.ravel(), oz.ravel()
+    for j in np.where(near)[0]:
+        rr = np.sqrt((x[j] + ox - centre[0]) ** 2 + (y[j] + oy - centre[1]) ** 2 + (z[j] + oz - centre[2]) ** 2)
+        phi[j] = np.mean(rr < R)
+    params = default_params(tau=tau, rule=rule, sigma=sigma, periodic=(1, 1, 1), freeze=1)
+    params.update(kw)
+    flags = classify(dims, params["periodic"], 0, phi, sharp=True)
+    keep = (flags == INTERFACE) | (flags == GAS)
+    return Case(dims=dims, params=params, flags=flags, rho=np.ones(N), u=np.zeros((N, 3)),
+                phi=np.where(keep, phi, 0.0), noise=None, wall_delta=None, R=R, centre=centre, r=r)
+
+
 def standing_wave(n=128, depth=64.0, amp=2.0, tau=0.55, g=2e-5, sigma=1e-4,
                   phi_noise=1e-4, seed=SEED, quad=8, rule=1, **kw) -> Case:
     """Standing gravity-capillary wave in an n^3 box with walls on all faces:

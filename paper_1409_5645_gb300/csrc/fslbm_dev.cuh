@@ -503,11 +503,111 @@ struct Geo {
   R H[9];        // column heights H[(ib+1)*3 + (ic+1)]
 };
 
+// Curvature where the height columns along the dominant axis are not closed
+// (surface tension only; rare, so out of line and on the general neighbour
+// rule): heights along the two other axes by decreasing |n_a|, else the
+// divergence of the unit Parker-Youngs normal by central differences over the
+// six face neighbours (a neighbour without a normal, or a wall, takes the
+// cell's own).  n: the cell's Parker-Youngs normal -grad phi, not normalised.
+template <class R>
+__device__ __forceinline__ R fill_at(const Par& p, const uint8_t* __restrict__ flags, const R* __restrict__ phin,
+                                     long long j, uint8_t& kj) {
+  kj = kind_at(flags, j);
+  if (kj == LIQ) return R(1);
+  if (kj == IFC || (kj == GAS && p.freeze)) return phin[j];
+  return R(0);
+}
+template <class R>
+__device__ __forceinline__ bool height_curvature(const Par& p, const uint8_t* __restrict__ flags,
+                                                 const R* __restrict__ phin, int x, int y, int z, int a, int s,
+                                                 R& kap) {
+  const int b = (a == 0) ? 1 : 0;
+  const int c = (a == 2) ? 1 : 2;
+  R H[9];
+  for (int ib = -1; ib <= 1; ++ib)
+    for (int ic = -1; ic <= 1; ++ic) {
+      R sum = R(0);
+      for (int k = -3; k <= 3; ++k) {
+        int o[3] = {0, 0, 0};
+        o[a] = k; o[b] = ib; o[c] = ic;
+        uint8_t kj;
+        const R v = fill_at<R>(p, flags, phin, nbr(p, x, y, z, o[0], o[1], o[2]), kj);
+        if (kj == WALL) return false;
+        if (k == -3 * s && kj != LIQ) return false;
+        if (k == 3 * s && kj != GAS) return false;
+        sum += v;
+      }
+      H[(ib + 1) * 3 + (ic + 1)] = sum;
+    }
+  const R Hb = R(0.5) * (H[7] - H[1]);
+  const R Hc = R(0.5) * (H[5] - H[3]);
+  const R Hbb = H[7] - R(2) * H[4] + H[1];
+  const R Hcc = H[5] - R(2) * H[4] + H[3];
+  const R Hbc = R(0.25) * (H[8] - H[6] - H[2] + H[0]);
+  const R q2 = R(1) + Hb * Hb + Hc * Hc;
+  const R num = Hbb * (R(1) + Hc * Hc) + Hcc * (R(1) + Hb * Hb) - R(2) * Hb * Hc * Hbc;
+  kap = -num / (q2 * sqrt(q2));
+  return true;
+}
+template <class R>
+__device__ __noinline__ R curvature_open(const Par& p, const uint8_t* __restrict__ flags,
+                                         const R* __restrict__ phin, int x, int y, int z, R n0, R n1, R n2,
+                                         int a) {
+  const R nv[3] = {n0, n1, n2};
+  int ax0 = (a + 1) % 3, ax1 = (a + 2) % 3;
+  if (fabs(nv[ax1]) > fabs(nv[ax0])) {
+    const int t = ax0;
+    ax0 = ax1;
+    ax1 = t;
+  }
+  R kap = R(0);
+  if (height_curvature<R>(p, flags, phin, x, y, z, ax0, nv[ax0] > R(0) ? 1 : -1, kap)) return kap;
+  if (height_curvature<R>(p, flags, phin, x, y, z, ax1, nv[ax1] > R(0) ? 1 : -1, kap)) return kap;
+  const R l0 = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+  R div = R(0);
+  for (int d = 0; d < 3; ++d) {
+    R comp[2];
+    for (int sg = 0; sg < 2; ++sg) {
+      int o[3] = {0, 0, 0};
+      o[d] = sg ? 1 : -1;
+      const int xj = x + o[0], yj = y + o[1], zj = z + o[2];
+      const long long j = nbr(p, x, y, z, o[0], o[1], o[2]);
+      R m0 = n0, m1 = n1, m2 = n2, lm = l0;
+      if (j >= 0 && kind_at(flags, j) != WALL) {
+        // Parker-Youngs gradient around the neighbour (its own fill across walls)
+        uint8_t kc;
+        const R pc = fill_at<R>(p, flags, phin, j, kc);
+        R g0 = R(0), g1 = R(0), g2 = R(0);
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (!dx && !dy && !dz) continue;
+              uint8_t kk;
+              R pj = fill_at<R>(p, flags, phin, nbr(p, xj, yj, zj, dx, dy, dz), kk);
+              if (kk == WALL) pj = pc;
+              const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy, adz = dz < 0 ? -dz : dz;
+              if (dx) g0 += R(dx * (2 - ady) * (2 - adz)) * pj;
+              if (dy) g1 += R(dy * (2 - adz) * (2 - adx)) * pj;
+              if (dz) g2 += R(dz * (2 - adx) * (2 - ady)) * pj;
+            }
+        const R l = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+        if (l > R(1e-12)) {
+          m0 = -g0; m1 = -g1; m2 = -g2; lm = l;
+        }
+      }
+      comp[sg] = (d == 0 ? m0 : (d == 1 ? m1 : m2)) / lm;
+    }
+    div += R(0.5) * (comp[1] - comp[0]);
+  }
+  return div;
+}
+
 // MODE 0: any cell (plain offsets when every stencil cell is inside the
 // lattice, else the general neighbour rule); 1: the caller knows every cell
 // within 3 is inside; 2: a lattice without periodic axes (a stencil cell past
 // a face is a wall: a bounds test per cell instead of the neighbour rule).
-template <class R, int MODE = 0>
+// SIG: the instance for surface tension (curvature); without it kappa stays 0
+template <class R, int MODE = 0, bool SIG = false>
 __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict__ flags,
                                          const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
   R (&n)[3] = G.n;
@@ -631,7 +731,7 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
     }
     R nabs = fabs(a == 0 ? n[0] : (a == 1 ? n[1] : n[2]));
     d = nabs * (H[4] - R(3.5));
-    if (p.sigma != 0.0) {
+    if (SIG && p.sigma != 0.0) {
       R Hbb = H[7] - R(2) * H[4] + H[1];
       R Hcc = H[5] - R(2) * H[4] + H[3];
       R Hbc = R(0.25) * (H[8] - H[6] - H[2] + H[0]);
@@ -640,6 +740,7 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
       kap = -num / (q2 * sqrt(q2));
     }
   } else {
+    if (SIG && p.sigma != 0.0) kap = curvature_open<R>(p, flags, phin, x, y, z, n[0], n[1], n[2], a);
     if constexpr (sizeof(R) == 4) {
       const R il = rsqrtf(nn);
       n[0] *= il; n[1] *= il; n[2] *= il;

@@ -135,3 +135,22 @@ def test_film_velocity_reduced_precision_against_fp64():
     assert abs(drift["f64"]) < 1e-12
     assert e["f32"] < 1e-3 and abs(drift["f32"]) < 1e-4
     assert e["f16"] < 5e-2 and abs(drift["f16"]) < 1e-3
+
+
+def test_droplet_parity_and_laplace_jump():
+    """Frozen spherical droplet with surface tension (curvature from the
+    other axes' heights or the normal divergence where the dominant columns
+    are open): parity with the oracle over 200 steps, then the Laplace jump
+    rho - rho_G = 3 sigma 2/R within 6 % (R = 6) in FP64 and FP32."""
+    from gpu_util import run_parity
+    c = cases.droplet(n=24, R=6.0, sigma=1e-3)
+    run_parity(c, 200, every=50)
+    core = c["r"] < 3.0
+    for prec in ("f64", "f32"):
+        g = fslbm.Lattice.from_case(c, precision=prec)
+        g.step(1500)
+        rho = g.get(fslbm.FIELD_RHO)["rho"]
+        ratio = (rho[core].mean() - 1.0) / (3.0 * 1e-3 * 2.0 / 6.0)
+        print(f"droplet R=6 {prec}: Laplace jump / theory = {ratio:.4f}")
+        assert abs(ratio - 1.0) < 0.06
+        g.close()

@@ -804,3 +804,32 @@ def test_openmp_build_gives_the_same_bits():
             assert np.array_equal(a.get(fid), b.get(fid))
         assert np.array_equal(a.flags(), b.flags())
         assert a.total_mass() == b.total_mass()
+
+
+# --------------------------------------------------------------------------
+# Static droplet: the Laplace jump (Sec. 2.3, Laplace pressure)
+# --------------------------------------------------------------------------
+def _droplet_jump(R, sigma=1e-3, steps=1500):
+    c = cases.droplet(n=24, R=R, sigma=sigma)
+    o = Oracle.from_case(c)
+    assert o.step(steps) == 0
+    rho = o.get(RHO)
+    core = c["r"] < R / 2
+    fl = c["flags"]
+    umax = np.abs(o.get(VEL)[(fl == cases.LIQUID) | (fl == cases.INTERFACE)]).max()
+    return (rho[core].mean() - 1.0) / (3.0 * sigma * 2.0 / R), umax
+
+
+def test_static_droplet_laplace_jump():
+    """A frozen spherical droplet (radius 6 and 8, off-centre in a periodic
+    24^3 box, fill levels sampled on 16^3 points per cell) with surface
+    tension settles on the Laplace density jump rho - rho_G = 3 sigma 2/R:
+    within 6 % at R = 6 and 3 % at R = 8 (the error falls with R), with
+    residual currents below 1e-3.  Where the height columns along the
+    dominant axis are open, the curvature comes from the other axes' heights
+    or the divergence of the normal; with kappa = 0 there the jump came out
+    at half of the law."""
+    r6, u6 = _droplet_jump(6.0)
+    r8, u8 = _droplet_jump(8.0)
+    assert abs(r6 - 1) < 0.06 and abs(r8 - 1) < 0.03 and abs(r8 - 1) < abs(r6 - 1)
+    assert u6 < 1e-3 and u8 < 1e-3
