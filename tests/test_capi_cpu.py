@@ -63,6 +63,21 @@ def test_default_params_and_argument_checks(built_lib):
     assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
     bad.tau, bad.precision = 0.8, 7
     assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.precision = fslbm.F64
+    # options outside their ranges, each on its own (checked before any device work)
+    for field, value in (("stress", 3), ("ub_extrap", 2), ("recon_nc", -1), ("excess_split", 2),
+                         ("bulk_loads", 9), ("rule", 2)):
+        old = getattr(bad, field)
+        setattr(bad, field, value)
+        assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1, field
+        setattr(bad, field, old)
+    bad.compressible, bad.wall_u[0] = 1, 1e-3                # moving walls need rho_0 = 1
+    assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.compressible, bad.wall_u[0] = 0, 0.0
+    L.fslbm_check_grid_barrier.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    assert L.fslbm_check_grid_barrier(2, None) == -1          # expire must be 0 or 1
+    L.fslbm_launches_per_step.argtypes = [ctypes.c_void_p]
+    assert L.fslbm_launches_per_step(None) == -1
     assert L.fslbm_step(None, 1) == -1
     L.fslbm_last_error.restype = ctypes.c_char_p
     assert L.fslbm_last_error(None) == b"NULL handle"
