@@ -108,7 +108,10 @@ typedef struct {
                          (lambda_- = lambda_+); default 3/16 */
   double g[3];        /* body force per unit mass and step; F = rho_0 g */
   double rho_G;       /* gas density: boundary pressure P_b = rho_G/3 (Eq. koerner) */
-  double sigma;       /* surface tension: rho_b = rho_G + 3 sigma kappa (Sec. 2.3) */
+  double sigma;       /* surface tension: rho_b = rho_G + 3 sigma kappa (Sec. 2.3); kappa from
+                         height functions along the dominant normal axis, where those columns
+                         are open from the other axes' heights, else the divergence of the
+                         normal */
   int rule;           /* FSLBM_FSK or FSLBM_FSL */
   int compressible;   /* 1: rho_0 = rho (Qian); 0: rho_0 = 1 (He-Luo), default */
   int linear_eq;      /* 1: drop the non-linear part N_q of e^+ (Stokes flow) */
