@@ -90,3 +90,36 @@ def test_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(fslbm, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         fslbm.lib()
+
+
+def _c_struct_fields(text, start, end):
+    """Field names of a C struct body between two markers, in order."""
+    body = text[text.index(start):]
+    body = body[:body.index(end)]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    body = re.sub(r"//[^\n]*", "", body)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl or decl.startswith(("typedef", "struct")):
+            continue
+        # "int nx, ny, nz": the type goes with the first declarator only
+        for part in decl.split(","):
+            m = re.search(r"([A-Za-z_][A-Za-z0-9_]*)\s*(\[\d+\])?\s*$", part.strip())
+            if m:
+                names.append(m.group(1))
+    return names
+
+
+def test_ctypes_structs_follow_the_c_layouts():
+    """The ctypes mirrors of fslbm_params (binding) and of the oracle's Params
+    list the C fields in the same order (the structs cross the ABI by value)."""
+    from oracle import oracle as orc
+    from paper_1409_5645_gb300 import fslbm
+    hdr = open(os.path.join(ROOT, "include", "fslbm.h")).read()
+    c_lib = _c_struct_fields(hdr, "  int dims[3];", "} fslbm_params;")
+    assert c_lib == [f[0] for f in fslbm.Params._fields_]
+    src = open(os.path.join(ROOT, "oracle", "fslbm_oracle.cpp")).read()
+    src = src[src.index("struct Params {") + len("struct Params {"):]
+    c_orc = _c_struct_fields(src, "", "};")
+    assert c_orc == [f[0] for f in orc.Params._fields_]
