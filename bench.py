@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="f32,f64,f16", help="precision forms; the first is the headline")
     ap.add_argument("--form-steps", type=int, default=2000, help="timed steps of the non-headline forms")
-    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end run from the initial state (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--save-state", default=None, metavar="PREFIX",
@@ -414,11 +415,12 @@ def main():
                     "kernel_ms_per_step": [round(x, 5) for x in r["groups_ms"]]}
     line["forms"] = other
     # end to end through the C interface with host buffers
-    e2e = e2e_run(case, forms[0], args.e2e_steps, local_rank)
+    e2e_steps = args.e2e_steps or args.steps
+    e2e = e2e_run(case, forms[0], e2e_steps, local_rank)
     e2e_v = max_over_ranks(-e2e["value"], ws, torch.device("cuda", local_rank))
     line["e2e"] = {"value": round(-e2e_v * ws, 2), "unit": "MLUPS",
-                   "h2d_bytes_per_step": e2e["h2d_bytes"] // args.e2e_steps,
-                   "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "steps": args.e2e_steps,
+                   "h2d_bytes_per_step": e2e["h2d_bytes"] // e2e_steps,
+                   "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "steps": e2e_steps,
                    "includes": "state upload from pinned host memory, per-step mass read"}
     # differentiation: adjoint step cost per forward step (FP64 and FP32)
     if not args.no_adjoint:
