@@ -833,3 +833,23 @@ def test_static_droplet_laplace_jump():
     r8, u8 = _droplet_jump(8.0)
     assert abs(r6 - 1) < 0.06 and abs(r8 - 1) < 0.03 and abs(r8 - 1) < abs(r6 - 1)
     assert u6 < 1e-3 and u8 < 1e-3
+
+
+def test_step_from_post_equals_the_step():
+    """One step restarted from the post-collision populations (the entry the
+    full-size window check uses: u and n^+ recovered from f~ by inverting the
+    collision) equals the ordinary step: dam break with conversions, FSL, and
+    a capillary wave with the shear term."""
+    for c in (_mini_dam(1), cases.standing_wave(n=16, depth=8.0, amp=1.0, tau=0.6, g=1e-4, sigma=5e-3,
+                                                  phi_noise=1e-4, stress=1)):
+        a = Oracle.from_case(c)
+        assert a.step(25) == 0
+        # F_POST is the collision of the current state
+        flags, m, phi, ft = a.flags().copy(), a.get(2), a.get(PHI), a.get(F_POST)
+        assert a.step(1) == 0
+        b = Oracle(c["dims"], c["params"])
+        assert b.step_from_post(flags, ft, m, phi) == 0
+        assert np.array_equal(a.flags(), b.flags())
+        for fid in (F_PRE, 2, PHI):
+            ra, rb = a.get(fid), b.get(fid)
+            assert np.abs(ra - rb).max() <= 1e-13 * np.abs(ra).max(), fid
