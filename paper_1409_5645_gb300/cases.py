@@ -444,3 +444,39 @@ def couette(h=8, tau=1.1, rule=1, shear=1e-3, headroom=3, **kw) -> Case:
     flags = np.where(z < h - 1, LIQUID, np.where(z == h - 1, INTERFACE, GAS)).astype(np.uint8)
     return Case(dims=dims, params=params, flags=flags, rho=np.ones(N), u=np.zeros((N, 3)),
                 phi=np.where(flags == INTERFACE, 1.0, 0.0), noise=None, wall_delta=None, h=h, shear=shear)
+
+
+def churn(nx=3, ny=3, nz=6, seed=SEED, u_amp=0.04, g=(2e-3, 0.0, -4e-3), tau=0.7, rule=0,
+          plant=True, **kw) -> Case:
+    """A tiny lattice whose interface converts every few steps (pins of the
+    conversion rules): x and y periodic, walls at the z faces; column heights
+    between 1.5 and 3.5 cells over the 3 x 3 footprint; seeded velocities of
+    amplitude u_amp and density noise 1e-2 on the fluid cells; strong gravity.
+    ``plant`` sets two diagonal neighbours of the interface layer over- and
+    under-full (fill levels 1.3 and -0.3), so that the first step has a cell
+    that fills next to one that empties."""
+    dims = (nx, ny, nz)
+    N = nx * ny * nz
+    i = np.arange(N, dtype=np.int64)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    heights = 2.5 + uniform(seed, nx * ny, 1.0)
+    h = heights[x + nx * y]
+    phi = np.clip(h - z, 0.0, 1.0)
+    params = default_params(tau=tau, g=tuple(g), rule=rule, periodic=(1, 1, 0))
+    params.update(kw)
+    flags = classify(dims, params["periodic"], 0, phi)
+    fluid = (flags == LIQUID) | (flags == INTERFACE)
+    ifc = flags == INTERFACE
+    phi = np.where(ifc, np.clip(phi, 0.05, 1.0), np.where(flags == LIQUID, 1.0, 0.0))
+    if plant:
+        cand = np.nonzero(ifc)[0]
+        for a in cand:
+            ax, ay, az = a % nx, (a // nx) % ny, a // (nx * ny)
+            b = ((ax + 1) % nx) + nx * (((ay + 1) % ny) + ny * az)
+            if ifc[b]:
+                phi[a], phi[b] = 1.3, -0.3
+                break
+    u = np.zeros((N, 3))
+    u[fluid] = uniform(seed, 3 * int(fluid.sum()), u_amp, offset=N).reshape(-1, 3)
+    rho = np.where(fluid, 1.0 + uniform(seed, N, 1e-2, offset=4 * N), params["rho_G"])
+    return Case(dims=dims, params=params, flags=flags, rho=rho, u=u, phi=phi, noise=None, wall_delta=None)
