@@ -56,8 +56,11 @@ typedef struct fslbm fslbm_t;
 enum fslbm_rule { FSLBM_FSK = 0, FSLBM_FSL = 1 };
 
 /* Precision forms: FP64 throughout; FP32 populations with FP64 interface
- * mass and mass balance; FP16 storage of f_q - w_q (rho_0 = 1) with FP32
- * arithmetic and FP64 interface mass and mass balance. */
+ * mass and mass balance; FP16 storage with FP32 arithmetic and FP64
+ * interface mass and mass balance.  Both reduced forms store, and compute
+ * with, the deviation f_q - w_q of each population from its rest value
+ * (rho_0 = 1): the step is affine in the populations with rho - 1 in place
+ * of rho, and the deviations keep the full mantissa for the flow. */
 enum fslbm_precision { FSLBM_F64 = 0, FSLBM_F32 = 1, FSLBM_F16 = 2 };
 
 enum fslbm_status {
@@ -173,6 +176,11 @@ void fslbm_default_params(fslbm_params *p);
 int fslbm_create(const int dims[3], double tau, const double g[3], double rho_G, double sigma,
                  int rule, fslbm_t **out);
 
+/* Relaxation time of a kinematic viscosity: tau = 3 nu + 1/2 (Sec. 2.1,
+ * nu = c_s^2 (tau - 1/2), c_s^2 = 1/3).  *tau receives it.  Returns
+ * FSLBM_ERR_ARG for nu <= 0, a non-finite nu or tau == NULL.  Host only. */
+int fslbm_tau_of_viscosity(double nu, double *tau);
+
 /* As fslbm_create with every parameter given.  FSL with |1 - tau| < 1e-3 is
  * rejected (FSLBM_ERR_ARG): the library stores post-collision populations
  * and recovers n^+ from them by dividing by 1 + lambda_+. */
@@ -287,8 +295,8 @@ int fslbm_adjoint_stats(fslbm_t *h, double *fwd_ms_per_step, double *adj_ms_per_
  * GPU that loads the library until the process exits).
  *   flags     uint8 [n_cells] cell kinds, device memory
  *   f_post    [19][n_cells] populations in the storage of `precision`:
- *             double (FSLBM_F64), float (FSLBM_F32) or half holding f - w_q
- *             (FSLBM_F16), device memory (e.g. from fslbm_get_fields)
+ *             double holding f (FSLBM_F64), float (FSLBM_F32) or half
+ *             (FSLBM_F16) holding f - w_q, device memory
  *   m         double [n_cells] interface mass (read on interface cells only)
  *   lost      added to the sum (the lost ledger of fslbm_total_mass)
  *   mass_out  one double in device memory, written by the call

@@ -14,8 +14,8 @@ from . import fslbm
 class FslbmRun(torch.autograd.Function):
     """J = objective after ``nsteps`` steps.
 
-    Inputs: ``nu`` (0-d float64 tensor, tau = 3 nu + 1/2 with the magic
-    parameter held fixed), ``g`` (3 float64), ``phi0`` (N float64 fill levels,
+    Inputs: ``nu`` (0-d float64 tensor, mapped to tau by the library with the
+    magic parameter held fixed), ``g`` (3 float64), ``phi0`` (N float64 fill levels,
     read on interface cells).  ``case`` supplies flags, rho, u, noise and the
     remaining parameters.
     """
@@ -23,7 +23,7 @@ class FslbmRun(torch.autograd.Function):
     @staticmethod
     def forward(ctx, nu, g, phi0, case, nsteps, K=200, objective=0, precision="f64"):
         params = dict(case["params"])
-        params["tau"] = 3.0 * float(nu) + 0.5
+        params["tau"] = fslbm.tau_of_viscosity(float(nu))
         params["g"] = tuple(float(v) for v in g.detach().cpu())
         params["keep_f0"] = 1
         dev = phi0.device if phi0.is_cuda else torch.device("cuda", torch.cuda.current_device())

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
     coords(p, i, x, y, z);
     double own[19], F[19], f[19];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) own[q] = (double)ldq<P>(a.f, q * N + i, q);
+    for (int q = 0; q < 19; ++q) own[q] = ldq_full<P>(a.f, q * N + i, q);
     unsigned wallm = 0u, gasm = 0u;
     long long src[19];
     F[0] = own[0];
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
       long long s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
       src[q] = s;
       uint8_t ks = kind_at(a.flags, s);
-      if (is_fluid(ks)) F[q] = (double)ldq<P>(a.f, q * N + s, q);
+      if (is_fluid(ks)) F[q] = ldq_full<P>(a.f, q * N + s, q);
       else if (ks == WALL) { wallm |= 1u << q; F[q] = 0.0; }
       else { gasm |= 1u << q; F[q] = 0.0; }
     }
@@ -458,7 +458,7 @@ __global__ void k_objective(Par p, const uint8_t* flags, const typename Form<P>:
     double jx = 0.0;
 #pragma unroll
     for (int q = 0; q < 19; ++q)
-      if (cx(q)) jx += cx(q) * (double)ldq<P>(f, q * N + i, q);
+      if (cx(q)) jx += cx(q) * ldq_full<P>(f, q * N + i, q);
     double ux = jx - 0.5 * p.g[0];
     double w = objective == 0 ? 1.0 : (k == IFC ? (double)phi[i] : 1.0);
     s += w * ux;
@@ -486,7 +486,7 @@ __global__ void k_obj_seed(Par p, const uint8_t* flags, const typename Form<P>::
           double jx = 0.0;
 #pragma unroll
           for (int q = 0; q < 19; ++q)
-            if (cx(q)) jx += cx(q) * (double)ldq<P>(f, q * N + i, q);
+            if (cx(q)) jx += cx(q) * ldq_full<P>(f, q * N + i, q);
           pb = (jx - 0.5 * p.g[0]) * scale;
         }
       }
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(128) k_adj_init(Par p, const uint8_t* flags, c
     double r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
-      ft[q] = (double)ldq<P>(f, q * N + i, q);
+      ft[q] = ldq_full<P>(f, q * N + i, q);
       ab[q] = abar[q * N + i];
       fb[q] = 0.0;
       r += ft[q];

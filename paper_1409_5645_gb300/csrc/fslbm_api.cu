@@ -245,6 +245,13 @@ extern "C" int fslbm_create(const int dims[3], double tau, const double g[3], do
   return fslbm_create_ex(&p, out);
 }
 
+// Sec. 2.1: nu = c_s^2 (tau - 1/2) with c_s^2 = 1/3 (lambda_+ = -1/tau)
+extern "C" int fslbm_tau_of_viscosity(double nu, double* tau) {
+  if (!tau || !(nu > 0.0) || !(nu < 1e300)) return FSLBM_ERR_ARG;
+  *tau = 3.0 * nu + 0.5;
+  return FSLBM_OK;
+}
+
 extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
   if (!h) return FSLBM_ERR_ARG;
   return h->bulk_mode == BULK_TMA ? FSLBM_LOADS_TMA : (h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC : FSLBM_LOADS_PLAIN);

@@ -54,13 +54,14 @@ __device__ __forceinline__ void push(bool pred, int* list, int* count, int cap, 
 }
 __device__ __forceinline__ int load_count(const int* c) { return *((volatile const int*)c); }
 
+// density of cell i at t+1 (summed in q order in the arithmetic type)
 template <int P>
-__device__ __forceinline__ typename Form<P>::R rho_out(const Par& p, const View<P>& v, long long i) {
+__device__ __forceinline__ double rho_out(const Par& p, const View<P>& v, long long i) {
   using R = typename Form<P>::R;
   R r = R(0);
 #pragma unroll
   for (int q = 0; q < 19; ++q) r += ldq<P>(v.fout, (size_t)q * (size_t)p.N + (size_t)i, q);
-  return r;
+  return rho_full<Form<P>::SH>(r);
 }
 
 // one warp per fill cell, lane q (1..18) takes link q
@@ -121,7 +122,7 @@ __device__ __forceinline__ void do_newg(const Par& p, const View<P>& v) {
         R g[19];
 #pragma unroll
         for (int r = 0; r < 19; ++r) g[r] = ldq<P>(v.fout, (size_t)r * N + (size_t)y2, r);
-        moments_post<R>(p, g, rr, ux, uy, uz);
+        moments_post<R, Form<P>::SH>(p, g, rr, ux, uy, uz);
       }
     }
     R rs = R(0), s0 = R(0), s1 = R(0), s2 = R(0);
@@ -133,8 +134,9 @@ __device__ __forceinline__ void do_newg(const Par& p, const View<P>& v) {
       const R b1 = __shfl_sync(FULL, uy, l), b2 = __shfl_sync(FULL, uz, l);
       if (ul) { rs += a; s0 += b0; s1 += b1; s2 += b2; ++c; }
     }
+    // (rbar is rho - 1 in the shifted forms: the mean of rho - 1)
     const R rbar = rs / R(c), u0 = s0 / R(c), u1 = s1 / R(c), u2 = s2 / R(c);
-    const R r0 = p.compressible ? rbar : R(1);
+    const R r0 = p.compressible ? rho_full_r<Form<P>::SH>(rbar) : R(1);
     const R usq = u0 * u0 + u1 * u1 + u2 * u2;
     const R wq_ = q == 0 ? R(1) / R(3) : (q <= 6 ? R(1) / R(18) : R(1) / R(36));
     // f^eq(rbar, ubar) with u^eq = ubar
@@ -150,7 +152,7 @@ __device__ __forceinline__ void do_newg(const Par& p, const View<P>& v) {
       jy += __shfl_xor_sync(FULL, jy, o);
       jz += __shfl_xor_sync(FULL, jz, o);
     }
-    const R rc = p.compressible ? rho : R(1);
+    const R rc = p.compressible ? rho_full_r<Form<P>::SH>(rho) : R(1);
     const R Ux = jx / rc, Uy = jy / rc, Uz = jz / rc;
     const R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
     const R vx_ = Ux + R(0.5) * gx, vy_ = Uy + R(0.5) * gy, vz_ = Uz + R(0.5) * gz;
@@ -202,10 +204,9 @@ __device__ __forceinline__ void do_newl(const Par& p, const View<P>& v) {
   int nl = min(load_count(&v.cnt[4]), v.cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x) {
     long long j = v.nllist[k];
-    R r = rho_out<P>(p, v, j);
-    double mm = (double)r;
-    v.m[j] = mm;
-    v.phout[j] = (R)(mm / (double)r);
+    const double r = rho_out<P>(p, v, j);
+    v.m[j] = r;
+    v.phout[j] = (R)(r / r);
   }
 }
 
@@ -275,7 +276,7 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
       for (int s = 1; s < 19; ++s) V += __shfl_sync(FULL, w, s);
     }
     if (lane == 0) {
-      const double rho = (double)rho_out<P>(p, v, i);
+      const double rho = rho_out<P>(p, v, i);
       const double ex = isF ? v.m[i] - rho : v.m[i];
       const int nr = __popc(rm);
       if (nr == 0) {
@@ -347,8 +348,7 @@ __device__ __forceinline__ void do_recv(const Par& p, const View<P>& v) {
     // (the weighted split reads the fill levels of interface cells here, so
     // its receivers take their new fill level in k_final)
     if (!p.excess_split) {
-      const R r = rho_out<P>(p, v, yj);
-      v.phout[yj] = (R)(mm / (double)r);
+      v.phout[yj] = (R)(mm / rho_out<P>(p, v, yj));
     }
   }
 }
@@ -405,7 +405,7 @@ __device__ __forceinline__ void do_final(const Par& p, const View<P>& v) {
     kk -= nl;
     const long long r = v.rlist[kk];
     v.mark[r] = 0;
-    if (p.excess_split) v.phout[r] = (R)(v.m[r] / (double)rho_out<P>(p, v, r));
+    if (p.excess_split) v.phout[r] = (R)(v.m[r] / rho_out<P>(p, v, r));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) emptied += __shfl_down_sync(0xffffffffu, emptied, o);

@@ -7,7 +7,7 @@
 //   m      f64 [N]        interface mass
 //   phiA/B R   [N]        fill level phi(t) / phi(t+1)
 //   wd     f64 [19][N]    wall link fractions (only when given)
-// S = double / float / half (f - w_q stored), R = double (FP64 form) or float.
+// S = double (f_q) / float / half (f_q - w_q), R = double (FP64 form) or float.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -49,30 +49,68 @@ enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8,
 // Precision forms
 // ---------------------------------------------------------------------------
 enum { P64 = 0, P32 = 1, P16 = 2 };
+// SH: the reduced forms store, and compute with, the deviation f_q - w_q of
+// each population from its rest-state value (rho_0 = 1).  Every step of the
+// method is affine in the populations with coefficients that sum to one per
+// link pair (w_q = w_qbar), so it takes the same form in the deviations, with
+// rho' = rho - 1 in place of rho in the equilibria; the stored values (of
+// order |u| rather than w_q) then keep the full float or half mantissa for the
+// part that carries the flow.  FP64 stores f_q itself.
 template <int P> struct Form;
-template <> struct Form<P64> { using S = double; using R = double; };
-template <> struct Form<P32> { using S = float; using R = float; };
-template <> struct Form<P16> { using S = __half; using R = float; };
+template <> struct Form<P64> { using S = double; using R = double; static constexpr bool SH = false; };
+template <> struct Form<P32> { using S = float; using R = float; static constexpr bool SH = true; };
+template <> struct Form<P16> { using S = __half; using R = float; static constexpr bool SH = true; };
 
+// loads and stores in the arithmetic type: f_q (FP64) or f_q - w_q (FP32/FP16)
 template <int P, int q>
 __device__ __forceinline__ typename Form<P>::R ld(const typename Form<P>::S* __restrict__ p, size_t k) {
-  if constexpr (P == P16) return __half2float(__ldg(p + k)) + wq<float>(q);
+  if constexpr (P == P16) return __half2float(__ldg(p + k));
   else return __ldg(p + k);
 }
 template <int P>
 __device__ __forceinline__ typename Form<P>::R ldq(const typename Form<P>::S* __restrict__ p, size_t k, int q) {
-  if constexpr (P == P16) return __half2float(p[k]) + wq<float>(q);
+  if constexpr (P == P16) return __half2float(p[k]);
   else return p[k];
 }
 template <int P, int q>
 __device__ __forceinline__ void st(typename Form<P>::S* __restrict__ p, size_t k, typename Form<P>::R v) {
-  if constexpr (P == P16) p[k] = __float2half_rn(v - wq<float>(q));
+  if constexpr (P == P16) p[k] = __float2half_rn(v);
   else p[k] = v;
 }
 template <int P>
 __device__ __forceinline__ void stq(typename Form<P>::S* __restrict__ p, size_t k, int q, typename Form<P>::R v) {
-  if constexpr (P == P16) p[k] = __float2half_rn(v - wq<float>(q));
+  if constexpr (P == P16) p[k] = __float2half_rn(v);
   else p[k] = v;
+}
+// the population f_q itself, in FP64 (state read-back, the adjoint)
+template <int P>
+__device__ __forceinline__ double ldq_full(const typename Form<P>::S* __restrict__ p, size_t k, int q) {
+  double v;
+  if constexpr (P == P16) v = (double)__half2float(p[k]);
+  else v = (double)p[k];
+  if constexpr (Form<P>::SH) v += (q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0));
+  return v;
+}
+// the stored value of a population f_q given in FP64
+template <int P>
+__device__ __forceinline__ typename Form<P>::R to_arith(double f, int q) {
+  if constexpr (Form<P>::SH) f -= (q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0));
+  return (typename Form<P>::R)f;
+}
+// density from a sum of populations in the arithmetic type (rho' or rho)
+template <bool SH, class R>
+__device__ __forceinline__ double rho_full(R r) {
+  return SH ? 1.0 + (double)r : (double)r;
+}
+template <bool SH, class R>
+__device__ __forceinline__ R rho_full_r(R r) {
+  return SH ? R(1) + r : r;
+}
+// instability test of a density given as a sum in the arithmetic type
+template <bool SH, class R>
+__device__ __forceinline__ bool rho_bad(R r) {
+  const R rf = rho_full_r<SH>(r);
+  return !(rf > R(0)) || !(rf < R(1e30));
 }
 
 // ---------------------------------------------------------------------------
@@ -235,8 +273,10 @@ __device__ __forceinline__ R cdot(R ux, R uy, R uz) {
 // TRT collision of one cell (Eq. lbe2) in place: f <- f + l+ n^+ + l- n^-,
 // with u = U + g/2 in e^+ and u^eq = U - g/lambda_- in e^- (Sec. 2.1).
 // On return rho holds sum f and (ux,uy,uz) the velocity u of the
-// pre-collision state.
-template <class R>
+// pre-collision state.  SH: f holds f_q - w_q and rho receives rho - 1 (the
+// equilibria below are affine in rho with the weights w_q as slopes, so the
+// same expressions give e_q - w_q from rho - 1).
+template <class R, bool SH = false>
 __device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux, R& uy, R& uz) {
   R r = f[0], jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
@@ -250,7 +290,7 @@ __device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux,
     if (cz(q) == 1) jz = fx_add(jz, f[q]);
     if (cz(q) == -1) jz = fx_sub(jz, f[q]);
   }
-  const R r0 = p.compressible ? r : R(1);
+  const R r0 = p.compressible ? rho_full_r<SH>(r) : R(1);
   const R ir0 = p.compressible ? R(1) / r0 : R(1);
   const R Ux = fx_mul(jx, ir0), Uy = fx_mul(jy, ir0), Uz = fx_mul(jz, ir0);
   const R gx = R(p.g[0]), gy = R(p.g[1]), gz = R(p.g[2]);
@@ -295,7 +335,8 @@ __device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux,
 
 // Moments of the pre-collision state recovered from post-collision f~:
 // sum f~ = rho and sum c f~ = rho_0 U + F, so u = U + g/2 = (sum c f~)/rho_0 - g/2.
-template <class R>
+// SH: f holds f~_q - w_q and rho receives rho - 1.
+template <class R, bool SH = false>
 __device__ __forceinline__ void moments_post(const Par& p, const R (&f)[19], R& rho, R& ux, R& uy, R& uz) {
   R r = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
@@ -305,7 +346,7 @@ __device__ __forceinline__ void moments_post(const Par& p, const R (&f)[19], R& 
     if (cy(q)) jy += R(cy(q)) * f[q];
     if (cz(q)) jz += R(cz(q)) * f[q];
   }
-  R ir0 = p.compressible ? R(1) / r : R(1);
+  R ir0 = p.compressible ? R(1) / rho_full_r<SH>(r) : R(1);
   ux = jx * ir0 - R(0.5) * R(p.g[0]);
   uy = jy * ir0 - R(0.5) * R(p.g[1]);
   uz = jz * ir0 - R(0.5) * R(p.g[2]);

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_noalloc_partials(const uint8_t* __restr
       R r = R(0);
 #pragma unroll
       for (int q = 0; q < 19; ++q) r += fsl::ldq<P>(f, (size_t)q * (size_t)n + (size_t)i, q);
-      s += (double)r;
+      s += fsl::rho_full<fsl::Form<P>::SH>(r);
     } else if (k == fsl::IFC) {
       s += m[i];
     }
@@ -85,17 +85,23 @@ extern "C" int fslbm_mass_balance_noalloc(const uint8_t* flags, const void* f_po
   }
   double* partials = (double*)g_scratch_addr[dev];
   cudaStream_t st = (cudaStream_t)stream;
-  switch (precision) {
-    case FSLBM_F64:
-      k_noalloc_partials<fsl::P64><<<(int)nb, 256, 0, st>>>(flags, (const double*)f_post, m, n_cells, partials);
-      break;
-    case FSLBM_F32:
-      k_noalloc_partials<fsl::P32><<<(int)nb, 256, 0, st>>>(flags, (const float*)f_post, m, n_cells, partials);
-      break;
-    default:
-      k_noalloc_partials<fsl::P16><<<(int)nb, 256, 0, st>>>(flags, (const __half*)f_post, m, n_cells, partials);
-      break;
+  // each launch's own status (cudaLaunchKernel returns it): an earlier error
+  // of unrelated work is neither reported as this call's nor cleared by it
+  int nbi = (int)nb;
+  long long n = n_cells;
+  const void* fp = f_post;
+  void* a1[] = {(void*)&flags, (void*)&fp, (void*)&m, (void*)&n, (void*)&partials};
+  const void* kern = precision == FSLBM_F64   ? (const void*)k_noalloc_partials<fsl::P64>
+                     : precision == FSLBM_F32 ? (const void*)k_noalloc_partials<fsl::P32>
+                                              : (const void*)k_noalloc_partials<fsl::P16>;
+  cudaError_t e = cudaLaunchKernel(kern, dim3(nbi), dim3(256), a1, 0, st);
+  if (e == cudaSuccess) {
+    void* a2[] = {(void*)&partials, (void*)&nbi, (void*)&lost, (void*)&mass_out};
+    e = cudaLaunchKernel((const void*)k_noalloc_final, dim3(1), dim3(256), a2, 0, st);
   }
-  k_noalloc_final<<<1, 256, 0, st>>>(partials, (int)nb, lost, mass_out);
-  return cudaGetLastError() == cudaSuccess ? FSLBM_OK : FSLBM_ERR_CUDA;
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();  // the failed launch recorded its own error there
+    return FSLBM_ERR_CUDA;
+  }
+  return FSLBM_OK;
 }

@@ -105,7 +105,7 @@ template <int P, int q>
 __device__ __forceinline__ typename Form<P>::R ld_row(const unsigned char* row, int idx) {
   using S = typename Form<P>::S;
   const S s = reinterpret_cast<const S*>(row)[idx];
-  if constexpr (P == P16) return __half2float(s) + wq<float>(q);
+  if constexpr (P == P16) return __half2float(s);
   else return s;
 }
 
@@ -212,14 +212,14 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
       }
     }
     R rho, ux, uy, uz;
-    collide<R>(p, f, rho, ux, uy, uz);
-    if (!(rho > R(0)) || !(rho < R(1e30))) atomicOr(v.err, ERRB_UNSTABLE);
+    collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
+    if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
     FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
     FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-    msum += (double)rho;
+    msum += rho_full<Form<P>::SH>(rho);
   }
   if (failed && lane == 0) {
     atomicOr(v.err, ERRB_TMA);
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
         if constexpr (P == P16) {
           const long long e = (long long)q * (long long)N + i - (cx(q) + sy * cy(q) + sz * cz(q));
           const unsigned short hb = (unsigned short)(w >> (16 * (int)(e & 1)));
-          f[q] = __half2float(__ushort_as_half(hb)) + wq<float>(q);
+          f[q] = __half2float(__ushort_as_half(hb));
         } else {
           f[q] = __uint_as_float(w);
         }
@@ -343,14 +343,14 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
         }
       }
       R rho, ux, uy, uz;
-      collide<R>(p, f, rho, ux, uy, uz);
-      if (!(rho > R(0)) || !(rho < R(1e30))) atomicOr(v.err, ERRB_UNSTABLE);
+      collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
+      if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
       FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
       FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
       FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-      msum += (double)rho;
+      msum += rho_full<Form<P>::SH>(rho);
     }
     // the slots of this stage have been read (their values are consumed above)
     issue(si + AS_STAGES * nw, stg);

@@ -57,9 +57,9 @@ __global__ void k_init_pre(Par p, View<P> v, const double* __restrict__ fin, con
     }
     R f[19];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) f[q] = (R)fd[q];
+    for (int q = 0; q < 19; ++q) f[q] = to_arith<P>(fd[q], q);
     R rho, ux, uy, uz;
-    collide<R>(p, f, rho, ux, uy, uz);
+    collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
 #pragma unroll
     for (int q = 0; q < 19; ++q) stq<P>(const_cast<typename Form<P>::S*>(v.fin), (size_t)q * N + i, q, f[q]);
   }
@@ -81,7 +81,7 @@ __global__ void k_init_post(Par p, View<P> v, const double* __restrict__ fpost, 
     }
 #pragma unroll
     for (int q = 0; q < 19; ++q)
-      stq<P>(const_cast<typename Form<P>::S*>(v.fin), (size_t)q * N + i, q, (R)fpost[(size_t)q * N + i]);
+      stq<P>(const_cast<typename Form<P>::S*>(v.fin), (size_t)q * N + i, q, to_arith<P>(fpost[(size_t)q * N + i], q));
     v.m[i] = (k == IFC) ? m[i] : 0.0;
     phA[i] = (k == IFC) ? (R)phi[i] : R(1);
   }
@@ -118,24 +118,26 @@ __global__ void k_fields(Par p, View<P> v, unsigned mask, uint8_t* oflags, doubl
        i += (long long)gridDim.x * blockDim.x) {
     uint8_t k = v.flags[i] & KIND;
     bool fl = is_fluid(k);
+    constexpr bool SH = Form<P>::SH;
     R f[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) f[q] = fl ? ldq<P>(v.fin, (size_t)q * N + i, q) : R(0);
     R rho = R(0), ux = R(0), uy = R(0), uz = R(0);
-    if (fl) moments_post<R>(p, f, rho, ux, uy, uz);
+    if (fl) moments_post<R, SH>(p, f, rho, ux, uy, uz);
+    const double rhof = fl ? rho_full<SH>(rho) : 0.0;
     if (oflags) oflags[i] = k;
     if (of) {
 #pragma unroll
-      for (int q = 0; q < 19; ++q) of[(size_t)q * N + i] = (double)f[q];
+      for (int q = 0; q < 19; ++q) of[(size_t)q * N + i] = fl ? ldq_full<P>(v.fin, (size_t)q * N + i, q) : 0.0;
     }
-    if (om) om[i] = k == IFC ? v.m[i] : (k == LIQ ? (double)rho : 0.0);
+    if (om) om[i] = k == IFC ? v.m[i] : (k == LIQ ? rhof : 0.0);
     if (ophi) {
       double ph = 0.0;
       if (k == LIQ) ph = 1.0;
       else if (k == IFC || (k == GAS && p.freeze)) ph = (double)v.phin[i];
       ophi[i] = ph;
     }
-    if (orho) orho[i] = (double)rho;
+    if (orho) orho[i] = rhof;
     if (ou) { ou[3 * i] = (double)ux; ou[3 * i + 1] = (double)uy; ou[3 * i + 2] = (double)uz; }
   }
 }
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(256) k_mass_partials(Par p, View<P> v, double*
       R r = R(0);
 #pragma unroll
       for (int q = 0; q < 19; ++q) r += ldq<P>(v.fin, (size_t)q * N + i, q);
-      s += (double)r;
+      s += rho_full<Form<P>::SH>(r);
     } else if (k == IFC) {
       s += v.m[i];
     }

@@ -157,14 +157,14 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
       }
     }
     R rho, ux, uy, uz;
-    collide<R>(p, f, rho, ux, uy, uz);
-    if (!(rho > R(0)) || !(rho < R(1e30))) atomicOr(v.err, ERRB_UNSTABLE);
+    collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
+    if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
     FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
     FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-    msum += (double)rho;
+    msum += rho_full<Form<P>::SH>(rho);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
@@ -199,7 +199,7 @@ __device__ __forceinline__ Vel3<typename Form<P>::R> cell_velocity(const typenam
     if (cy(q)) jy += R(cy(q)) * fq;
     if (cz(q)) jz += R(cz(q)) * fq;
   }
-  const R ir0 = compressible ? R(1) / r : R(1);
+  const R ir0 = compressible ? R(1) / rho_full_r<Form<P>::SH>(r) : R(1);
   return Vel3<R>{jx * ir0 - R(0.5) * R(gx), jy * ir0 - R(0.5) * R(gy), jz * ir0 - R(0.5) * R(gz)};
 }
 
@@ -211,8 +211,9 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
   R own[19], f[19];
 #pragma unroll
   for (int q = 0; q < 19; ++q) own[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)i, q);
-  R rt, utx, uty, utz;
-  moments_post<R>(p, own, rt, utx, uty, utz);
+  constexpr bool SH = Form<P>::SH;
+  R rt, utx, uty, utz;  // rt: rho(t), or rho(t) - 1 in the shifted forms
+  moments_post<R, SH>(p, own, rt, utx, uty, utz);
   f[0] = own[0];
   unsigned wallm, gasm, liqm;
   int srcs[19];  // sources of the pull (only kept off the interior path)
@@ -262,7 +263,8 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     R rb = R(p.rho_G);
     if (p.sigma != 0.0) rb = rb + R(3.0 * p.sigma) * kap;
     const R r0b = p.compressible ? rb : R(1);
-    const R r0t = p.compressible ? rt : R(1);
+    const R r0t = p.compressible ? rho_full_r<SH>(rt) : R(1);
+    if (SH) rb = rb - R(1);  // e^+ below in the arithmetic of the stored values
     const R usq = utx * utx + uty * uty + utz * utz;
     const R lp = R(p.lam_p);
     // boundary shear rate S^b of Eq. bterm (stress mode): S from the cell's
@@ -338,19 +340,20 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
     }
   }
   R rho, ux, uy, uz;
-  collide<R>(p, f, rho, ux, uy, uz);
-  if (!(rho > R(0)) || !(rho < R(1e30))) atomicOr(v.err, ERRB_UNSTABLE);
+  collide<R, SH>(p, f, rho, ux, uy, uz);
+  if (rho_bad<SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
 #pragma unroll
   for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
   double mm = v.m[i];
   if (!p.freeze) {
+    const double rhof = rho_full<SH>(rho);
     mm = mm + dm;
     v.m[i] = mm;
-    v.phout[i] = (R)(mm / (double)rho);
+    v.phout[i] = (R)(mm / rhof);
     // thresholds, plus the isolated-cell rules: no gas neighbour -> fill,
     // no liquid/interface neighbour -> empty
-    fill = mm > (1.0 + p.eps) * (double)rho || ((p.cleanup & 1) && gasm == 0u);
-    empty = !fill && (mm < -p.eps * (double)rho || ((p.cleanup & 2) && (wallm | gasm) == 0x7fffeu));
+    fill = mm > (1.0 + p.eps) * rhof || ((p.cleanup & 1) && gasm == 0u);
+    empty = !fill && (mm < -p.eps * rhof || ((p.cleanup & 2) && (wallm | gasm) == 0x7fffeu));
     if (fill) v.mark[i] = MK_FILL;  // marks are zero between steps; each cell writes only its own
     else if (empty) v.mark[i] = MK_EMPTY;
   }

@@ -62,6 +62,7 @@ def lib():
             L.fslbm_create.argtypes = [C.POINTER(C.c_int), C.c_double, dp, C.c_double, C.c_double, ip,
                                        C.POINTER(vp)]
             L.fslbm_create_ex.argtypes = [C.POINTER(Params), C.POINTER(vp)]
+            L.fslbm_tau_of_viscosity.argtypes = [C.c_double, dp]
             L.fslbm_set_state.argtypes = [vp, u8p, vp, vp, vp, ip]
             L.fslbm_init_equilibrium.argtypes = [vp, u8p, vp, vp, vp, vp, vp, ip]
             L.fslbm_set_state_post.argtypes = [vp, u8p, vp, vp, vp, vp, ip]
@@ -92,6 +93,16 @@ def lib():
             L.fslbm_destroy.restype = None
             _lib = L
     return _lib
+
+
+def tau_of_viscosity(nu: float) -> float:
+    """Relaxation time tau of the kinematic viscosity nu (the library's
+    map of Sec. 2.1)."""
+    tau = C.c_double()
+    rc = lib().fslbm_tau_of_viscosity(float(nu), C.byref(tau))
+    if rc:
+        raise FslbmError(rc, f"viscosity {nu}")
+    return tau.value
 
 
 def check_grid_barrier(expire: bool, stream=None) -> str:
@@ -193,6 +204,25 @@ class Lattice:
         if rc != 0:
             raise FslbmError(rc, "fslbm_create_ex")
         self.h = h
+
+    @classmethod
+    def create(cls, dims, tau, g, rho_G=1.0, sigma=0.0, rule=FSL):
+        """A lattice from the paper's problem data alone (fslbm_create): every
+        other parameter at the library's default."""
+        self = cls.__new__(cls)
+        self.L = lib()
+        self.dims = tuple(int(d) for d in dims)
+        self.N = int(np.prod(self.dims))
+        self.params = dict(tau=tau, g=tuple(g), rho_G=rho_G, sigma=sigma, rule=rule)
+        self.precision = "f64"
+        d = (C.c_int * 3)(*self.dims)
+        gv = (C.c_double * 3)(*[float(v) for v in g])
+        h = C.c_void_p()
+        rc = self.L.fslbm_create(d, float(tau), gv, float(rho_G), float(sigma), int(rule), C.byref(h))
+        if rc != 0:
+            raise FslbmError(rc, "fslbm_create")
+        self.h = h
+        return self
 
     @classmethod
     def from_case(cls, case, precision="f64", stream=None, **override):

@@ -123,3 +123,18 @@ def test_ctypes_structs_follow_the_c_layouts():
     src = src[src.index("struct Params {") + len("struct Params {"):]
     c_orc = _c_struct_fields(src, "", "};")
     assert c_orc == [f[0] for f in orc.Params._fields_]
+
+
+def test_viscosity_map_lives_in_the_library(built_lib):
+    """tau = 3 nu + 1/2 (Sec. 2.1) is the library's own entry point; the
+    autograd binding only marshals nu to it (no parameter arithmetic)."""
+    from paper_1409_5645_gb300 import fslbm
+    assert fslbm.tau_of_viscosity(0.1) == pytest.approx(0.8, abs=1e-15)
+    assert fslbm.tau_of_viscosity(1.0 / 60.0) == pytest.approx(0.55, abs=1e-15)
+    for bad in (0.0, -0.1, float("nan"), float("inf")):
+        with pytest.raises(fslbm.FslbmError):
+            fslbm.tau_of_viscosity(bad)
+    src = open(os.path.join(ROOT, "paper_1409_5645_gb300", "autograd.py")).read()
+    code = "\n".join(l.split("#")[0] for l in src.splitlines() if not l.strip().startswith(("\"", "'")))
+    assert "tau_of_viscosity" in code
+    assert not re.search(r"\d\s*\*\s*float\(nu\)|float\(nu\)\s*\*|\+\s*0\.5", code)

@@ -17,6 +17,8 @@ pytestmark = pytest.mark.gpu
 
 ERR_TOO_LARGE = -8
 MAX_CELLS = 4096 * 65536
+# rest-state values w_q of the links, in the library's population order
+W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 
 
 def _entry():
@@ -28,15 +30,21 @@ def _entry():
     return fn
 
 
-def test_noalloc_mass_balance_matches_total_mass_on_two_calls():
+def _state():
     import torch
-    fn = _entry()
     dev = torch.device("cuda:0")
     c = cases.dam_break(nx=37, ny=13, nz=21, col_x=11, col_z=15, tau=0.56, g=3e-4)
     lat = fslbm.Lattice.from_case(c)
     lat.step(60)
     st = lat.get(fslbm.FIELD_FLAGS | fslbm.FIELD_F | fslbm.FIELD_MASS, device=dev)
     ref, lost = lat.total_mass()
+    return c, dev, st, ref, lost
+
+
+def test_noalloc_mass_balance_matches_total_mass_on_two_calls():
+    import torch
+    fn = _entry()
+    c, dev, st, ref, lost = _state()
     out = torch.full((1,), -1.0, dtype=torch.float64, device=dev)
     for _ in range(2):
         rc = fn(st["flags"].data_ptr(), st["f"].data_ptr(), fslbm.F64, st["m"].data_ptr(), c.N, lost,
@@ -44,14 +52,36 @@ def test_noalloc_mass_balance_matches_total_mass_on_two_calls():
         torch.cuda.synchronize(dev)
         assert rc == 0
         assert out.item() == pytest.approx(ref, rel=1e-12)
-    # FP32-stored populations give the FP32 sum of the same state
-    f32 = st["f"].to(torch.float32).contiguous()
+
+
+@pytest.mark.parametrize("prec,dtype,rel", [("f32", "float32", 1e-7), ("f16", "float16", 1e-3)])
+def test_noalloc_mass_balance_reduced_storage(prec, dtype, rel):
+    """The reduced forms hand over f - w_q in float or half: the same state in
+    that storage gives the FP64 mass to the storage's resolution, and a
+    lattice run in that form gives its own fslbm_total_mass."""
+    import torch
+    fn = _entry()
+    c, dev, st, ref, lost = _state()
+    code = {"f32": fslbm.F32, "f16": fslbm.F16}[prec]
+    shifted = (st["f"] - torch.as_tensor(W, device=dev)[:, None]).to(getattr(torch, dtype)).contiguous()
+    out = torch.full((1,), -1.0, dtype=torch.float64, device=dev)
     for _ in range(2):
-        rc = fn(st["flags"].data_ptr(), f32.data_ptr(), fslbm.F32, st["m"].data_ptr(), c.N, lost,
+        rc = fn(st["flags"].data_ptr(), shifted.data_ptr(), code, st["m"].data_ptr(), c.N, lost,
                 out.data_ptr(), None)
         torch.cuda.synchronize(dev)
         assert rc == 0
-        assert out.item() == pytest.approx(ref, rel=1e-6)
+        assert out.item() == pytest.approx(ref, rel=rel)
+    # a lattice of this form: its stored populations through the entry point
+    lat = fslbm.Lattice.from_case(c, precision=prec)
+    lat.step(60)
+    mine = lat.get(fslbm.FIELD_FLAGS | fslbm.FIELD_F | fslbm.FIELD_MASS, device=dev)
+    M, L = lat.total_mass()
+    raw = (mine["f"] - torch.as_tensor(W, device=dev)[:, None]).to(getattr(torch, dtype)).contiguous()
+    for _ in range(2):
+        rc = fn(mine["flags"].data_ptr(), raw.data_ptr(), code, mine["m"].data_ptr(), c.N, L, out.data_ptr(), None)
+        torch.cuda.synchronize(dev)
+        assert rc == 0
+        assert out.item() == pytest.approx(M, rel=1e-12 if prec == "f32" else 1e-9)
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch():
