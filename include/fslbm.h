@@ -315,6 +315,44 @@ int fslbm_adjoint_stats(fslbm_t *h, double *fwd_ms_per_step, double *adj_ms_per_
 int fslbm_mass_balance_noalloc(const uint8_t *flags, const void *f_post, int precision, const double *m,
                                long long n_cells, double lost, double *mass_out, void *stream);
 
+/* ---- Slab decomposition ---------------------------------------------------
+ * The paper's runs used a parallel framework that splits the lattice into
+ * blocks (Sec. 4); these calls let a caller run a lattice as slabs, one
+ * handle per slab (one per GPU, or several on one GPU).  A slab's handle
+ * holds the cells it owns plus G ghost layers beside each cut, copies of the
+ * neighbouring slabs' cells.  One time step of a cell reads the state of time
+ * t within 7 cells of it (interface geometry 3, streaming 1, the chains of
+ * neighbour tests of the conversions 3), so with G >= 7 a step leaves every
+ * owned cell exact, and refilling the ghost layers from the neighbours'
+ * owned cells (pack, transport by the caller, unpack) makes the whole slab
+ * exact again: one exchange per step, conversions included.  A cut is a
+ * half-way wall to the handle; no ghost cell reaches an owned one within a
+ * step.  Implementation services, no counterpart in the paper. */
+
+/* Cells of the box [lo, hi) (per axis, 0 <= lo < hi <= dims) are the ones the
+ * handle owns: the mass balance (fslbm_total_mass, fslbm_step_mass) sums them
+ * only, and only their excess mass enters the lost ledger; the others are
+ * ghost cells, stepped like every cell.  Default: every cell.  Applies to the
+ * steps enqueued after the call.  FSLBM_ERR_ARG for an empty or outside box. */
+int fslbm_set_owned(fslbm_t *h, const int lo[3], const int hi[3]);
+
+/* Bytes of the packed state of the box [lo, hi): u8 cell kinds, f64 interface
+ * mass, fill levels phi(t) in the arithmetic type (f64 for FSLBM_F64, else
+ * f32) and post-collision populations [19][n] in the storage type (f - w_q in
+ * the reduced forms), each block 16-byte aligned, cells in box order (x
+ * fastest).  FSLBM_ERR_ARG (negative) for a bad box. */
+long long fslbm_halo_bytes(const fslbm_t *h, const int lo[3], const int hi[3]);
+
+/* Copy the current state of the box [lo, hi) into the device buffer buf
+ * (16-byte aligned, fslbm_halo_bytes long, on the handle's GPU), or set the
+ * box's state from one: cell kinds (static wall bits stay the handle's own),
+ * interface mass, fill levels and post-collision populations.  Asynchronous
+ * on the handle's stream; the caller orders the transport between a pack and
+ * the matching unpack.  Unpacking ends a differentiation in progress.
+ * FSLBM_ERR_ARG for a bad box or a misaligned or NULL buffer. */
+int fslbm_halo_pack(fslbm_t *h, const int lo[3], const int hi[3], void *buf);
+int fslbm_halo_unpack(fslbm_t *h, const int lo[3], const int hi[3], const void *buf);
+
 /* Steps taken since the last set_state. */
 long long fslbm_time(const fslbm_t *h);
 

@@ -447,10 +447,10 @@ def couette(h=8, tau=1.1, rule=1, shear=1e-3, headroom=3, **kw) -> Case:
 
 
 def churn(nx=3, ny=3, nz=6, seed=SEED, u_amp=0.04, g=(2e-3, 0.0, -4e-3), tau=0.7, rule=0,
-          plant=True, **kw) -> Case:
+          plant=True, base=2.5, periodic=(1, 1, 0), **kw) -> Case:
     """A tiny lattice whose interface converts every few steps (pins of the
     conversion rules): x and y periodic, walls at the z faces; column heights
-    between 1.5 and 3.5 cells over the 3 x 3 footprint; seeded velocities of
+    between base - 1 and base + 1 cells over the footprint; seeded velocities of
     amplitude u_amp and density noise 1e-2 on the fluid cells; strong gravity.
     ``plant`` sets two diagonal neighbours of the interface layer over- and
     under-full (fill levels 1.3 and -0.3), so that the first step has a cell
@@ -459,10 +459,10 @@ def churn(nx=3, ny=3, nz=6, seed=SEED, u_amp=0.04, g=(2e-3, 0.0, -4e-3), tau=0.7
     N = nx * ny * nz
     i = np.arange(N, dtype=np.int64)
     x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
-    heights = 2.5 + uniform(seed, nx * ny, 1.0)
+    heights = base + uniform(seed, nx * ny, 1.0)
     h = heights[x + nx * y]
     phi = np.clip(h - z, 0.0, 1.0)
-    params = default_params(tau=tau, g=tuple(g), rule=rule, periodic=(1, 1, 0))
+    params = default_params(tau=tau, g=tuple(g), rule=rule, periodic=tuple(periodic))
     params.update(kw)
     flags = classify(dims, params["periodic"], 0, phi)
     fluid = (flags == LIQUID) | (flags == INTERFACE)

@@ -156,6 +156,11 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   p.ub_extrap = q.ub_extrap;
   p.recon_nc = q.recon_nc;
   p.excess_split = q.excess_split;
+  for (int a = 0; a < 3; ++a) {
+    p.own_lo[a] = 0;
+    p.own_hi[a] = q.dims[a];
+  }
+  p.owned_all = 1;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;

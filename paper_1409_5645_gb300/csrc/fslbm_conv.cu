@@ -280,7 +280,7 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
       const double ex = isF ? v.m[i] - rho : v.m[i];
       const int nr = __popc(rm);
       if (nr == 0) {
-        atomicAdd(v.lost, ex);
+        if (owned(p, x, y, z)) atomicAdd(v.lost, ex);  // (a ghost cell's owner books it)
         v.share[i] = 0.0;
       } else if (V > 1e-12) {
         v.share[i] = ex / V;

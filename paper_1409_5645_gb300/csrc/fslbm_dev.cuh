@@ -150,7 +150,18 @@ struct Par {
   int ub_extrap;           // FSL: u_b extrapolated along the link to the surface point
   int recon_nc;            // interface cells also rebuild the links with n.c_p > 0
   int excess_split;        // 1: excess split along the fill-level normal
+  // cells this lattice owns when it is one subdomain of a decomposition (the
+  // others are ghost layers, computed but left out of the mass balance and
+  // the lost ledger); owned_all: every cell
+  int own_lo[3], own_hi[3];
+  int owned_all;
 };
+
+__device__ __forceinline__ bool owned(const Par& p, int x, int y, int z) {
+  return p.owned_all || ((unsigned)(x - p.own_lo[0]) < (unsigned)(p.own_hi[0] - p.own_lo[0]) &&
+                         (unsigned)(y - p.own_lo[1]) < (unsigned)(p.own_hi[1] - p.own_lo[1]) &&
+                         (unsigned)(z - p.own_lo[2]) < (unsigned)(p.own_hi[2] - p.own_lo[2]));
+}
 
 template <int P>
 struct View {
@@ -307,7 +318,21 @@ __device__ __forceinline__ void collide(const Par& p, R (&f)[19], R& rho, R& ux,
   const R k0 = fx_mul(fx_mul(R(1.5) * wq<R>(0), r0), nl);
   const R k1 = fx_mul(fx_mul(R(1.5) * wq<R>(1), r0), nl);
   const R k7 = fx_mul(fx_mul(R(1.5) * wq<R>(7), r0), nl);
-  const R m1 = fx_mul(R(3) * wq<R>(1), r0), m7 = fx_mul(R(3) * wq<R>(7), r0);
+  // 3 w_q rho_0 of e^-.  In float the rounded weights would make
+  // sum_q 3 w_q c_qa c_qa = 2 (3 w_1) + 8 (3 w_7) differ from 1 by ~1e-7, and
+  // the momentum would relax toward (1 + 1e-7) U every step: a systematic
+  // drift of the velocity that grows with time.  3 w_7 = fl(1/12) and
+  // 3 w_1 = (1 - 8 fl(1/12))/2 (both exact in float) keep that sum at 1.
+  R m1, m7;
+  if constexpr (sizeof(R) == 4) {
+    constexpr R m7f = R(1) / R(12);
+    constexpr R m1f = (R(1) - R(8) * m7f) * R(0.5);
+    m1 = fx_mul(m1f, r0);
+    m7 = fx_mul(m7f, r0);
+  } else {
+    m1 = fx_mul(R(3) * wq<R>(1), r0);
+    m7 = fx_mul(R(3) * wq<R>(7), r0);
+  }
   R out[19];
   {
     const R ep = fx_fma(k0, -usq, fx_mul(wq<R>(0), r));

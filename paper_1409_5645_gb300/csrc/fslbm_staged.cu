@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
     FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-    msum += rho_full<Form<P>::SH>(rho);
+    if (owned(p, x, y, z)) msum += rho_full<Form<P>::SH>(rho);
   }
   if (failed && lane == 0) {
     atomicOr(v.err, ERRB_TMA);
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
       FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
       FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-      msum += rho_full<Form<P>::SH>(rho);
+      if (owned(p, x, y, z)) msum += rho_full<Form<P>::SH>(rho);
     }
     // the slots of this stage have been read (their values are consumed above)
     issue(si + AS_STAGES * nw, stg);

@@ -154,6 +154,11 @@ __global__ void __launch_bounds__(256) k_mass_partials(Par p, View<P> v, double*
   double s = 0.0;
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     uint8_t k = v.flags[i] & KIND;
+    if (!p.owned_all) {
+      int x, y, z;
+      coords(p, i, x, y, z);
+      if (!owned(p, x, y, z)) continue;
+    }
     if (k == LIQ) {
       R r = R(0);
 #pragma unroll

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
     FSL_ST(17) FSL_ST(18)
 #undef FSL_ST
-    msum += rho_full<Form<P>::SH>(rho);
+    if (owned(p, x, y, z)) msum += rho_full<Form<P>::SH>(rho);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
@@ -430,8 +430,9 @@ __global__ void __launch_bounds__(128, (EXT ? 2 : (P == P64 ? 3 : 5))) k_iface(P
       icell = (int)i;
       int x, y, z;
       coords(p, i, x, y, z);
-      msum += in3 ? iface_cell<P, true, EXT>(p, v, pos, i, x, y, z, fill, empty)
-                  : iface_cell<P, false, EXT>(p, v, pos, i, x, y, z, fill, empty);
+      const double mm = in3 ? iface_cell<P, true, EXT>(p, v, pos, i, x, y, z, fill, empty)
+                            : iface_cell<P, false, EXT>(p, v, pos, i, x, y, z, fill, empty);
+      if (owned(p, x, y, z)) msum += mm;
     }
     warp_append(fill, icell, v.flist, &v.cnt[1], v.cap, v.err);
     warp_append(empty, icell, v.elist, &v.cnt[2], v.cap, v.err);

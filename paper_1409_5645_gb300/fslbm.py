@@ -63,6 +63,12 @@ def lib():
                                        C.POINTER(vp)]
             L.fslbm_create_ex.argtypes = [C.POINTER(Params), C.POINTER(vp)]
             L.fslbm_tau_of_viscosity.argtypes = [C.c_double, dp]
+            box = C.POINTER(C.c_int)
+            L.fslbm_set_owned.argtypes = [vp, box, box]
+            L.fslbm_halo_bytes.argtypes = [vp, box, box]
+            L.fslbm_halo_bytes.restype = C.c_longlong
+            L.fslbm_halo_pack.argtypes = [vp, box, box, vp]
+            L.fslbm_halo_unpack.argtypes = [vp, box, box, vp]
             L.fslbm_set_state.argtypes = [vp, u8p, vp, vp, vp, ip]
             L.fslbm_init_equilibrium.argtypes = [vp, u8p, vp, vp, vp, vp, vp, ip]
             L.fslbm_set_state_post.argtypes = [vp, u8p, vp, vp, vp, vp, ip]
@@ -290,6 +296,14 @@ class Lattice:
         self._check(self.L.fslbm_get_fields(self.h, mask, arr, DEVICE if device is not None else HOST), "get_fields")
         return out
 
+    def get_into(self, mask: int, out: dict):
+        """Fields into caller-owned host arrays (``out`` keyed like get())."""
+        names = [(FIELD_FLAGS, "flags"), (FIELD_F, "f"), (FIELD_MASS, "m"), (FIELD_PHI, "phi"), (FIELD_RHO, "rho"),
+                 (FIELD_U, "u")]
+        ptrs = [out[n].ctypes.data for bit, n in names if mask & bit]
+        arr = (C.c_void_p * len(ptrs))(*ptrs)
+        self._check(self.L.fslbm_get_fields(self.h, mask, arr, HOST), "get_fields")
+
     def total_mass(self):
         M, L = C.c_double(), C.c_double()
         self._check(self.L.fslbm_total_mass(self.h, C.byref(M), C.byref(L)), "total_mass")
@@ -314,6 +328,29 @@ class Lattice:
         n = C.c_longlong()
         self._check(self.L.fslbm_timing_read(self.h, ms, C.byref(n)), "timing_read")
         return list(ms), n.value
+
+    # -- slab decomposition ---------------------------------------------------
+    @staticmethod
+    def _box(lo, hi):
+        return (C.c_int * 3)(*[int(v) for v in lo]), (C.c_int * 3)(*[int(v) for v in hi])
+
+    def set_owned(self, lo, hi):
+        """Cells of [lo, hi) are this handle's own (mass balance, lost ledger)."""
+        self._check(self.L.fslbm_set_owned(self.h, *self._box(lo, hi)), "set_owned")
+
+    def halo_bytes(self, lo, hi) -> int:
+        n = int(self.L.fslbm_halo_bytes(self.h, *self._box(lo, hi)))
+        if n < 0:
+            raise FslbmError(n, "halo_bytes")
+        return n
+
+    def halo_pack(self, lo, hi, buf):
+        """Pack the box's state into ``buf`` (a CUDA uint8 tensor of
+        halo_bytes(lo, hi)); asynchronous on the handle's stream."""
+        self._check(self.L.fslbm_halo_pack(self.h, *self._box(lo, hi), C.c_void_p(buf.data_ptr())), "halo_pack")
+
+    def halo_unpack(self, lo, hi, buf):
+        self._check(self.L.fslbm_halo_unpack(self.h, *self._box(lo, hi), C.c_void_p(buf.data_ptr())), "halo_unpack")
 
     # -- differentiation ------------------------------------------------------
     def adjoint_forward(self, nsteps: int, K: int = 200, objective: int = 0) -> float:

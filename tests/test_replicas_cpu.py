@@ -1,8 +1,8 @@
-"""The multi-GPU path of the benchmark is independent replicas (one lattice
-per rank, no collective on the data path); its host plumbing -- process
-group set-up, barrier, the max over ranks of the timed region -- runs here on
-CPU as two gloo ranks, and the CPU reference arm under torchrun prints one
-line from rank 0 only."""
+"""Host plumbing of the benchmark's multi-GPU path (one lattice split into
+y-slabs, one slab per rank; its exchange logic is tested in
+test_slabs_cpu.py): process group set-up, barrier and the max over ranks of
+the timed region run here on CPU as two gloo ranks, and the CPU reference arm
+under torchrun prints one line from rank 0 only."""
 import os
 import socket
 import subprocess
