@@ -47,9 +47,16 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--spinup", type=int, default=5000,
+                    help="untimed steps from the initial column before the warm-up, so that the timed window "
+                         "sits in the middle of the 10000-step run (its interface and conversions), not at its "
+                         "start")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="f32,f64,f16", help="precision forms; the first is the headline")
     ap.add_argument("--form-steps", type=int, default=2000, help="timed steps of the non-headline forms")
+    ap.add_argument("--as-written-steps", type=int, default=2000,
+                    help="timed steps of the dam break at tau = 0.51, Lambda = 3/16 from its initial state "
+                         "(0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end run from the initial state (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -119,6 +126,58 @@ def max_over_ranks(v, ws, device=None):
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
+class NvmlClocks:
+    """SM clock, power and clock-event reasons sampled every millisecond by a
+    host thread through NVML (read-only queries), so that a timed region of a
+    few milliseconds still gets samples."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, gpu_index, period_s=0.001):
+        import ctypes
+        import threading
+        self.ok = False
+        try:
+            self.L = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.L.nvmlInit_v2() != 0:
+                return
+            self.dev = ctypes.c_void_p()
+            if self.L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(self.dev)) != 0:
+                return
+            mx = ctypes.c_uint()
+            self.L.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(mx))
+            self.max_mhz = float(mx.value)
+        except (OSError, AttributeError):
+            return
+        self.ok = True
+        self.samples, self.period = [], period_s
+        self.stop_ev = threading.Event()
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+
+    def _run(self):
+        import ctypes
+        clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_r = getattr(self.L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.L.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop_ev.is_set():
+            self.L.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(clk))
+            self.L.nvmlDeviceGetPowerUsage(self.dev, ctypes.byref(pw))
+            get_r(self.dev, ctypes.byref(rs))
+            self.samples.append((float(clk.value), pw.value / 1000.0, int(rs.value)))
+            time.sleep(self.period)
+
+    def stop(self):
+        if not self.ok:
+            return None
+        self.stop_ev.set()
+        self.th.join(timeout=2)
+        sm = [a for a, _, _ in self.samples]
+        reasons = sorted({nm for _, _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sm), "power_w_median": statistics.median([p for _, p, _ in self.samples])
+                if sm else None, "source": "NVML, 1 ms"}
+
+
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -229,7 +288,7 @@ def load_state(lat, prefix, dev):
     del t
 
 
-def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False, state=None):
+def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False, state=None, spinup=0):
     import torch
     from paper_1409_5645_gb300 import fslbm
     dev = torch.device("cuda", local_rank)
@@ -241,7 +300,7 @@ def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False, stat
         t = {k: torch.from_numpy(case[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
         lat.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
         del t
-    lat.step(warmup)
+    lat.step(spinup + warmup)
     lat.sync()
     M0, _ = lat.total_mass()
     nliq0, nifc0 = count_kinds(lat)
@@ -250,7 +309,12 @@ def run_form(case, form, steps, warmup, ws, rank, local_rank, clocks=False, stat
     e1 = torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize(dev)
-    ck = Clocks(local_rank) if clocks else None
+    ck = None
+    if clocks:
+        ck = NvmlClocks(local_rank)
+        if not ck.ok:
+            ck = Clocks(local_rank)
+        time.sleep(0.01)
     e0.record(stream)
     lat.step(steps)
     e1.record(stream)
@@ -292,15 +356,22 @@ def adjoint_run(form, steps=4000, K=200):
 
 
 def e2e_run(case, form, steps, local_rank):
-    """The user's call sequence with host buffers: state from pinned host
-    memory, then every step fslbm_step + a device->host read of that step's
-    mass balance."""
+    """The user's call sequence with host buffers: the initial state from
+    pinned host memory (fslbm_init_equilibrium), then every step fslbm_step
+    and a device->host read of that step's mass balance, and at the end the
+    fields read back to pinned host memory (fslbm_get_fields: flags, rho, u,
+    phi)."""
+    import numpy as np
     import torch
     from paper_1409_5645_gb300 import fslbm
     dev = torch.device("cuda", local_rank)
-    pinned = {k: torch.from_numpy(case[k]).pin_memory() for k in ("flags", "rho", "u", "phi")}
-    host = {k: v.numpy() for k, v in pinned.items()}
+    N = int(case["flags"].size)
+    host = {k: torch.from_numpy(case[k]).pin_memory().numpy() for k in ("flags", "rho", "u", "phi")}
     h2d = sum(v.nbytes for v in host.values())
+    mask = fslbm.FIELD_FLAGS | fslbm.FIELD_RHO | fslbm.FIELD_U | fslbm.FIELD_PHI
+    out = {"flags": np.empty(N, np.uint8), "rho": np.empty(N), "u": np.empty((N, 3)), "phi": np.empty(N)}
+    out = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in out.items()}
+    d2h_end = sum(v.nbytes for v in out.values())
     lat = fslbm.Lattice(case["dims"], case["params"], precision=form)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -308,11 +379,11 @@ def e2e_run(case, form, steps, local_rank):
     for _ in range(steps):
         lat.step(1)
         lat.step_mass()
+    lat.get_into(mask, out)
     t1 = time.perf_counter()
     lat.close()
-    N = int(case["flags"].size)
     return dict(value=N * steps / (t1 - t0) / 1e6, seconds=t1 - t0, h2d_bytes=h2d,
-                d2h_bytes_per_step=8 + 4)
+                d2h_bytes_per_step=8 + 4 + d2h_end / steps)
 
 
 # ---------------------------------------------------------------------------
@@ -359,8 +430,10 @@ def main():
         print(json.dumps({"saved": args.save_state, "steps": args.save_after, "counters": lat.counters()}))
         return 0
 
+    if ws > 1:
+        return main_slabs(args, rank, ws, local_rank, forms[0])
     head = run_form(case, forms[0], args.steps, args.warmup, ws, rank, local_rank, clocks=True,
-                    state=args.load_state)
+                    state=args.load_state, spinup=0 if args.load_state else args.spinup)
     ms_max = max_over_ranks(head["ms"], ws, torch.device("cuda", local_rank))
     value = ws * N * args.steps / (ms_max / 1e3) / 1e6
 
@@ -382,16 +455,21 @@ def main():
         "config": {"workload": WORKLOAD if dims_for(args) == DIMS else "dam_break_%dx%dx%d" % dims_for(args),
                    "dims": list(dims_for(args)), "rule": "FSL" if args.rule else "FSK", "tau": args.tau,
                    "magic": args.magic, "g": 1e-5,
-                   "precision": forms[0], "parallelism": f"replicas x{ws}",
+                   "precision": forms[0], "parallelism": "one lattice, one GPU",
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (N * 2 * 19 * s / 1e9),
-                   "start": ("saved state " + args.load_state) if args.load_state else "initial column"},
+                   "start": ("saved state " + args.load_state) if args.load_state else
+                   ("after %d untimed steps from the initial column (middle of the 10000-step run)" % args.spinup
+                    if args.spinup else "initial column")},
         "mflups_active": round(ws * (head["n_liquid"] + head["n_interface"]) * args.steps
                                / (ms_max / 1e3) / 1e6, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": ncu_traffic(forms[0]),
                      "kernel": {"tma": "k_bulk_tma", "async": "k_bulk_async"}.get(head["bulk_loads"], "k_bulk"),
                      "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_bulk, "launch_ms": round(bulk_ms, 5)},
+                     "alg_bytes_per_launch": alg_bulk, "launch_ms": round(bulk_ms, 5),
+                     "step": {"frac": round(step_gbs / peak, 4), "achieved": round(step_gbs, 1),
+                              "note": "whole FP32 step (all kernels) over the same peak; the target of 0.70 is "
+                                      "for this figure"}},
         "step_roofline": {"achieved": round(step_gbs, 1), "frac": round(step_gbs / peak, 4),
                           "alg_bytes_per_step": alg_step},
         "kernel_ms_per_step": {"bulk": round(head["groups_ms"][0], 5), "iface": round(head["groups_ms"][1], 5),
@@ -413,15 +491,32 @@ def main():
                     "bulk_gbs": round(bulk / (r["groups_ms"][0] / 1e3) / 1e9, 1),
                     "bulk_frac": round(bulk / (r["groups_ms"][0] / 1e3) / 1e9 / peak, 4),
                     "kernel_ms_per_step": [round(x, 5) for x in r["groups_ms"]]}
+    # the configuration as written (tau = 0.51, Lambda = 3/16): from its
+    # initial state for the steps it runs stably (a non-finite density
+    # appears between 3500 and 9000 steps)
+    if args.as_written_steps:
+        aw = argparse.Namespace(**{**vars(args), "tau": 0.51, "magic": 3.0 / 16.0})
+        case_aw = make_case(aw)
+        r = run_form(case_aw, forms[0], args.as_written_steps, 0, ws, rank, local_rank)
+        sb = STORE_BYTES[forms[0]]
+        st_b = (r["n_liquid"] + r["n_interface"]) * 2 * 19 * sb + N + r["n_interface"] * 24
+        other["as_written_tau0.51_magic3/16"] = {
+            "form": forms[0], "value": round(N * args.as_written_steps / (r["ms"] / 1e3) / 1e6, 2),
+            "steps": args.as_written_steps, "start": "initial column",
+            "ms_per_step": round(r["ms"] / args.as_written_steps, 5),
+            "step_frac": round(st_b / (r["ms"] / args.as_written_steps / 1e3) / 1e9 / peak, 4),
+            "kernel_ms_per_step": [round(x, 5) for x in r["groups_ms"]],
+            "mass_drift_rel": (r["mass1"] - r["mass0"]) / r["mass0"]}
     line["forms"] = other
     # end to end through the C interface with host buffers
-    e2e_steps = args.e2e_steps or args.steps
+    e2e_steps = args.e2e_steps or (args.spinup + args.warmup + args.steps)
     e2e = e2e_run(case, forms[0], e2e_steps, local_rank)
     e2e_v = max_over_ranks(-e2e["value"], ws, torch.device("cuda", local_rank))
     line["e2e"] = {"value": round(-e2e_v * ws, 2), "unit": "MLUPS",
                    "h2d_bytes_per_step": e2e["h2d_bytes"] // e2e_steps,
-                   "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "steps": e2e_steps,
-                   "includes": "state upload from pinned host memory, per-step mass read"}
+                   "d2h_bytes_per_step": round(e2e["d2h_bytes_per_step"], 1), "steps": e2e_steps,
+                   "includes": "initial state from pinned host memory, per-step mass read, final fields "
+                               "(flags, rho, u, phi) read back"}
     # differentiation: adjoint step cost per forward step (FP64 and FP32)
     if not args.no_adjoint:
         # (FP32 rounding drifts the film's mass and fills a surface cell after
@@ -451,6 +546,110 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def main_slabs(args, rank, ws, local_rank, form):
+    """N > 1: one lattice of the dam break widened N times along y (weak
+    scaling: every rank owns a full-size 512 x 256 x 256 slab), split into N
+    y-slabs with ghost layers, one exchange of ghost layers with the
+    neighbouring ranks per step (NCCL point-to-point) and an FP64 all-reduce
+    of the mass.  The dam break is uniform along y, so every slab carries the
+    same work."""
+    import torch
+    import torch.distributed as dist
+    from paper_1409_5645_gb300 import cases, fslbm, slabs
+    dev = torch.device("cuda", local_rank)
+    nx, ny, nz = dims_for(args)
+    cx, cz = col_for(args)
+    gdims = (nx, ny * ws, nz)
+    slab = slabs.Slab(gdims, 1, ws, rank)
+    local = cases.dam_break(nx=nx, ny=slab.hi - slab.lo, nz=nz, col_x=cx, col_z=cz, tau=args.tau,
+                            magic=args.magic, rule=args.rule, bulk_loads=args.bulk_loads, seed=cases.SEED + rank)
+    stream = torch.cuda.Stream(device=dev)
+    lat = fslbm.Lattice(local["dims"], local["params"], precision=form, stream=stream.cuda_stream)
+    t = {k: torch.from_numpy(local[k]).to(dev) for k in ("flags", "rho", "u", "phi")}
+    lat.init_equilibrium(t["flags"], t["rho"], t["u"], t["phi"])
+    del t
+    run = slabs.DistSlab(lat, slab, dev)
+    run.exchange()  # ghost layers from the neighbours' owned cells
+    run.step(args.spinup + args.warmup)
+    lat.sync()
+    M0, _ = run.total_mass()
+    lat.timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    ck = NvmlClocks(local_rank)
+    time.sleep(0.01)
+    e0.record(stream)
+    run.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = ck.stop() if ck.ok else None
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, ws, dev)
+    groups, _ = lat.timing_read()
+    lat.timing(False)
+    M1, lost = run.total_mass()
+    own = nx * (slab.o1 - slab.o0) * nz
+    nliq, nifc = count_kinds(lat)
+    s_b = STORE_BYTES[form]
+    peak, peak_kind = hbm_peak()
+    alg_bulk = nliq * 2 * 19 * s_b + lat.N
+    achieved = alg_bulk / (groups[0] / 1e3) / 1e9
+    value = ws * own * args.steps / (ms_max / 1e3) / 1e6
+    launches = (lat.launches_per_step + 2 * len(slab.neighbours())) * args.steps
+    # end to end: the slab's initial state from pinned host memory, steps with
+    # their exchanges, the all-reduced mass read every step, fields read back
+    host = {k: torch.from_numpy(local[k]).pin_memory().numpy() for k in ("flags", "rho", "u", "phi")}
+    e2e_steps = args.e2e_steps or args.steps
+    lat2 = fslbm.Lattice(local["dims"], local["params"], precision=form)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    lat2.init_equilibrium(host["flags"], host["rho"], host["u"], host["phi"])
+    run2 = slabs.DistSlab(lat2, slab, dev)
+    run2.exchange()
+    for _ in range(e2e_steps):
+        run2.step(1)
+        run2.total_mass()
+    fields = lat2.get(fslbm.FIELD_FLAGS | fslbm.FIELD_RHO | fslbm.FIELD_U | fslbm.FIELD_PHI)
+    t1 = time.perf_counter()
+    e2e_max = max_over_ranks(t1 - t0, ws, dev)
+    d2h = sum(v.nbytes for v in fields.values())
+    lat2.close()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": form, "data": "synthetic",
+        "config": {"workload": "dam_break_%dx%dx%d_fsl_y_slabs" % gdims, "dims": list(gdims), "rule":
+                   "FSL" if args.rule else "FSK", "tau": args.tau, "magic": args.magic, "g": 1e-5,
+                   "precision": form, "parallelism": f"y-slabs x{ws}, {slabs.GHOST} ghost layers per cut, "
+                                                     f"NCCL point-to-point",
+                   "l2": "inputs larger than L2", "start": "after %d untimed steps" % args.spinup},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_bulk",
+                     "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bulk, "launch_ms": round(groups[0], 5),
+                     "rank": 0},
+        "kernel_ms_per_step": {"bulk": round(groups[0], 5), "iface": round(groups[1], 5),
+                               "reduce": round(groups[2], 5), "conversions": round(groups[3], 5)},
+        "halo_bytes_per_step": run.bytes_per_exchange,
+        "mass_drift_rel": (M1 - M0) / M0,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": {"value": round(ws * own * e2e_steps / e2e_max / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": sum(v.nbytes for v in host.values()) // e2e_steps,
+                "d2h_bytes_per_step": round(16 + d2h / e2e_steps, 1), "steps": e2e_steps,
+                "includes": "slab state from pinned host memory, exchanges, all-reduced mass read every step, "
+                            "fields read back"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    dist.destroy_process_group()
+    return 0
 
 
 def reference_arm(args):

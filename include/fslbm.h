@@ -161,6 +161,13 @@ typedef struct {
                          pulled values (FP64 always loads them plainly); same results every way */
   int precision;      /* fslbm_precision */
   void *stream;       /* cudaStream_t for all work of the handle; NULL = legacy default */
+  int elvira;         /* 1: where the height columns along the dominant axis are open, the
+                         interface normal by ELVIRA (Pilliod & Puckett) in place of the Parker-Youngs
+                         gradient: 27 candidates from backward, central and forward differences of
+                         3-cell column sums of the 3x3x3 block along each axis, the one whose planes
+                         (each through the cell's own fill) best reproduce the block's fill levels;
+                         exact for planes.  The higher-order reconstruction the conclusion (Sec. 5)
+                         asks of the interface position.  0 (default): Parker-Youngs */
 } fslbm_params;
 
 /* Defaults: tau 0.8, magic 3/16, g 0, rho_G 1, sigma 0, FSL, rho_0 = 1,
@@ -252,12 +259,15 @@ int fslbm_timing_read(fslbm_t *h, double ms[4], long long *steps);
 /* ---- Differentiation: hand-written adjoint -------------------------------
  * The differentiated map runs from the initial populations of the current
  * state (as set by fslbm_init_equilibrium / fslbm_set_state, whose collision
- * is included) through nsteps time steps to an objective J, at fixed cell
- * flags: every discrete decision of the forward pass (flags, the height-
- * function or plane-fit branch, the dominant axis, clamps of delta) is held.
+ * is included) through nsteps time steps to an objective J, with every
+ * discrete decision of the forward pass held: the cell flags of every step,
+ * so that cell conversions are replayed as the forward pass took them (the
+ * adjoints of the new cells' equilibrium initialisation, of the excess split
+ * and of m = rho for new cells from liquid are taken; Sec. 2.3), the height-
+ * function or plane-fit branch, the dominant axis, clamps of delta.
  * Supported: rho_0 = 1, sigma = 0, D = 0 (stress off), resting walls (wall_u = 0), u_b = u(x_b)
- * (ub_extrap = 0), gas links only (recon_nc = 0), and no cell conversion inside the window
- * (FSLBM_ERR_STATE otherwise).  Parameters: nu = (tau - 1/2)/3 with the magic
+ * (ub_extrap = 0), gas links only (recon_nc = 0) and the equal excess split (excess_split = 0);
+ * FSLBM_ERR_ARG otherwise.  Parameters: nu = (tau - 1/2)/3 with the magic
  * parameter Lambda held fixed, g, and the initial fill levels phi0 of
  * interface cells (m0 = phi0 rho0). */
 enum fslbm_objective {
@@ -266,14 +276,15 @@ enum fslbm_objective {
 };
 
 /* Forward pass: run nsteps >= 1 steps from the current state with a full
- * checkpoint (f~, m, phi) every K >= 1 steps, and return J.  Holds
+ * checkpoint (flags, f~, m, phi) every K >= 1 steps, and return J.  Holds
  * ceil(nsteps/K) checkpoints on the device until the handle's state is set
  * again or the handle is destroyed. */
 int fslbm_adjoint_forward(fslbm_t *h, int nsteps, int K, int objective, double *J);
 
 /* Reverse pass (once per forward pass): recompute each K-step segment from
- * its checkpoint, storing its states, and run the adjoint step kernels
- * backwards.  Returns dJ/dnu, dJ/dg[3], and dJ/dphi0[N] (zero off interface
+ * its checkpoint, storing its K + 1 states (flags included), and run the
+ * adjoint step kernels backwards, the reverse of each step's conversions
+ * first.  Returns dJ/dnu, dJ/dg[3], and dJ/dphi0[N] (zero off interface
  * cells; host or device per `where`; NULL to skip).  Afterwards the handle
  * holds the state of step min(K, nsteps). */
 int fslbm_adjoint_backward(fslbm_t *h, double *dJ_dnu, double dJ_dg[3], double *dJ_dphi0, int where);

@@ -140,6 +140,8 @@ struct Params {
   int recon_nc;      // 1: interface cells also rebuild links p with n.c_p > 0 toward a fluid node
                      //    (Koerner et al.'s reconstruction along the normal, Sec. 4.4 citation)
   int excess_split;  // 1: excess mass split with weights along the fill-level normal (Thuerey)
+  int elvira;        // 1: where the height columns are open, the ELVIRA normal (Pilliod & Puckett)
+                     //    in place of the Parker-Youngs one (the higher-order reconstruction of Sec. 5)
 };
 
 template <class T>
@@ -471,9 +473,84 @@ struct Sim {
         for (int t = 0; t < 2 && !got; ++t) got = height_curvature(i, ax[t], val(n[ax[t]]) > 0 ? 1 : -1, kappa);
         if (!got) kappa = normal_divergence(i, n);
       }
-      T len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-      for (int k = 0; k < 3; ++k) n[k] = n[k] / len;
-      d = plic_offset(n, phi_of(i));
+      if (p.elvira) {
+        elvira(i, n, d);
+      } else {
+        T len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int k = 0; k < 3; ++k) n[k] = n[k] / len;
+        d = plic_offset(n, phi_of(i));
+      }
+    }
+  }
+
+  // Volume fraction of the unit cell around a node on the side n.x <= d of
+  // the plane (n a unit vector, x from the node).
+  static T plane_volume(const T n[3], const T& d) {
+    T ms[3] = {absT(n[0]), absT(n[1]), absT(n[2])};
+    T L1 = ms[0] + ms[1] + ms[2];
+    for (int a = 0; a < 3; ++a) ms[a] = ms[a] / L1;
+    std::sort(ms, ms + 3, [](const T& a, const T& b) { return val(a) < val(b); });
+    return cube_volume(d / L1 + T(0.5), ms);
+  }
+
+  // ELVIRA (Pilliod and Puckett, "Second-order accurate volume-of-fluid
+  // algorithms for tracking material interfaces", J. Comput. Phys. 2004),
+  // in three dimensions: along each axis a, the fill levels of the 3x3x3
+  // block summed over 3 cells give column heights h(b, c); the backward,
+  // central and forward differences of h in the two other axes give nine
+  // candidate normals (s_a, -dh/db, -dh/dc), s_a the gas side of a (the sign
+  // of the Parker-Youngs component).  For each of the 27 candidates the plane
+  // through the cell's own fill is continued through the block; the one whose
+  // volume fractions match the block's fill levels best (least squares over
+  // the cells that are not walls, first minimum in the order a, b-difference,
+  // c-difference) gives the normal and the offset.  n: the Parker-Youngs
+  // normal on entry (not normalised).  A wall in a column takes the cell's own
+  // fill level, as in the gradient.
+  void elvira(long i, T n[3], T& d) const {
+    const T phc = phi_of(i);
+    const T npy[3] = {n[0], n[1], n[2]};
+    double best = 1e300;
+    for (int a = 0; a < 3; ++a) {
+      const int s = val(npy[a]) > 0 ? 1 : -1;
+      const int b = (a + 1) % 3, c = (a + 2) % 3;
+      T h[3][3];
+      for (int ib = -1; ib <= 1; ++ib)
+        for (int ic = -1; ic <= 1; ++ic) {
+          T sum = T(0);
+          for (int k = -1; k <= 1; ++k) {
+            int o[3] = {0, 0, 0};
+            o[a] = k; o[b] = ib; o[c] = ic;
+            long j = nbr(i, o[0], o[1], o[2]);
+            sum += type(j) == WALL ? phc : phi_of(j);
+          }
+          h[ib + 1][ic + 1] = sum;
+        }
+      const T db[3] = {h[1][1] - h[0][1], T(0.5) * (h[2][1] - h[0][1]), h[2][1] - h[1][1]};
+      const T dc[3] = {h[1][1] - h[1][0], T(0.5) * (h[1][2] - h[1][0]), h[1][2] - h[1][1]};
+      for (int kb = 0; kb < 3; ++kb)
+        for (int kc = 0; kc < 3; ++kc) {
+          T v[3];
+          v[a] = T((double)s); v[b] = T(-1.0) * db[kb]; v[c] = T(-1.0) * dc[kc];
+          T len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          T m[3] = {v[0] / len, v[1] / len, v[2] / len};
+          T dd = plic_offset(m, phc);
+          double err = 0.0;
+          for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+              for (int ox = -1; ox <= 1; ++ox) {
+                if (!ox && !oy && !oz) continue;
+                long j = nbr(i, ox, oy, oz);
+                if (type(j) == WALL) continue;
+                T shift = m[0] * T((double)ox) + m[1] * T((double)oy) + m[2] * T((double)oz);
+                double e = val(plane_volume(m, dd - shift)) - val(phi_of(j));
+                err += e * e;
+              }
+          if (err < best) {
+            best = err;
+            for (int k = 0; k < 3; ++k) n[k] = m[k];
+            d = dd;
+          }
+        }
     }
   }
 

@@ -55,7 +55,7 @@ class Params(C.Structure):
                 ("cleanup", C.c_int), ("delta_min", C.c_double), ("stress", C.c_int),
                 ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
                 ("ub_extrap", C.c_int), ("recon_nc", C.c_int),
-                ("excess_split", C.c_int)]
+                ("excess_split", C.c_int), ("elvira", C.c_int)]
 
 
 def lib(omp: bool = False):
@@ -133,6 +133,7 @@ def make_params(dims, p) -> Params:
     P.ub_extrap = int(p.get("ub_extrap", 0))
     P.recon_nc = int(p.get("recon_nc", 0))
     P.excess_split = int(p.get("excess_split", 0))
+    P.elvira = int(p.get("elvira", 0))
     return P
 
 

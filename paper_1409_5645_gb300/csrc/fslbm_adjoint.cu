@@ -13,10 +13,30 @@
 //                 read (mass-exchange weights, height functions) with atomics.
 //   k_adj_gather  reverse of the pull: abar_q(y) = O_q(y) + P_q(y + c_q).
 // Parameters: lambda_+, lambda_- (-> nu with Lambda fixed) and g, reduced per
-// block.  Interface decisions (flags, the height-function/PLIC branch, the
-// dominant axis, clamps of delta) are held fixed: a clamped delta or a cell
-// whose plane came from the PLIC fallback passes no derivative to phi.
-// Supported: rho_0 = 1, sigma = 0, no conversions inside the window.
+// block.  Interface decisions (flags, the height-function/plane-fit branch,
+// the dominant axis, clamps of delta) are held fixed; a clamped delta passes
+// no derivative.  delta = d / (n.c_p) is differentiated through the heights
+// where the height columns are closed, and through the plane fit elsewhere:
+// the volume identity V(n, d) = phi (the section's area and centroid) and
+// the Parker-Youngs normal of the fill levels around the cell.
+// Cell conversions are replayed as the forward pass took them: the flags of
+// every step are recorded (in the checkpoints and in the recomputed segment),
+// and two kernels per step reverse the conversion stage before k_adj_local
+// reverses the rest of the step:
+//   k_adj_conv1   per cell of the new state: the adjoint of the final mass
+//                 (m_bar + phi_bar / rho) and of the density (from phi =
+//                 m / rho) of every interface cell; per new cell from gas the
+//                 reverse of its collided equilibrium f^eq(mean rho, mean u)
+//                 down to the means of its fluid neighbours
+//   k_adj_conv2   per fluid cell of the old state: the adjoint of its
+//                 post-collision populations and mass before the
+//                 conversions: the excess of a filled (m - rho) or emptied
+//                 (m) cell gathers its receivers' mass adjoints over their
+//                 number (equal split), a new cell from liquid passes its mass
+//                 adjoint to rho, the new cells' means to their neighbours.
+// The receivers of a step are the cells that are interface after it, so the
+// two recorded flag fields decide every branch.
+// Supported: rho_0 = 1, sigma = 0, equal excess split.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -35,9 +55,14 @@ struct AdjointState {
   void* ck_f = nullptr;
   double* ck_m = nullptr;
   void* ck_phi = nullptr;
-  void* seg_f = nullptr;
+  uint8_t* ck_flags = nullptr;
+  void* seg_f = nullptr;  // K + 1 states of the segment being reversed
   double* seg_m = nullptr;
   void* seg_phi = nullptr;
+  uint8_t* seg_flags = nullptr;
+  double* Mh = nullptr;  // conversion reverse: final-mass and density adjoints, new-cell means
+  double* rh = nullptr;
+  double* ngb = nullptr;
   double* abar[2] = {nullptr, nullptr};
   double* P = nullptr;
   double* mbar[2] = {nullptr, nullptr};
@@ -46,6 +71,7 @@ struct AdjointState {
   double* red = nullptr;    // objective reductions
   double* dphi0 = nullptr;
   int conv0 = 0;
+  long long conversions = 0;  // cell conversions inside the window
   double J = 0.0, gseed = 0.0;
   double fwd_ms = 0.0, adj_ms = 0.0;
   size_t bytes = 0;
@@ -167,6 +193,73 @@ __device__ __forceinline__ void block_add(double (&th)[5], double* out) {
     double s = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
     if (s != 0.0) atomicAdd(out + threadIdx.x, s);
   }
+}
+
+// Area A and centroid c of the section of the unit cell [-1/2, 1/2]^3 by the
+// plane n.x = d (n a unit vector).  The volume V(n, d) on the side n.x <= d
+// has dV/dd = A and dV/dn = -A c, so at fixed V the plane offset moves by
+// dd = dV / A + c.dn (the adjoint of the plane fit).  The polygon's corners
+// are the plane's crossings of the twelve cell edges, ordered by angle about
+// their mean; triangles from the mean give A and c.
+__device__ void plane_section(const double (&n)[3], double d, double& A, double (&c)[3]) {
+  double P[12][3];
+  int np = 0;
+  for (int e = 0; e < 3; ++e) {
+    if (fabs(n[e]) < 1e-12) continue;  // the four edges along e are parallel to the plane
+    const int a1 = (e + 1) % 3, a2 = (e + 2) % 3;
+    for (int s1 = -1; s1 <= 1; s1 += 2)
+      for (int s2 = -1; s2 <= 1; s2 += 2) {
+        const double x1 = 0.5 * s1, x2 = 0.5 * s2;
+        const double t = (d - n[a1] * x1 - n[a2] * x2) / n[e];
+        if (t >= -0.5 && t <= 0.5) {
+          P[np][e] = t;
+          P[np][a1] = x1;
+          P[np][a2] = x2;
+          ++np;
+        }
+      }
+  }
+  A = 0.0;
+  c[0] = c[1] = c[2] = 0.0;
+  if (np < 3) return;
+  double m[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < np; ++k)
+    for (int j = 0; j < 3; ++j) m[j] += P[k][j] / np;
+  // in-plane basis: u from the axis least aligned with n, v = n x u
+  int ax = 0;
+  if (fabs(n[1]) < fabs(n[ax])) ax = 1;
+  if (fabs(n[2]) < fabs(n[ax])) ax = 2;
+  double u[3] = {-n[ax] * n[0], -n[ax] * n[1], -n[ax] * n[2]};
+  u[ax] += 1.0;
+  const double lu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  u[0] /= lu; u[1] /= lu; u[2] /= lu;
+  const double v[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+  double ang[12];
+  int ord[12];
+  for (int k = 0; k < np; ++k) {
+    const double r0 = P[k][0] - m[0], r1 = P[k][1] - m[1], r2 = P[k][2] - m[2];
+    ang[k] = atan2(r0 * v[0] + r1 * v[1] + r2 * v[2], r0 * u[0] + r1 * u[1] + r2 * u[2]);
+    ord[k] = k;
+  }
+  for (int k = 1; k < np; ++k)  // insertion sort by angle
+    for (int j = k; j > 0 && ang[ord[j]] < ang[ord[j - 1]]; --j) {
+      const int t = ord[j];
+      ord[j] = ord[j - 1];
+      ord[j - 1] = t;
+    }
+  for (int k = 0; k < np; ++k) {
+    const double* p0 = P[ord[k]];
+    const double* p1 = P[ord[(k + 1) % np]];
+    const double e0[3] = {p0[0] - m[0], p0[1] - m[1], p0[2] - m[2]};
+    const double e1[3] = {p1[0] - m[0], p1[1] - m[1], p1[2] - m[2]};
+    const double cr = (e0[1] * e1[2] - e0[2] * e1[1]) * n[0] + (e0[2] * e1[0] - e0[0] * e1[2]) * n[1] +
+                      (e0[0] * e1[1] - e0[1] * e1[0]) * n[2];
+    const double at = 0.5 * fabs(cr);
+    A += at;
+    for (int j = 0; j < 3; ++j) c[j] += at * (m[j] + p0[j] + p1[j]) / 3.0;
+  }
+  if (A > 0.0)
+    for (int j = 0; j < 3; ++j) c[j] /= A;
 }
 
 template <int P>
@@ -335,6 +428,8 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
     double utb[3] = {0, 0, 0}, rtb = 0.0;
     double Hbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool geo_used = false;
+    double dbar = 0.0, nbar[3] = {0.0, 0.0, 0.0};  // plane-fit cells: adjoints of the offset and unit normal
+    bool plic_used = false;
     if (gasm) {
 #pragma unroll
       for (int q = 1; q < 19; ++q) {
@@ -360,8 +455,23 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
         rtb += (pq <= 6 ? 1.0 / 18.0 : 1.0 / 36.0) * etb;
         deplus_du(p, pq, utx, uty, utz, etb, utb);
         th[0] += -nb * (0.5 * (own[pq] + own[q]) - et[q]) * inv1 * inv1;
-        // delta -> heights (closed height columns, unclamped delta only)
+        // delta -> heights (closed height columns) or -> plane offset and
+        // normal (plane fit), unclamped delta only
         const double db = fbq * (-own[pq] + F[pq] + lp * npl[q]);
+        if (G.ok && !G.closed && db != 0.0) {
+          const double cn = cx(pq) * (double)G.n[0] + cy(pq) * (double)G.n[1] + cz(pq) * (double)G.n[2];
+          if (cn > 0.0) {
+            const double raw = (double)G.d / cn;
+            if (raw > p.delta_min && raw < 1.0) {  // delta = d / (n.c_p)
+              dbar += db / cn;
+              const double t = -db * raw / cn;
+              nbar[0] += t * cx(pq);
+              nbar[1] += t * cy(pq);
+              nbar[2] += t * cz(pq);
+              plic_used = true;
+            }
+          }
+        }
         if (G.ok && G.closed && db != 0.0) {
           const int A = G.a, B = G.b, Cc = 3 - G.a - G.b;
           const int ca = A == 0 ? cx(pq) : (A == 1 ? cy(pq) : cz(pq));
@@ -407,6 +517,49 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
             }
           }
         }
+    }
+    if (plic_used) {
+      // the plane fit: d = d(n, phi_c) with V(n, d) = phi_c (phi_c kept in
+      // [1e-9, 1 - 1e-9]), n = -g / |g| with g the Parker-Youngs gradient of
+      // the fill levels around the cell (a wall takes phi_c)
+      const double nh[3] = {(double)G.n[0], (double)G.n[1], (double)G.n[2]};
+      double A, cen[3];
+      plane_section(nh, (double)G.d, A, cen);
+      if (A > 0.0 && phic > 1e-9 && phic < 1.0 - 1e-9) phib_self += dbar / A;
+      for (int k = 0; k < 3; ++k) nbar[k] += dbar * cen[k];
+      double gr[3] = {0.0, 0.0, 0.0};
+      double ws[26][3];
+      long long js[26];
+      int no = 0;
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (!dx && !dy && !dz) continue;
+            const long long j = nbr(p, x, y, z, dx, dy, dz);
+            const uint8_t kj = kind_at(a.flags, j);
+            double pj = 0.0;
+            if (kj == LIQ) pj = 1.0;
+            else if (kj == IFC || (kj == GAS && p.freeze)) pj = (double)a.phi[j];
+            else if (kj == WALL) pj = phic;
+            const int ax_ = dx < 0 ? -dx : dx, ay_ = dy < 0 ? -dy : dy, az_ = dz < 0 ? -dz : dz;
+            ws[no][0] = dx * (2 - ay_) * (2 - az_);
+            ws[no][1] = dy * (2 - az_) * (2 - ax_);
+            ws[no][2] = dz * (2 - ax_) * (2 - ay_);
+            for (int k = 0; k < 3; ++k) gr[k] += ws[no][k] * pj;
+            js[no] = (kj == WALL) ? -2 : ((kj == IFC || (kj == GAS && p.freeze)) ? j : -1);
+            ++no;
+          }
+      const double gl = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+      const double nd = nbar[0] * nh[0] + nbar[1] * nh[1] + nbar[2] * nh[2];
+      double gb[3];  // adjoint of g (n = -g / |g|)
+      for (int k = 0; k < 3; ++k) gb[k] = -(nbar[k] - nd * nh[k]) / gl;
+      for (int o = 0; o < no; ++o) {
+        if (js[o] == -1) continue;
+        const double val = gb[0] * ws[o][0] + gb[1] * ws[o][1] + gb[2] * ws[o][2];
+        if (val == 0.0) continue;
+        if (js[o] == -2) phib_self += val;
+        else atomicAdd(a.phibar_out + js[o], val);
+      }
     }
     // own moments: rho_t = sum f~, u_t = sum c f~ - g/2
 #pragma unroll
@@ -554,6 +707,164 @@ __global__ void __launch_bounds__(128) k_adj_init(Par p, const uint8_t* flags, c
   block_add(th, theta);
 }
 
+// Reverse of the conversions of one step, part 1 (see the file header).
+// flags0 / flags1: the flags before / after the step; f1, m1: the state after
+// it (post-collision populations, mass); abar, mbar, phibar: adjoints of that
+// state.  Writes Mh, rh (interface cells after the step) and, per new cell
+// from gas, ngb[4 j + 0..3] = (adjoint of mean rho, of mean u) / count.
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_conv1(Par p, const uint8_t* __restrict__ flags0,
+                                                   const uint8_t* __restrict__ flags1,
+                                                   const typename Form<P>::S* __restrict__ f1,
+                                                   const double* __restrict__ m1, const double* __restrict__ abar,
+                                                   const double* __restrict__ mbar, const double* __restrict__ phibar,
+                                                   double* __restrict__ Mh, double* __restrict__ rh,
+                                                   double* __restrict__ ngb, double* theta) {
+  const size_t N = (size_t)p.N;
+  double th[5] = {0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t k0 = flags0[i] & KIND, k1 = flags1[i] & KIND;
+    Mh[i] = 0.0;
+    rh[i] = 0.0;
+    if (k1 != IFC) continue;
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) r += ldq_full<P>(f1, q * N + i, q);
+    // phi = m / rho after the step
+    const double pb = phibar[i];
+    const double Mhat = mbar[i] + pb / r;
+    const double rhat = -pb * m1[i] / (r * r);
+    Mh[i] = Mhat;
+    rh[i] = rhat;
+    if (k0 != GAS) continue;
+    // a new cell from gas: f~ = C(f^eq(rbar, ubar)), means over the fluid
+    // neighbours (flags before the step) of their rho = sum f~ and
+    // u = sum c f~ - g/2 (rho_0 = 1)
+    int x, y, z;
+    coords(p, i, x, y, z);
+    double rs = 0.0, us[3] = {0.0, 0.0, 0.0};
+    int cnt = 0;
+    for (int l = 1; l < 19; ++l) {
+      const long long yj = nbr(p, x, y, z, cx(l), cy(l), cz(l));
+      if (yj < 0 || !is_fluid(flags0[yj] & KIND)) continue;
+      double ry = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+      for (int q = 0; q < 19; ++q) {
+        const double v = ldq_full<P>(f1, q * N + yj, q);
+        ry += v;
+        jx += cx(q) * v;
+        jy += cy(q) * v;
+        jz += cz(q) * v;
+      }
+      rs += ry;
+      us[0] += jx - 0.5 * p.g[0];
+      us[1] += jy - 0.5 * p.g[1];
+      us[2] += jz - 0.5 * p.g[2];
+      ++cnt;
+    }
+    ngb[4 * i] = ngb[4 * i + 1] = ngb[4 * i + 2] = ngb[4 * i + 3] = 0.0;
+    if (!cnt) continue;
+    const double rbar = rs / cnt, ub0 = us[0] / cnt, ub1 = us[1] / cnt, ub2 = us[2] / cnt;
+    double feq[19], ab[19], fb[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+      feq[q] = eplus_d(p, q, rbar, ub0, ub1, ub2) + 3.0 * w * (cx(q) * ub0 + cy(q) * ub1 + cz(q) * ub2);
+      // its density after the step, sum f~ = sum f^eq, carries rhat
+      ab[q] = abar[q * N + i] + rhat;
+      fb[q] = 0.0;
+    }
+    collide_rev(p, feq, ab, fb, th);
+    double rb = 0.0, ubr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+      rb += w * fb[q];
+      deplus_du(p, q, ub0, ub1, ub2, fb[q], ubr);
+      ubr[0] += 3.0 * w * cx(q) * fb[q];
+      ubr[1] += 3.0 * w * cy(q) * fb[q];
+      ubr[2] += 3.0 * w * cz(q) * fb[q];
+    }
+    // u of each neighbour carries -g/2
+    th[2] -= 0.5 * ubr[0];
+    th[3] -= 0.5 * ubr[1];
+    th[4] -= 0.5 * ubr[2];
+    ngb[4 * i] = rb / cnt;
+    ngb[4 * i + 1] = ubr[0] / cnt;
+    ngb[4 * i + 2] = ubr[1] / cnt;
+    ngb[4 * i + 3] = ubr[2] / cnt;
+  }
+  block_add(th, theta);
+}
+
+// Part 2, per fluid cell of the old flags: abar (in place) becomes the adjoint
+// of the step's post-collision populations before the conversions, mbar that
+// of the exchanged mass m + dm, phibar zero (the fill levels' adjoints are in
+// Mh / rh).
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_conv2(Par p, const uint8_t* __restrict__ flags0,
+                                                   const uint8_t* __restrict__ flags1,
+                                                   const double* __restrict__ Mh, const double* __restrict__ rh,
+                                                   const double* __restrict__ ngb, double* __restrict__ abar,
+                                                   double* __restrict__ mbar, double* __restrict__ phibar) {
+  const size_t N = (size_t)p.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint8_t k0 = flags0[i] & KIND, k1 = flags1[i] & KIND;
+    phibar[i] = 0.0;
+    if (!is_fluid(k0)) continue;
+    int x, y, z;
+    coords(p, i, x, y, z);
+    double add = 0.0, mb = 0.0;
+    if (k1 == IFC) add += rh[i];                 // rho after the step = sum f~
+    if (k0 == LIQ && k1 == IFC) add += Mh[i];    // new from liquid: m = rho + shares
+    if (k0 == IFC) {
+      if (k1 == IFC) {
+        mb = Mh[i];                              // m + dm + shares
+      } else {
+        // filled (-> liquid) or emptied (-> gas): excess over the receivers,
+        // the neighbours that are interface after the step
+        double s = 0.0;
+        int nr = 0;
+        for (int l = 1; l < 19; ++l) {
+          const long long r = nbr(p, x, y, z, cx(l), cy(l), cz(l));
+          if (r < 0 || (flags1[r] & KIND) != IFC) continue;
+          s += Mh[r];
+          ++nr;
+        }
+        const double exb = nr ? s / nr : 0.0;
+        mb = exb;                                // excess m + dm - rho (filled) or m + dm (emptied)
+        if (k1 == LIQ) add -= exb;
+      }
+    }
+    double ng0 = 0.0, ng1 = 0.0, ng2 = 0.0, ng3 = 0.0;  // means of the new cells from gas next to i
+    for (int l = 1; l < 19; ++l) {
+      const long long j = nbr(p, x, y, z, cx(l), cy(l), cz(l));
+      if (j < 0 || (flags0[j] & KIND) != GAS || (flags1[j] & KIND) != IFC) continue;
+      ng0 += ngb[4 * j];
+      ng1 += ngb[4 * j + 1];
+      ng2 += ngb[4 * j + 2];
+      ng3 += ngb[4 * j + 3];
+    }
+    const bool keep = is_fluid(k1);  // an emptied cell's populations reach nothing else
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+      abar[q * N + i] = (keep ? abar[q * N + i] : 0.0) + add + ng0 + cx(q) * ng1 + cy(q) * ng2 + cz(q) * ng3;
+    mbar[i] = mb;
+  }
+}
+
+template <int P>
+static void launch_conv(const Par& p, const uint8_t* flags0, const uint8_t* flags1,
+                        const typename Form<P>::S* f1, const double* m1, double* abar, double* mbar,
+                        double* phibar, double* Mh, double* rh, double* ngb, double* theta, cudaStream_t st) {
+  int blocks = (int)((p.N + 127) / 128);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_adj_conv1<P><<<blocks, 128, 0, st>>>(p, flags0, flags1, f1, m1, abar, mbar, phibar, Mh, rh, ngb, theta);
+  k_adj_conv2<P><<<blocks, 128, 0, st>>>(p, flags0, flags1, Mh, rh, ngb, abar, mbar, phibar);
+}
+
 template <int P>
 static void launch_local(const Par& p, const AdjView<P>& a, cudaStream_t st) {
   int blocks = (int)((p.N + 127) / 128);
@@ -575,8 +886,9 @@ static int adj_fail(fslbm* h, int code, const char* what) {
 void fslbm_free_adjoint(fslbm* h) {
   if (!h || !h->adj) return;
   AdjointState* A = h->adj;
-  void* ptrs[] = {A->ck_f, A->ck_m, A->ck_phi, A->seg_f, A->seg_m, A->seg_phi, A->abar[0], A->abar[1], A->P,
-                  A->mbar[0], A->mbar[1], A->phibar[0], A->phibar[1], A->theta, A->red, A->dphi0};
+  void* ptrs[] = {A->ck_f, A->ck_m, A->ck_phi, A->ck_flags, A->seg_f, A->seg_m, A->seg_phi, A->seg_flags,
+                  A->Mh, A->rh, A->ngb, A->abar[0], A->abar[1], A->P, A->mbar[0], A->mbar[1], A->phibar[0],
+                  A->phibar[1], A->theta, A->red, A->dphi0};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete A;
@@ -595,17 +907,19 @@ static bool amalloc(AdjointState* A, void** p, size_t bytes) {
 static void* cur_f(fslbm* h) { return h->cur ? h->fB : h->fA; }
 static void* cur_phi(fslbm* h) { return (h->par.freeze || !h->cur) ? h->phiA : h->phiB; }
 
-static int save_state(fslbm* h, void* f, double* m, void* phi) {
+static int save_state(fslbm* h, void* f, double* m, void* phi, uint8_t* flags) {
   AdjointState* A = h->adj;
+  if (cudaMemcpyAsync(flags, h->flags, (size_t)h->par.N, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   if (cudaMemcpyAsync(f, cur_f(h), A->fbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   if (cudaMemcpyAsync(m, h->m, (size_t)h->par.N * 8, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   if (cudaMemcpyAsync(phi, cur_phi(h), A->rbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   return 0;
 }
 
-static int restore_state(fslbm* h, const void* f, const double* m, const void* phi) {
+static int restore_state(fslbm* h, const void* f, const double* m, const void* phi, const uint8_t* flags) {
   AdjointState* A = h->adj;
   h->cur = 0;
+  if (cudaMemcpyAsync(h->flags, flags, (size_t)h->par.N, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   if (cudaMemcpyAsync(h->fA, f, A->fbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   if (cudaMemcpyAsync(h->m, m, (size_t)h->par.N * 8, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
   if (cudaMemcpyAsync(h->phiA, phi, A->rbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess) return 1;
@@ -642,6 +956,8 @@ extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objectiv
   if (h->par.has_uw) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs resting walls");
   if (h->par.ub_extrap) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs u_b = u(x_b) (ub_extrap = 0)");
   if (h->par.recon_nc) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs the gas links only (recon_nc = 0)");
+  if (h->par.excess_split) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs the equal excess split");
+  if (h->par.elvira) return adj_fail(h, FSLBM_ERR_ARG, "adjoint needs the Parker-Youngs plane fit (elvira = 0)");
   fslbm_free_adjoint(h);
   AdjointState* A = new AdjointState();
   h->adj = A;
@@ -654,7 +970,8 @@ extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objectiv
   A->fbytes = 19 * N * sb;
   A->rbytes = N * (h->prec == FSLBM_F64 ? 8 : 4);
   bool ok = amalloc(A, &A->ck_f, A->fbytes * A->nck) && amalloc(A, (void**)&A->ck_m, N * 8 * A->nck) &&
-            amalloc(A, &A->ck_phi, A->rbytes * A->nck) && amalloc(A, (void**)&A->red, 64);
+            amalloc(A, &A->ck_phi, A->rbytes * A->nck) && amalloc(A, (void**)&A->ck_flags, N * A->nck) &&
+            amalloc(A, (void**)&A->red, 64);
   if (!ok) {
     fslbm_free_adjoint(h);
     return adj_fail(h, FSLBM_ERR_OOM, "adjoint checkpoint allocation");
@@ -667,7 +984,8 @@ extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objectiv
   cudaEventCreate(&e1);
   cudaEventRecord(e0, h->st);
   for (int s = 0; s < A->nck; ++s) {
-    if (save_state(h, (char*)A->ck_f + s * A->fbytes, A->ck_m + s * N, (char*)A->ck_phi + s * A->rbytes))
+    if (save_state(h, (char*)A->ck_f + s * A->fbytes, A->ck_m + s * N, (char*)A->ck_phi + s * A->rbytes,
+                   A->ck_flags + s * N))
       return adj_fail(h, FSLBM_ERR_CUDA, "checkpoint copy");
     int n = nsteps - s * K < K ? nsteps - s * K : K;
     int rc = fslbm_step(h, n);
@@ -683,8 +1001,7 @@ extern "C" int fslbm_adjoint_forward(fslbm_t* h, int nsteps, int K, int objectiv
   int rc = fslbm_sync(h);
   if (rc) return rc;
   cudaMemcpy(c, h->cnt, sizeof c, cudaMemcpyDeviceToHost);
-  if (c[8] != A->conv0)
-    return adj_fail(h, FSLBM_ERR_STATE, "cell conversions inside the differentiated window are not supported");
+  A->conversions = c[8] - A->conv0;
   double norm = 0.0;
   int orc;
   switch (h->prec) {
@@ -720,18 +1037,24 @@ static int backward_t(fslbm* h) {
   float adj_total = 0.f;
   long long adj_steps = 0;
   for (int s = A->nck - 1; s >= 0; --s) {
-    if (restore_state(h, (char*)A->ck_f + s * A->fbytes, A->ck_m + s * N, (char*)A->ck_phi + s * A->rbytes))
+    if (restore_state(h, (char*)A->ck_f + s * A->fbytes, A->ck_m + s * N, (char*)A->ck_phi + s * A->rbytes,
+                      A->ck_flags + s * N))
       return 1;
     int n = A->nsteps - s * A->K < A->K ? A->nsteps - s * A->K : A->K;
-    for (int k = 0; k < n; ++k) {
-      if (save_state(h, (char*)A->seg_f + k * A->fbytes, A->seg_m + k * N, (char*)A->seg_phi + k * A->rbytes))
+    for (int k = 0; k <= n; ++k) {  // the states before each step and after the last
+      if (save_state(h, (char*)A->seg_f + k * A->fbytes, A->seg_m + k * N, (char*)A->seg_phi + k * A->rbytes,
+                     A->seg_flags + k * N))
         return 1;
-      if (fslbm_step(h, 1)) return 1;
+      if (k < n && fslbm_step(h, 1)) return 1;
     }
     cudaEventRecord(e0, st);
     for (int k = n - 1; k >= 0; --k) {
+      if (!h->par.freeze)  // the step's conversions, as the forward pass took them
+        launch_conv<P>(h->par, A->seg_flags + k * N, A->seg_flags + (k + 1) * N,
+                       (const S*)((char*)A->seg_f + (k + 1) * A->fbytes), A->seg_m + (k + 1) * N, A->abar[cur],
+                       A->mbar[cur], A->phibar[cur], A->Mh, A->rh, A->ngb, A->theta, st);
       AdjView<P> a;
-      a.flags = h->flags;
+      a.flags = A->seg_flags + k * N;
       a.f = (const S*)((char*)A->seg_f + k * A->fbytes);
       a.m = A->seg_m + k * N;
       a.phi = (const R*)((char*)A->seg_phi + k * A->rbytes);
@@ -760,7 +1083,7 @@ static int backward_t(fslbm* h) {
   A->adj_ms = adj_total / (adj_steps ? adj_steps : 1);
   // initial collision and phi0
   k_adj_init<P><<<(int)((N + 127) / 128 < 152 * 16 ? (N + 127) / 128 : 152 * 16), 128, 0, st>>>(
-      h->par, h->flags, (const S*)A->ck_f, h->f0_valid ? h->f0 : nullptr, A->abar[cur], A->mbar[cur],
+      h->par, A->ck_flags, (const S*)A->ck_f, h->f0_valid ? h->f0 : nullptr, A->abar[cur], A->mbar[cur],
       A->phibar[cur], A->theta, A->dphi0);
   return cudaGetLastError() != cudaSuccess;
 }
@@ -775,8 +1098,11 @@ extern "C" int fslbm_adjoint_backward(fslbm_t* h, double* dJ_dnu, double dJ_dg[3
               amalloc(A, (void**)&A->P, 19 * N * 8) && amalloc(A, (void**)&A->mbar[0], N * 8) &&
               amalloc(A, (void**)&A->mbar[1], N * 8) && amalloc(A, (void**)&A->phibar[0], N * 8) &&
               amalloc(A, (void**)&A->phibar[1], N * 8) && amalloc(A, (void**)&A->theta, 64) &&
-              amalloc(A, (void**)&A->dphi0, N * 8) && amalloc(A, &A->seg_f, A->fbytes * A->K) &&
-              amalloc(A, (void**)&A->seg_m, N * 8 * A->K) && amalloc(A, &A->seg_phi, A->rbytes * A->K);
+              amalloc(A, (void**)&A->dphi0, N * 8) && amalloc(A, &A->seg_f, A->fbytes * (A->K + 1)) &&
+              amalloc(A, (void**)&A->seg_m, N * 8 * (A->K + 1)) &&
+              amalloc(A, &A->seg_phi, A->rbytes * (A->K + 1)) &&
+              amalloc(A, (void**)&A->seg_flags, N * (A->K + 1)) && amalloc(A, (void**)&A->Mh, N * 8) &&
+              amalloc(A, (void**)&A->rh, N * 8) && amalloc(A, (void**)&A->ngb, N * 4 * 8);
     if (!ok) return adj_fail(h, FSLBM_ERR_OOM, "adjoint buffer allocation");
   }
   int r;

@@ -108,6 +108,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   if (q.ub_extrap < 0 || q.ub_extrap > 1) return FSLBM_ERR_ARG;
   if (q.recon_nc < 0 || q.recon_nc > 1) return FSLBM_ERR_ARG;
   if (q.excess_split < 0 || q.excess_split > 1) return FSLBM_ERR_ARG;
+  if (q.elvira < 0 || q.elvira > 1) return FSLBM_ERR_ARG;
   if (q.compressible && (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0)) return FSLBM_ERR_ARG;
 
   fslbm* h = (fslbm*)calloc(1, sizeof(fslbm));
@@ -161,6 +162,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
     p.own_hi[a] = q.dims[a];
   }
   p.owned_all = 1;
+  p.elvira = q.elvira;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;

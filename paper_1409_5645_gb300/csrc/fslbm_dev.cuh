@@ -155,6 +155,7 @@ struct Par {
   // the lost ledger); owned_all: every cell
   int own_lo[3], own_hi[3];
   int owned_all;
+  int elvira;              // 1: ELVIRA normal where the height columns are open
 };
 
 __device__ __forceinline__ bool owned(const Par& p, int x, int y, int z) {
@@ -668,12 +669,99 @@ __device__ __noinline__ R curvature_open(const Par& p, const uint8_t* __restrict
   return div;
 }
 
+// Volume fraction of the cell around a node on the side n.x <= d of a plane
+// (n unit, x from the node): the plane/cube volume in the L1-normalised,
+// sorted normal.
+template <class R>
+__device__ __forceinline__ R plane_volume(R n0, R n1, R n2, R d) {
+  R a0 = fabs(n0), a1 = fabs(n1), a2 = fabs(n2);
+  const R L1 = a0 + a1 + a2;
+  a0 /= L1; a1 /= L1; a2 /= L1;
+  R t;
+  if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
+  if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
+  if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
+  return cube_vol(d / L1 + R(0.5), a0, a1, a2);
+}
+
+// ELVIRA (Pilliod and Puckett, "Second-order accurate volume-of-fluid
+// algorithms for tracking material interfaces", J. Comput. Phys. 2004) in
+// three dimensions, for a cell whose height columns are open: along each
+// axis a the fill levels of the 3x3x3 block summed over 3 cells give column
+// heights h(b, c); backward, central and forward differences of h in the two
+// other axes give nine candidate normals (s_a, -dh/db, -dh/dc), s_a the gas
+// side of a (sign of the Parker-Youngs component npy_a).  Each candidate's
+// plane through the cell's own fill is continued through the block; the
+// candidate whose volume fractions match the block's fill levels best (least
+// squares over the cells that are not walls, summed z-major; first minimum in
+// the order a, b-difference, c-difference) gives n and d.  A wall takes the
+// cell's own fill level in the column sums.  Out of line: rare, and kept out
+// of the registers of the common path.
+template <class R>
+__device__ __noinline__ void elvira_plane(const Par& p, const uint8_t* __restrict__ flags,
+                                          const R* __restrict__ phin, int x, int y, int z, R phic, R npy0, R npy1,
+                                          R npy2, R* nout, R* dout) {
+  R blk[27];
+  unsigned wallm = 0u;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int k = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+        uint8_t kj;
+        const R v = fill_at<R>(p, flags, phin, nbr(p, x, y, z, dx, dy, dz), kj);
+        if (kj == WALL) wallm |= 1u << k;
+        blk[k] = kj == WALL ? phic : v;
+      }
+  const R npy[3] = {npy0, npy1, npy2};
+  R best = R(1e30);
+  for (int a = 0; a < 3; ++a) {
+    const int s = npy[a] > R(0) ? 1 : -1;
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    R h[9];
+    for (int ib = -1; ib <= 1; ++ib)
+      for (int ic = -1; ic <= 1; ++ic) {
+        R sum = R(0);
+        for (int k = -1; k <= 1; ++k) {
+          int o[3];
+          o[a] = k; o[b] = ib; o[c] = ic;
+          sum += blk[(o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1)];
+        }
+        h[(ib + 1) * 3 + (ic + 1)] = sum;
+      }
+    const R db[3] = {h[4] - h[1], R(0.5) * (h[7] - h[1]), h[7] - h[4]};
+    const R dc[3] = {h[4] - h[3], R(0.5) * (h[5] - h[3]), h[5] - h[4]};
+    for (int kb = 0; kb < 3; ++kb)
+      for (int kc = 0; kc < 3; ++kc) {
+        R v[3];
+        v[a] = R(s); v[b] = -db[kb]; v[c] = -dc[kc];
+        const R len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const R m0 = v[0] / len, m1 = v[1] / len, m2 = v[2] / len;
+        const R dd = plic_offset<R>(m0, m1, m2, phic);
+        R err = R(0);
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int k = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+              if (k == 13 || (wallm & (1u << k))) continue;
+              const R e = plane_volume<R>(m0, m1, m2, dd - (m0 * R(dx) + m1 * R(dy) + m2 * R(dz))) - blk[k];
+              err += e * e;
+            }
+        if (err < best) {
+          best = err;
+          nout[0] = m0; nout[1] = m1; nout[2] = m2;
+          *dout = dd;
+        }
+      }
+  }
+}
+
 // MODE 0: any cell (plain offsets when every stencil cell is inside the
 // lattice, else the general neighbour rule); 1: the caller knows every cell
 // within 3 is inside; 2: a lattice without periodic axes (a stencil cell past
 // a face is a wall: a bounds test per cell instead of the neighbour rule).
-// SIG: the instance for surface tension (curvature); without it kappa stays 0
-template <class R, int MODE = 0, bool SIG = false>
+// SIG: the instance for surface tension (curvature); without it kappa stays 0.
+// ELV: the instance with the ELVIRA normal where the columns are open.
+template <class R, int MODE = 0, bool SIG = false, bool ELV = false>
 __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict__ flags,
                                          const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
   R (&n)[3] = G.n;
@@ -807,6 +895,12 @@ __device__ __forceinline__ void geometry(const Par& p, const uint8_t* __restrict
     }
   } else {
     if (SIG && p.sigma != 0.0) kap = curvature_open<R>(p, flags, phin, x, y, z, n[0], n[1], n[2], a);
+    if constexpr (ELV) {
+      R ne[3];
+      elvira_plane<R>(p, flags, phin, x, y, z, phic, n[0], n[1], n[2], ne, &d);
+      n[0] = ne[0]; n[1] = ne[1]; n[2] = ne[2];
+      return;
+    }
     if constexpr (sizeof(R) == 4) {
       const R il = rsqrtf(nn);
       n[0] *= il; n[1] *= il; n[2] *= il;

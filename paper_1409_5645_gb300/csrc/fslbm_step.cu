@@ -363,10 +363,10 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
 // the geometry of cells within 3 of a face (bounded: no periodic axis);
 // inlined, so that its Geo stays in registers (an out-of-line call measured
 // slower: the edge warps set the kernel's tail)
-template <class R, bool BOUNDED, bool SIG>
+template <class R, bool BOUNDED, bool SIG, bool ELV>
 __device__ __forceinline__ void geometry_edge(const Par& p, const uint8_t* __restrict__ flags,
                                            const R* __restrict__ phin, int x, int y, int z, R phic, Geo<R>& G) {
-  geometry<R, BOUNDED ? 2 : 0, SIG>(p, flags, phin, x, y, z, phic, G);
+  geometry<R, BOUNDED ? 2 : 0, SIG, ELV>(p, flags, phin, x, y, z, phic, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -374,8 +374,9 @@ __device__ __forceinline__ void geometry_edge(const Par& p, const uint8_t* __res
 // from phi(t) (Sec. 2.2, Sec. 5), one thread per cell, into v.geo; kept apart
 // from k_iface so that each kernel holds fewer registers and less code.
 // ---------------------------------------------------------------------------
-// SIG: the instance that also computes the curvature (surface tension)
-template <int P, bool SIG>
+// SIG: the instance that also computes the curvature (surface tension); ELV:
+// the one with the ELVIRA normal where the height columns are open
+template <int P, bool SIG, bool ELV>
 __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
   pdl_begin();
   using R = typename Form<P>::R;
@@ -392,13 +393,13 @@ __global__ void __launch_bounds__(128) k_geom(Par p, View<P> v) {
     R o[5];
     if (in3) {
       Geo<R> G;  // (in registers)
-      geometry<R, 1, SIG>(p, v.flags, v.phin, x, y, z, phic, G);
+      geometry<R, 1, SIG, ELV>(p, v.flags, v.phin, x, y, z, phic, G);
       o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
       o[3] = G.d; o[4] = G.kap;
     } else {
       Geo<R> G;
-      if (!p.px && !p.py && !p.pz) geometry_edge<R, true, SIG>(p, v.flags, v.phin, x, y, z, phic, G);
-      else geometry_edge<R, false, SIG>(p, v.flags, v.phin, x, y, z, phic, G);
+      if (!p.px && !p.py && !p.pz) geometry_edge<R, true, SIG, ELV>(p, v.flags, v.phin, x, y, z, phic, G);
+      else geometry_edge<R, false, SIG, ELV>(p, v.flags, v.phin, x, y, z, phic, G);
       o[0] = G.ok ? G.n[0] : R(0); o[1] = G.ok ? G.n[1] : R(0); o[2] = G.ok ? G.n[2] : R(0);
       o[3] = G.d; o[4] = G.kap;
     }
@@ -480,7 +481,9 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
     return 1;
   if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
   if ((p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc) &&
-      launch_k(p.sigma != 0.0 ? k_geom<P, true> : k_geom<P, false>, iface_blocks, 128, 0, st, p, v))
+      launch_k(p.elvira ? (p.sigma != 0.0 ? k_geom<P, true, true> : k_geom<P, false, true>)
+                        : (p.sigma != 0.0 ? k_geom<P, true, false> : k_geom<P, false, false>),
+               iface_blocks, 128, 0, st, p, v))
     return 1;
   // the interface partials follow the bulk warps' ones
   if (launch_k((p.stress || p.ub_extrap || p.recon_nc) ? k_iface<P, true> : k_iface<P, false>, iface_blocks, 128, 0, st, p, v,

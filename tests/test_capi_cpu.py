@@ -66,7 +66,7 @@ def test_default_params_and_argument_checks(built_lib):
     bad.precision = fslbm.F64
     # options outside their ranges, each on its own (checked before any device work)
     for field, value in (("stress", 3), ("ub_extrap", 2), ("recon_nc", -1), ("excess_split", 2),
-                         ("bulk_loads", 9), ("rule", 2)):
+                         ("bulk_loads", 9), ("rule", 2), ("elvira", 2)):
         old = getattr(bad, field)
         setattr(bad, field, value)
         assert L.fslbm_create_ex(ctypes.byref(bad), ctypes.byref(h)) == -1, field

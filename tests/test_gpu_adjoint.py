@@ -153,14 +153,77 @@ def test_autograd_function_matches_c_interface():
     assert np.allclose(phi0.grad.cpu().numpy(), dphi, rtol=1e-12, atol=0)
 
 
-def test_adjoint_refuses_conversions_and_unsupported_settings():
-    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4)
-    g = fslbm.Lattice.from_case(c)
-    with pytest.raises(fslbm.FslbmError) as e:
-        g.adjoint_forward(200, 50)
-    assert e.value.code == -4
-    c2 = cases.adjoint_film(nz=48, h=30.0, compressible=1)
-    g2 = fslbm.Lattice.from_case(c2)
-    with pytest.raises(fslbm.FslbmError) as e:
-        g2.adjoint_forward(10, 5)
-    assert e.value.code == -1
+def test_adjoint_refuses_unsupported_settings():
+    for kw in (dict(compressible=1), dict(excess_split=1), dict(sigma=1e-4)):
+        c2 = cases.adjoint_film(nz=48, h=30.0, **kw)
+        g2 = fslbm.Lattice.from_case(c2)
+        with pytest.raises(fslbm.FslbmError) as e:
+            g2.adjoint_forward(10, 5)
+        assert e.value.code == -1
+
+
+def _dam(rule=1):
+    """Dam-break miniature whose cells fill, empty and appear every few
+    steps inside the window (equal excess split)."""
+    return cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=rule)
+
+
+def _tlm_dam(case, steps, **seed):
+    o = Oracle.from_case(case, dual=True)
+    o.seed(**seed)
+    conv = 0
+    for _ in range(steps):
+        o.step(1)
+        conv += sum(o.counters()[0])
+    fl = o.flags()
+    return o.get(VEL, tangent=True)[fl == 2, 0].mean(), conv
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_adjoint_through_conversions_matches_oracle_tangent_linear(rule):
+    """Conversions replayed: on the dam-break miniature (200 steps, several
+    checkpoint segments, conversions in every segment) the FP64 adjoint
+    equals the oracle's FP64 tangent-linear model, which differentiates the
+    conversion stage itself (new-cell equilibria, excess split), in nu, g and
+    the initial fill levels."""
+    c = _dam(rule)
+    steps = 200
+    J, dnu, dg, dphi, _ = _grad_gpu(c, steps, K=60)
+    o = Oracle.from_case(c)
+    o.step(steps)
+    assert J == pytest.approx(o.get(VEL)[o.flags() == 2, 0].mean(), rel=1e-10)
+    t_tau, conv = _tlm_dam(c, steps, dtau=1.0)
+    print(f"rule {rule}: dJ/dnu adjoint {dnu:.10e} tangent {3.0 * t_tau:.10e}; conversions {conv}")
+    assert conv > 20
+    assert dnu == pytest.approx(3.0 * t_tau, rel=1e-7)
+    for a in (0, 2):
+        e = [0.0, 0.0, 0.0]
+        e[a] = 1.0
+        t_g, _ = _tlm_dam(c, steps, dg=e)
+        assert dg[a] == pytest.approx(t_g, rel=1e-7, abs=1e-9 * abs(dg).max())
+    ifc = np.where(c["flags"] == cases.INTERFACE)[0]
+    scale = np.abs(dphi[ifc]).max()
+    for k in ifc[[0, 7, 19, len(ifc) // 2, len(ifc) - 3]]:
+        e = np.zeros(c.N)
+        e[k] = 1.0
+        t_phi, _ = _tlm_dam(c, steps, dphi=e)
+        assert dphi[k] == pytest.approx(t_phi, rel=1e-6, abs=1e-8 * scale)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_adjoint_through_conversions_central_differences(rule):
+    """The same gradient against central differences of the CUDA forward
+    path (relative steps 1e-6 in nu and g; the discrete decisions stay put
+    within them): 1e-4 relative."""
+    c = _dam(rule)
+    steps = 200
+    J, dnu, dg, dphi, _ = _grad_gpu(c, steps, K=60)
+    nu = (c["params"]["tau"] - 0.5) / 3
+    h = 1e-6 * nu
+    fd = (_J_gpu(c, steps, tau=0.5 + 3 * (nu + h)) - _J_gpu(c, steps, tau=0.5 + 3 * (nu - h))) / (2 * h)
+    print(f"rule {rule}: dJ/dnu adjoint {dnu:.10e} central difference {fd:.10e}")
+    assert dnu == pytest.approx(fd, rel=1e-4)
+    gz = c["params"]["g"][2]
+    h = 1e-6 * abs(gz)
+    fd = (_J_gpu(c, steps, g=(0.0, 0.0, gz + h)) - _J_gpu(c, steps, g=(0.0, 0.0, gz - h))) / (2 * h)
+    assert dg[2] == pytest.approx(fd, rel=1e-4)

@@ -136,3 +136,25 @@ def test_launches_per_step():
         g = fslbm.Lattice(film["dims"], dict(film["params"], rule=rule, freeze=freeze))
         assert g.launches_per_step == n, (rule, freeze, g.launches_per_step)
         g.close()
+
+
+def test_dam_break_parity_elvira():
+    """The ELVIRA normal where the height columns are open (Sec. 5's
+    higher-order reconstruction; walls and the column's corners leave many
+    columns open): FSL dam break with conversions, every step against the
+    oracle."""
+    c = cases.dam_break(nx=24, ny=8, nz=16, col_x=8, col_z=12, tau=0.6, g=2e-4, rule=1, elvira=1)
+    _, _, conv = run_parity(c, 150, every=1)
+    assert conv[0] > 0
+
+
+def test_plane_parity_elvira_open_columns():
+    """A frozen plane 2.4 cells above a wall (every surface column open),
+    FSL with ELVIRA: parity with the oracle, whose ELVIRA plane is exact
+    there (the oracle pins)."""
+    import sys
+    sys.path.insert(0, __file__.rsplit("/", 1)[0])
+    from test_oracle_pins import _plane_case
+    case, _, _, _ = _plane_case(0.17, -0.11, 2.45, elvira=1)
+    case["params"]["rule"] = 1
+    run_parity(case, 60, every=5, check_mass=False)
