@@ -256,6 +256,23 @@ def ncu_traffic(form):
     return float(val.group(1))
 
 
+def fp64_counts_per_cell():
+    """(FP64 operations with FMA = 2, FP64 instructions) per liquid-cell
+    update of the FP64 bulk kernel, from the committed ncu instruction counts;
+    None if absent or taken on other kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_bulk_dam_break_f64.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    fl = re.search(r"fp64_flops_per_liquid_cell:\s*([0-9.eE+]+)", text)
+    ins = re.search(r"fp64_instructions_per_liquid_cell:\s*([0-9.eE+]+)", text)
+    if not sha or not fl or not ins or sha.group(1) != kernel_source_sha():
+        return None
+    return float(fl.group(1)), float(ins.group(1))
+
+
 # ---------------------------------------------------------------------------
 # one precision form
 # ---------------------------------------------------------------------------
@@ -353,6 +370,41 @@ def adjoint_run(form, steps=4000, K=200):
     return {"steps": steps, "checkpoint_every": K, "fwd_ms_per_step": round(fwd, 5),
             "adj_ms_per_step": round(adj, 5), "adj_over_fwd": round(adj / fwd, 3) if fwd > 0 else None,
             "peak_bytes": int(peak)}
+
+
+def adjoint_large(form, steps=400, K=40, dims=(256, 128, 128), peak=None):
+    """Differentiation at scale: the dam break at 256 x 128 x 128 (4.2 M
+    cells; cells fill, empty and appear inside the window, replayed by the
+    adjoint), objective the mean x-velocity of the interface cells after
+    `steps` steps, checkpoints every K steps.  Reverse-step throughput over
+    the fluid cells, and its bytes: per fluid cell k_adj_local reads the saved
+    populations (19 s) and the incoming adjoint (19 x 8 B) and writes the
+    outgoing adjoint and the pulled-population adjoints (2 x 19 x 8 B), and
+    k_adj_gather reads the latter and updates the former (3 x 19 x 8 B): 19 (s + 48) B."""
+    import numpy as np
+    from paper_1409_5645_gb300 import cases, fslbm
+    nx, ny, nz = dims
+    c = cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=nx // 4, col_z=nz * 3 // 4, tau=TAU, magic=MAGIC)
+    lat = fslbm.Lattice.from_case(c, precision=form)
+    fl = c["flags"]
+    nfluid = int(np.count_nonzero((fl == 1) | (fl == 2)))
+    try:
+        lat.adjoint_forward(steps, K)
+        lat.adjoint_backward()
+    except fslbm.FslbmError as e:
+        lat.close()
+        return {"steps": steps, "checkpoint_every": K, "error": str(e)}
+    fwd, adj, pk = lat.adjoint_stats()
+    lat.close()
+    s = STORE_BYTES[form]
+    gbs = nfluid * 19 * (s + 48) / (adj / 1e3) / 1e9
+    out = {"dims": list(dims), "steps": steps, "checkpoint_every": K, "fwd_ms_per_step": round(fwd, 5),
+           "adj_ms_per_step": round(adj, 5), "adj_over_fwd": round(adj / fwd, 3) if fwd > 0 else None,
+           "adj_mlups": round(c.N / (adj / 1e3) / 1e6, 1), "fluid_cells": nfluid,
+           "adj_alg_gbs": round(gbs, 1), "peak_bytes": int(pk)}
+    if peak:
+        out["adj_hbm_frac"] = round(gbs / peak, 4)
+    return out
 
 
 def e2e_run(case, form, steps, local_rank):
@@ -482,7 +534,8 @@ def main():
     # the other precision forms on the same workload
     other = {}
     for f in forms[1:]:
-        r = run_form(case, f, args.form_steps, args.warmup, ws, rank, local_rank)
+        r = run_form(case, f, args.form_steps, args.warmup, ws, rank, local_rank,
+                     spinup=0 if args.load_state else args.spinup)
         msx = max_over_ranks(r["ms"], ws, torch.device("cuda", local_rank))
         sb = STORE_BYTES[f]
         bulk = r["n_liquid"] * 2 * 19 * sb + N
@@ -491,6 +544,24 @@ def main():
                     "bulk_gbs": round(bulk / (r["groups_ms"][0] / 1e3) / 1e9, 1),
                     "bulk_frac": round(bulk / (r["groups_ms"][0] / 1e3) / 1e9 / peak, 4),
                     "kernel_ms_per_step": [round(x, 5) for x in r["groups_ms"]]}
+        if f == "f64":
+            # the FP64 bulk kernel against the measured FP64 arithmetic rate:
+            # its FP64 operations per liquid-cell update from the committed ncu
+            # count (instructions of the same kernel source)
+            from paper_1409_5645_gb300 import fslbm
+            rate = fslbm.fp64_rate()
+            cnt = fp64_counts_per_cell()
+            alu = {"bound": "alu", "peak": round(rate, 3), "unit": "TFLOP/s",
+                   "peak_kind": "measured (dependent FMA chains on every SM)"}
+            if cnt:
+                t = r["groups_ms"][0] / 1e3
+                ach = cnt[0] * r["n_liquid"] / t / 1e12
+                # the FP64 pipe issues one FMA, add or multiply per slot: the
+                # instruction rate against the measured FMA instruction rate
+                ins = cnt[1] * r["n_liquid"] / t / 1e12
+                alu.update(achieved=round(ach, 3), frac=round(ach / rate, 4), flops_per_liquid_cell=cnt[0],
+                           instr_frac=round(ins / (rate / 2.0), 4), instructions_per_liquid_cell=cnt[1])
+            other[f]["bulk_alu"] = alu
     # the configuration as written (tau = 0.51, Lambda = 3/16): from its
     # initial state for the steps it runs stably (a non-finite density
     # appears between 3500 and 9000 steps)
@@ -524,7 +595,8 @@ def main():
         # FP32 form is timed on the first 1000 steps)
         line["adjoint"] = {"workload": "film 8x4x64 depth 40, checkpoints with recompute",
                            "objective": "mean x-velocity of interface cells",
-                           "f64": adjoint_run("f64", 4000, 200), "f32": adjoint_run("f32", 1000, 100)}
+                           "f64": adjoint_run("f64", 4000, 200), "f32": adjoint_run("f32", 1000, 100),
+                           "large": {f: adjoint_large(f, peak=peak) for f in ("f32", "f64")}}
     # the oracle on the host cores (rank 0, N = 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, st, el = oracle_rate((128, 64, 64), (32, 48), budget_s=12.0, tau=args.tau, magic=args.magic)

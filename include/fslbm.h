@@ -392,6 +392,14 @@ int fslbm_launches_per_step(const fslbm_t *h);
  * in the paper. */
 int fslbm_check_grid_barrier(int expire, void *stream);
 
+/* The current device's FP64 arithmetic rate in TFLOP/s (a fused multiply-add
+ * counts two): chains of dependent FMAs on every SM, timed with CUDA events
+ * on `stream` (NULL = legacy default), best of three after a warm-up run.
+ * The ceiling of the FP64 form, whose stream-collide is bound by arithmetic
+ * on GB300.  Synchronises the stream.  An implementation property with no
+ * counterpart in the paper. */
+int fslbm_fp64_rate(double *tflops, void *stream);
+
 /* Bytes of device memory held by the handle. */
 size_t fslbm_device_bytes(const fslbm_t *h);
 

@@ -60,6 +60,8 @@ struct AdjointState {
   double* seg_m = nullptr;
   void* seg_phi = nullptr;
   uint8_t* seg_flags = nullptr;
+  int* flist = nullptr;  // [2][2N + 2]: liquid and interface cells of a flag field, their counts
+                         // (double buffer: the fields before and after the step being reversed)
   double* Mh = nullptr;  // conversion reverse: final-mass and density adjoints, new-cell means
   double* rh = nullptr;
   double* ngb = nullptr;
@@ -97,7 +99,21 @@ struct AdjView {
   double* mbar_out;
   double* phibar_out;
   double* theta;
+  const int* flist;  // the liquid (or interface) cells of `flags`, nfl of them
+  const int* nfl;
 };
+
+// warp-level sums of th added to out (one atomic per warp and component; all
+// 32 lanes call it)
+__device__ __forceinline__ void warp_add(double (&th)[5], double* out) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double v = th[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out + k, v);
+  }
+}
 
 // d e_q^+ / d u for rho_0 = 1: w_q (9 (c.u) c - 3 u); zero for the linear equilibrium
 __device__ __forceinline__ void deplus_du(const Par& p, int q, double ux, double uy, double uz, double g,
@@ -262,38 +278,113 @@ __device__ void plane_section(const double (&n)[3], double d, double& A, double 
     for (int j = 0; j < 3; ++j) c[j] /= A;
 }
 
-template <int P>
+// The liquid and the interface cells of a flag field, in two lists
+// (warp-aggregated appends; the order does not matter: each cell's reverse
+// step is its own).  The adjoint kernels run over them only: the entries of
+// other cells are never read.
+__device__ __forceinline__ void list_append(bool pred, int i, int* list, int* count) {
+  const unsigned bal = __ballot_sync(0xffffffffu, pred);
+  if (!bal) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(bal));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) list[base + __popc(bal & ((1u << lane) - 1u))] = i;
+}
+__global__ void __launch_bounds__(256) k_adj_lists(Par p, const uint8_t* __restrict__ flags, int* __restrict__ liq,
+                                                   int* __restrict__ ifc, int* __restrict__ count) {
+  for (long long i0 = blockIdx.x * (long long)blockDim.x; i0 < p.N; i0 += (long long)gridDim.x * blockDim.x) {
+    const long long i = i0 + threadIdx.x;
+    const uint8_t k = i < p.N ? (flags[i] & KIND) : (uint8_t)GAS;
+    list_append(k == LIQ, (int)i, liq, count);
+    list_append(k == IFC, (int)i, ifc, count + 1);
+  }
+}
+
+// Reverse of the plane fit of a cell whose height columns are open: d =
+// d(n, phi_c) with V(n, d) = phi_c (phi_c kept in [1e-9, 1 - 1e-9]), n = -g/|g|
+// with g the Parker-Youngs gradient of the fill levels around the cell (a
+// wall takes phi_c).  dbar, nbar: adjoints of d and of the unit normal.  Adds
+// the neighbours' fill-level adjoints to phibar (atomics) and returns the
+// cell's own.  Out of line: rare, and its arrays stay out of the main frame.
+template <class R>
+__device__ __noinline__ double plane_fit_adjoint(const Par& p, const uint8_t* __restrict__ flags,
+                                                 const R* __restrict__ phi, double* phibar, int x, int y, int z,
+                                                 double phic, double n0, double n1, double n2, double d,
+                                                 double dbar, const double (&nb)[3]) {
+  const double nh[3] = {n0, n1, n2};
+  double nbar[3] = {nb[0], nb[1], nb[2]};
+  double own = 0.0;
+  double A, cen[3];
+  plane_section(nh, d, A, cen);
+  if (A > 0.0 && phic > 1e-9 && phic < 1.0 - 1e-9) own += dbar / A;
+  for (int k = 0; k < 3; ++k) nbar[k] += dbar * cen[k];
+  double gr[3] = {0.0, 0.0, 0.0};
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy && !dz) continue;
+        const uint8_t kj = kind_at(flags, nbr(p, x, y, z, dx, dy, dz));
+        double pj = 0.0;
+        if (kj == LIQ) pj = 1.0;
+        else if (kj == IFC || (kj == GAS && p.freeze)) pj = (double)phi[nbr(p, x, y, z, dx, dy, dz)];
+        else if (kj == WALL) pj = phic;
+        const int ax_ = dx < 0 ? -dx : dx, ay_ = dy < 0 ? -dy : dy, az_ = dz < 0 ? -dz : dz;
+        gr[0] += dx * (2 - ay_) * (2 - az_) * pj;
+        gr[1] += dy * (2 - az_) * (2 - ax_) * pj;
+        gr[2] += dz * (2 - ax_) * (2 - ay_) * pj;
+      }
+  const double gl = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+  const double nd = nbar[0] * nh[0] + nbar[1] * nh[1] + nbar[2] * nh[2];
+  double gb[3];  // adjoint of g
+  for (int k = 0; k < 3; ++k) gb[k] = -(nbar[k] - nd * nh[k]) / gl;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy && !dz) continue;
+        const long long j = nbr(p, x, y, z, dx, dy, dz);
+        const uint8_t kj = kind_at(flags, j);
+        const int ax_ = dx < 0 ? -dx : dx, ay_ = dy < 0 ? -dy : dy, az_ = dz < 0 ? -dz : dz;
+        const double val = gb[0] * (dx * (2 - ay_) * (2 - az_)) + gb[1] * (dy * (2 - az_) * (2 - ax_)) +
+                           gb[2] * (dz * (2 - ax_) * (2 - ay_));
+        if (val == 0.0) continue;
+        if (kj == WALL) own += val;
+        else if (kj == IFC || (kj == GAS && p.freeze)) atomicAdd(phibar + j, val);
+      }
+  return own;
+}
+
+// IFCP: the instance for interface cells (gas links, mass exchange,
+// geometry); the other runs the liquid cells, whose code is a small part of
+// this one (a liquid cell never touches gas).
+template <int P, bool IFCP>
 __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
   using R = typename Form<P>::R;
   const size_t N = (size_t)p.N;
   double th[5] = {0, 0, 0, 0, 0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const uint8_t kc = a.flags[i] & KIND;
-    if (!is_fluid(kc)) {
-#pragma unroll
-      for (int q = 0; q < 19; ++q) { a.abar_out[q * N + i] = 0.0; a.Pb[q * N + i] = 0.0; }
-      a.mbar_out[i] = 0.0;
-      continue;
-    }
+  const int nf = *a.nfl;
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < nf; li += gridDim.x * blockDim.x) {
+    const long long i = a.flist[li];
+    const uint8_t kc = IFCP ? (uint8_t)IFC : (uint8_t)LIQ;
     int x, y, z;
     coords(p, i, x, y, z);
     double own[19], F[19], f[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) own[q] = ldq_full<P>(a.f, q * N + i, q);
     unsigned wallm = 0u, gasm = 0u;
-    long long src[19];
+    int src[19];
     F[0] = own[0];
-    src[0] = i;
+    src[0] = (int)i;
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
       long long s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
-      src[q] = s;
+      src[q] = (int)s;
       uint8_t ks = kind_at(a.flags, s);
       if (is_fluid(ks)) F[q] = ldq_full<P>(a.f, q * N + s, q);
       else if (ks == WALL) { wallm |= 1u << q; F[q] = 0.0; }
       else { gasm |= 1u << q; F[q] = 0.0; }
     }
+    if constexpr (!IFCP) gasm = 0u;  // (liquid cells have no gas neighbour)
 #pragma unroll
     for (int q = 0; q < 19; ++q) f[q] = F[q];
     // own moments at t (rho_0 = 1): rho_t = sum f~, u_t = sum c f~ - g/2
@@ -518,49 +609,9 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
           }
         }
     }
-    if (plic_used) {
-      // the plane fit: d = d(n, phi_c) with V(n, d) = phi_c (phi_c kept in
-      // [1e-9, 1 - 1e-9]), n = -g / |g| with g the Parker-Youngs gradient of
-      // the fill levels around the cell (a wall takes phi_c)
-      const double nh[3] = {(double)G.n[0], (double)G.n[1], (double)G.n[2]};
-      double A, cen[3];
-      plane_section(nh, (double)G.d, A, cen);
-      if (A > 0.0 && phic > 1e-9 && phic < 1.0 - 1e-9) phib_self += dbar / A;
-      for (int k = 0; k < 3; ++k) nbar[k] += dbar * cen[k];
-      double gr[3] = {0.0, 0.0, 0.0};
-      double ws[26][3];
-      long long js[26];
-      int no = 0;
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (!dx && !dy && !dz) continue;
-            const long long j = nbr(p, x, y, z, dx, dy, dz);
-            const uint8_t kj = kind_at(a.flags, j);
-            double pj = 0.0;
-            if (kj == LIQ) pj = 1.0;
-            else if (kj == IFC || (kj == GAS && p.freeze)) pj = (double)a.phi[j];
-            else if (kj == WALL) pj = phic;
-            const int ax_ = dx < 0 ? -dx : dx, ay_ = dy < 0 ? -dy : dy, az_ = dz < 0 ? -dz : dz;
-            ws[no][0] = dx * (2 - ay_) * (2 - az_);
-            ws[no][1] = dy * (2 - az_) * (2 - ax_);
-            ws[no][2] = dz * (2 - ax_) * (2 - ay_);
-            for (int k = 0; k < 3; ++k) gr[k] += ws[no][k] * pj;
-            js[no] = (kj == WALL) ? -2 : ((kj == IFC || (kj == GAS && p.freeze)) ? j : -1);
-            ++no;
-          }
-      const double gl = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-      const double nd = nbar[0] * nh[0] + nbar[1] * nh[1] + nbar[2] * nh[2];
-      double gb[3];  // adjoint of g (n = -g / |g|)
-      for (int k = 0; k < 3; ++k) gb[k] = -(nbar[k] - nd * nh[k]) / gl;
-      for (int o = 0; o < no; ++o) {
-        if (js[o] == -1) continue;
-        const double val = gb[0] * ws[o][0] + gb[1] * ws[o][1] + gb[2] * ws[o][2];
-        if (val == 0.0) continue;
-        if (js[o] == -2) phib_self += val;
-        else atomicAdd(a.phibar_out + js[o], val);
-      }
-    }
+    if (plic_used)
+      phib_self += plane_fit_adjoint(p, a.flags, a.phi, a.phibar_out, x, y, z, phic, (double)G.n[0],
+                                     (double)G.n[1], (double)G.n[2], (double)G.d, dbar, nbar);
     // own moments: rho_t = sum f~, u_t = sum c f~ - g/2
 #pragma unroll
     for (int q = 0; q < 19; ++q) ob[q] += rtb + cx(q) * utb[0] + cy(q) * utb[1] + cz(q) * utb[2];
@@ -574,17 +625,19 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
     }
     if (phib_self != 0.0) atomicAdd(a.phibar_out + i, phib_self);
   }
-  block_add(th, a.theta);
+  warp_add(th, a.theta);
 }
 
 // reverse of the pull: abar_q(y) += P_q(y + c_q) when y + c_q pulled from y
+// (over the liquid and the interface cells of the step: lists liq, ifc)
 template <int P>
 __global__ void k_adj_gather(Par p, const uint8_t* __restrict__ flags, const double* __restrict__ Pb,
-                             double* __restrict__ abar) {
+                             double* __restrict__ abar, const int* __restrict__ liq, const int* __restrict__ ifc,
+                             const int* __restrict__ cnt) {
   const size_t N = (size_t)p.N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (!is_fluid(flags[i] & KIND)) continue;
+  const int nl = cnt[0], ni = cnt[1];
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < nl + ni; li += gridDim.x * blockDim.x) {
+    const long long i = li < nl ? liq[li] : ifc[li - nl];
     int x, y, z;
     coords(p, i, x, y, z);
 #pragma unroll
@@ -710,11 +763,12 @@ __global__ void __launch_bounds__(128) k_adj_init(Par p, const uint8_t* flags, c
 // Reverse of the conversions of one step, part 1 (see the file header).
 // flags0 / flags1: the flags before / after the step; f1, m1: the state after
 // it (post-collision populations, mass); abar, mbar, phibar: adjoints of that
-// state.  Writes Mh, rh (interface cells after the step) and, per new cell
-// from gas, ngb[4 j + 0..3] = (adjoint of mean rho, of mean u) / count.
+// state.  Writes Mh, rh (interface cells after the step, the list ifc1 of
+// n1 cells; the entries of other cells are not read) and, per new cell from
+// gas, ngb[4 j + 0..3] = (adjoint of mean rho, of mean u) / count.
 template <int P>
 __global__ void __launch_bounds__(128) k_adj_conv1(Par p, const uint8_t* __restrict__ flags0,
-                                                   const uint8_t* __restrict__ flags1,
+                                                   const int* __restrict__ ifc1, const int* __restrict__ n1p,
                                                    const typename Form<P>::S* __restrict__ f1,
                                                    const double* __restrict__ m1, const double* __restrict__ abar,
                                                    const double* __restrict__ mbar, const double* __restrict__ phibar,
@@ -722,12 +776,10 @@ __global__ void __launch_bounds__(128) k_adj_conv1(Par p, const uint8_t* __restr
                                                    double* __restrict__ ngb, double* theta) {
   const size_t N = (size_t)p.N;
   double th[5] = {0, 0, 0, 0, 0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const uint8_t k0 = flags0[i] & KIND, k1 = flags1[i] & KIND;
-    Mh[i] = 0.0;
-    rh[i] = 0.0;
-    if (k1 != IFC) continue;
+  const int n1 = *n1p;
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < n1; li += gridDim.x * blockDim.x) {
+    const long long i = ifc1[li];
+    const uint8_t k0 = flags0[i] & KIND;
     double r = 0.0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) r += ldq_full<P>(f1, q * N + i, q);
@@ -795,25 +847,32 @@ __global__ void __launch_bounds__(128) k_adj_conv1(Par p, const uint8_t* __restr
     ngb[4 * i + 2] = ubr[1] / cnt;
     ngb[4 * i + 3] = ubr[2] / cnt;
   }
-  block_add(th, theta);
+  warp_add(th, theta);
 }
 
-// Part 2, per fluid cell of the old flags: abar (in place) becomes the adjoint
-// of the step's post-collision populations before the conversions, mbar that
-// of the exchanged mass m + dm, phibar zero (the fill levels' adjoints are in
-// Mh / rh).
+// Part 2, per fluid cell of the old flags that the conversions touch: abar
+// (in place) becomes the adjoint of the step's post-collision populations
+// before the conversions, mbar that of the exchanged mass m + dm, phibar zero
+// (the fill levels' adjoints are in Mh / rh).  A cell liquid before and after
+// the step is left as it is: no new cell from gas can neighbour it (it had
+// no gas neighbour) and its populations and density pass through.  So the
+// cells are the interface cells before the step (list ifc0) and the new
+// interface cells from liquid (liquid cells of the list ifc1).
 template <int P>
 __global__ void __launch_bounds__(128) k_adj_conv2(Par p, const uint8_t* __restrict__ flags0,
                                                    const uint8_t* __restrict__ flags1,
+                                                   const int* __restrict__ ifc0, const int* __restrict__ n0p,
+                                                   const int* __restrict__ ifc1, const int* __restrict__ n1p,
                                                    const double* __restrict__ Mh, const double* __restrict__ rh,
                                                    const double* __restrict__ ngb, double* __restrict__ abar,
                                                    double* __restrict__ mbar, double* __restrict__ phibar) {
   const size_t N = (size_t)p.N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.N;
-       i += (long long)gridDim.x * blockDim.x) {
+  const int n0 = *n0p, n1 = *n1p;
+  for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < n0 + n1; li += gridDim.x * blockDim.x) {
+    const long long i = li < n0 ? ifc0[li] : ifc1[li - n0];
     const uint8_t k0 = flags0[i] & KIND, k1 = flags1[i] & KIND;
-    phibar[i] = 0.0;
-    if (!is_fluid(k0)) continue;
+    if (li >= n0 && k0 != LIQ) continue;  // (interface before and after: done from ifc0)
+    if (k0 == IFC) phibar[i] = 0.0;
     int x, y, z;
     coords(p, i, x, y, z);
     double add = 0.0, mb = 0.0;
@@ -855,22 +914,46 @@ __global__ void __launch_bounds__(128) k_adj_conv2(Par p, const uint8_t* __restr
   }
 }
 
-template <int P>
-static void launch_conv(const Par& p, const uint8_t* flags0, const uint8_t* flags1,
-                        const typename Form<P>::S* f1, const double* m1, double* abar, double* mbar,
-                        double* phibar, double* Mh, double* rh, double* ngb, double* theta, cudaStream_t st) {
-  int blocks = (int)((p.N + 127) / 128);
+// the liquid and interface cells of a flag field (see k_adj_lists)
+struct CellLists {
+  int* liq;
+  int* ifc;
+  int* cnt;  // [0] liquid, [1] interface
+};
+static void build_lists(const Par& p, const uint8_t* flags, const CellLists& L, cudaStream_t st) {
+  int blocks = (int)((p.N + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_adj_conv1<P><<<blocks, 128, 0, st>>>(p, flags0, flags1, f1, m1, abar, mbar, phibar, Mh, rh, ngb, theta);
-  k_adj_conv2<P><<<blocks, 128, 0, st>>>(p, flags0, flags1, Mh, rh, ngb, abar, mbar, phibar);
+  cudaMemsetAsync(L.cnt, 0, 2 * sizeof(int), st);
+  k_adj_lists<<<blocks, 256, 0, st>>>(p, flags, L.liq, L.ifc, L.cnt);
 }
 
 template <int P>
-static void launch_local(const Par& p, const AdjView<P>& a, cudaStream_t st) {
-  int blocks = (int)((p.N + 127) / 128);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_adj_local<P><<<blocks, 128, 0, st>>>(p, a);
-  k_adj_gather<P><<<blocks, 128, 0, st>>>(p, a.flags, a.Pb, a.abar_out);
+static void launch_conv(const Par& p, const uint8_t* flags0, const uint8_t* flags1, const CellLists& L0,
+                        const CellLists& L1, const typename Form<P>::S* f1, const double* m1, double* abar,
+                        double* mbar, double* phibar, double* Mh, double* rh, double* ngb, double* theta,
+                        cudaStream_t st) {
+  int blocks = (int)((p.N / 8 + 127) / 128);  // (over the interface lists: a small share of the cells)
+  if (blocks < 152) blocks = 152;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_adj_conv1<P><<<blocks, 128, 0, st>>>(p, flags0, L1.ifc, L1.cnt + 1, f1, m1, abar, mbar, phibar, Mh, rh, ngb,
+                                         theta);
+  k_adj_conv2<P><<<blocks, 128, 0, st>>>(p, flags0, flags1, L0.ifc, L0.cnt + 1, L1.ifc, L1.cnt + 1, Mh, rh, ngb,
+                                         abar, mbar, phibar);
+}
+
+template <int P>
+static void launch_local(const Par& p, AdjView<P> a, const CellLists& L0, cudaStream_t st) {
+  int lb = (int)((p.N + 127) / 128);
+  if (lb > 152 * 8) lb = 152 * 8;
+  a.flist = L0.liq;
+  a.nfl = L0.cnt;
+  k_adj_local<P, false><<<lb, 128, 0, st>>>(p, a);
+  a.flist = L0.ifc;
+  a.nfl = L0.cnt + 1;
+  k_adj_local<P, true><<<lb, 128, 0, st>>>(p, a);
+  int gb = (int)((p.N + 127) / 128);
+  if (gb > 152 * 16) gb = 152 * 16;
+  k_adj_gather<P><<<gb, 128, 0, st>>>(p, a.flags, a.Pb, a.abar_out, L0.liq, L0.ifc, L0.cnt);
 }
 
 }  // namespace fsl
@@ -887,7 +970,7 @@ void fslbm_free_adjoint(fslbm* h) {
   if (!h || !h->adj) return;
   AdjointState* A = h->adj;
   void* ptrs[] = {A->ck_f, A->ck_m, A->ck_phi, A->ck_flags, A->seg_f, A->seg_m, A->seg_phi, A->seg_flags,
-                  A->Mh, A->rh, A->ngb, A->abar[0], A->abar[1], A->P, A->mbar[0], A->mbar[1], A->phibar[0],
+                  A->Mh, A->rh, A->ngb, A->flist, A->abar[0], A->abar[1], A->P, A->mbar[0], A->mbar[1], A->phibar[0],
                   A->phibar[1], A->theta, A->red, A->dphi0};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -1031,6 +1114,15 @@ static int backward_t(fslbm* h) {
   k_obj_seed<P><<<blocks, 256, 0, st>>>(h->par, h->flags, (const S*)cur_f(h), (const R*)cur_phi(h), A->objective,
                                         norm, A->abar[0], A->phibar[0], A->mbar[0]);
   int cur = 0;
+  // cell lists of the flags before (L[lb ^ 1]) and after (L[lb]) the step
+  // being reversed; those after the last step from the final flags
+  CellLists L[2];
+  for (int b = 0; b < 2; ++b) {
+    int* base = A->flist + (size_t)b * (2 * N + 2);
+    L[b] = CellLists{base, base + N, base + 2 * N};
+  }
+  int lb = 0;
+  build_lists(h->par, h->flags, L[lb], st);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1049,8 +1141,9 @@ static int backward_t(fslbm* h) {
     }
     cudaEventRecord(e0, st);
     for (int k = n - 1; k >= 0; --k) {
+      build_lists(h->par, A->seg_flags + k * N, L[lb ^ 1], st);
       if (!h->par.freeze)  // the step's conversions, as the forward pass took them
-        launch_conv<P>(h->par, A->seg_flags + k * N, A->seg_flags + (k + 1) * N,
+        launch_conv<P>(h->par, A->seg_flags + k * N, A->seg_flags + (k + 1) * N, L[lb ^ 1], L[lb],
                        (const S*)((char*)A->seg_f + (k + 1) * A->fbytes), A->seg_m + (k + 1) * N, A->abar[cur],
                        A->mbar[cur], A->phibar[cur], A->Mh, A->rh, A->ngb, A->theta, st);
       AdjView<P> a;
@@ -1068,8 +1161,9 @@ static int backward_t(fslbm* h) {
       a.phibar_out = A->phibar[cur ^ 1];
       a.theta = A->theta;
       cudaMemsetAsync(a.phibar_out, 0, N * 8, st);
-      launch_local<P>(h->par, a, st);
+      launch_local<P>(h->par, a, L[lb ^ 1], st);
       cur ^= 1;
+      lb ^= 1;
     }
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
@@ -1102,6 +1196,7 @@ extern "C" int fslbm_adjoint_backward(fslbm_t* h, double* dJ_dnu, double dJ_dg[3
               amalloc(A, (void**)&A->seg_m, N * 8 * (A->K + 1)) &&
               amalloc(A, &A->seg_phi, A->rbytes * (A->K + 1)) &&
               amalloc(A, (void**)&A->seg_flags, N * (A->K + 1)) && amalloc(A, (void**)&A->Mh, N * 8) &&
+              amalloc(A, (void**)&A->flist, 2 * (2 * N + 2) * sizeof(int)) &&
               amalloc(A, (void**)&A->rh, N * 8) && amalloc(A, (void**)&A->ngb, N * 4 * 8);
     if (!ok) return adj_fail(h, FSLBM_ERR_OOM, "adjoint buffer allocation");
   }

@@ -63,6 +63,7 @@ def lib():
                                        C.POINTER(vp)]
             L.fslbm_create_ex.argtypes = [C.POINTER(Params), C.POINTER(vp)]
             L.fslbm_tau_of_viscosity.argtypes = [C.c_double, dp]
+            L.fslbm_fp64_rate.argtypes = [dp, vp]
             box = C.POINTER(C.c_int)
             L.fslbm_set_owned.argtypes = [vp, box, box]
             L.fslbm_halo_bytes.argtypes = [vp, box, box]
@@ -109,6 +110,15 @@ def tau_of_viscosity(nu: float) -> float:
     if rc:
         raise FslbmError(rc, f"viscosity {nu}")
     return tau.value
+
+
+def fp64_rate(stream=None) -> float:
+    """The current device's FP64 arithmetic rate, TFLOP/s (measured)."""
+    t = C.c_double()
+    rc = lib().fslbm_fp64_rate(C.byref(t), stream)
+    if rc:
+        raise FslbmError(rc, "fp64 rate")
+    return t.value
 
 
 def check_grid_barrier(expire: bool, stream=None) -> str:

@@ -76,14 +76,20 @@ def test_adjoint_matches_central_differences_film_4000_steps():
     assert dg[0] == pytest.approx(fd, rel=1e-4)
     ifc = np.where(c["flags"] == cases.INTERFACE)[0]
     k = ifc[9]
-    hp = 1e-4
-    cp, cm = cases.Case(c), cases.Case(c)
-    cp["phi"] = c["phi"].copy()
-    cm["phi"] = c["phi"].copy()
-    cp["phi"][k] += hp
-    cm["phi"][k] -= hp
-    fd = (_J_gpu(cp, steps) - _J_gpu(cm, steps)) / (2 * hp)
-    assert dphi[k] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(dphi[ifc]).max())
+
+    def cd(hp):
+        cp, cm = cases.Case(c), cases.Case(c)
+        cp["phi"] = c["phi"].copy()
+        cm["phi"] = c["phi"].copy()
+        cp["phi"][k] += hp
+        cm["phi"][k] -= hp
+        return (_J_gpu(cp, steps) - _J_gpu(cm, steps)) / (2 * hp)
+
+    # dJ/dphi0 is ~1e-10 against J ~ 1e-3: a step of 1e-4 keeps the rounding
+    # of J below 1e-5 of the difference, and Richardson extrapolation of the
+    # steps 2e-4 and 1e-4 removes the O(h^2) truncation
+    fd = (4.0 * cd(1e-4) - cd(2e-4)) / 3.0
+    assert dphi[k] == pytest.approx(fd, rel=1e-4)
     fwd_ms, adj_ms, peak = stats
     assert fwd_ms > 0 and adj_ms > 0 and peak > 0
 
@@ -105,6 +111,20 @@ def test_adjoint_nu_derivative_against_film_series():
     us = cases.film_profile(np.array([z]), 40.0, 1e-6, nu)[0]
     # steady limit of the same derivative: d u_s / d nu = -u_s / nu
     assert dser > -us / nu
+
+
+def test_adjoint_nu_derivative_steady_film_closed_form():
+    """At steady state the film's surface velocity is u_s = g h^2 / (2 nu)
+    (Sec. 4.3), so dJ/dnu = -J/nu exactly: a shallow film (depth 8, FSL, which
+    is exact for the aligned film) run for 20 diffusion times h^2/nu."""
+    c = cases.film(nx=4, ny=4, nz=12, h=8.0, gx=1e-6, rule=1, noise_amp=0.0)
+    nu = (c["params"]["tau"] - 0.5) / 3
+    steps = int(20 * 64 / nu)
+    J, dnu, _, _, _ = _grad_gpu(c, steps, K=500)
+    z = 8.0 - 0.5
+    us = cases.film_profile(np.array([z]), 8.0, 1e-6, nu)[0]
+    assert J == pytest.approx(us, rel=1e-6)
+    assert dnu == pytest.approx(-J / nu, rel=1e-6)
 
 
 def test_adjoint_keep_f0_equals_inversion_in_fp64():
@@ -130,11 +150,11 @@ def test_adjoint_fp32_against_fp64():
     e_g = abs(g32[0] - g64[0]) / abs(g64[0])
     e_phi = np.abs(p32[ifc] - p64[ifc]).max() / np.abs(p64[ifc]).max()
     print(f"FP32 adjoint vs FP64 (g = 1e-4 film): nu {e_nu:.2e}, g {e_g:.2e}, phi0 {e_phi:.2e}")
-    assert e_g < 1e-3
-    assert e_nu < 5e-2
-    # the per-cell fill gradients rest on differences of populations that FP32
-    # storage does not resolve on this film; the error is reported, not bounded
-    assert np.isfinite(p32[ifc]).all()
+    assert e_g < 1e-6
+    assert e_nu < 5e-3
+    # the per-cell fill gradients rest on small differences of populations;
+    # FP32 (storing f - w_q) carries them to a few percent of the largest
+    assert e_phi < 0.1
 
 
 def test_autograd_function_matches_c_interface():

@@ -158,3 +158,13 @@ def test_plane_parity_elvira_open_columns():
     case, _, _, _ = _plane_case(0.17, -0.11, 2.45, elvira=1)
     case["params"]["rule"] = 1
     run_parity(case, 60, every=5, check_mass=False)
+
+
+def test_fp64_rate_is_measured():
+    """The FP64 arithmetic ceiling the FP64 form is reported against: dependent
+    FMA chains on every SM give a rate of the order of the device's nominal
+    FP64 throughput (1.25 TFLOP/s for GB300)."""
+    from paper_1409_5645_gb300 import fslbm
+    r = fslbm.fp64_rate()
+    print(f"FP64 FMA rate {r:.3f} TFLOP/s")
+    assert 0.2 < r < 10.0
