@@ -71,8 +71,9 @@ def parse():
     ap.add_argument("--tau", type=float, default=TAU)
     ap.add_argument("--magic", type=float, default=MAGIC)
     ap.add_argument("--rule", type=int, default=1, help="1 = FSL, 0 = FSK")
-    ap.add_argument("--bulk-loads", default="plain", choices=["plain", "async", "tma"],
-                    help="how the FP32/FP16 bulk kernel reaches its pulled values")
+    ap.add_argument("--bulk-loads", default="pairs", choices=["plain", "async", "tma", "pairs"],
+                    help="how the FP32/FP16 bulk kernel reaches its pulled values (pairs: two cells per lane, "
+                         "packed FP32x2 collision; the fastest on GB300)")
     return ap.parse_args()
 
 
@@ -236,7 +237,7 @@ def hbm_peak():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("fslbm_step.cu", "fslbm_staged.cu", "fslbm_pull.cuh", "fslbm_dev.cuh"):
+    for f in ("fslbm_step.cu", "fslbm_staged.cu", "fslbm_pairs.cu", "fslbm_pull.cuh", "fslbm_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -516,7 +517,7 @@ def main():
                                / (ms_max / 1e3) / 1e6, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": ncu_traffic(forms[0]),
-                     "kernel": {"tma": "k_bulk_tma", "async": "k_bulk_async"}.get(head["bulk_loads"], "k_bulk"),
+                     "kernel": {"tma": "k_bulk_tma", "async": "k_bulk_async", "pairs": "k_bulk_pairs"}.get(head["bulk_loads"], "k_bulk"),
                      "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bulk, "launch_ms": round(bulk_ms, 5),
                      "step": {"frac": round(step_gbs / peak, 4), "achieved": round(step_gbs, 1),

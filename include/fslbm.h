@@ -84,12 +84,16 @@ enum fslbm_where { FSLBM_HOST = 0, FSLBM_DEVICE = 1 };
  * counterpart in the paper; the pull of Eq. lbe1 is the same every way, and
  * so are the results, bit for bit).  FP64 lattices always load plainly. */
 enum fslbm_loads {
-  FSLBM_LOADS_PLAIN = 0, /* default: plain coalesced global loads (the fastest on GB300) */
+  FSLBM_LOADS_PLAIN = 0, /* default: one cell per lane, plain coalesced global loads */
   FSLBM_LOADS_ASYNC = 1, /* each lane copies its 19 values into shared memory with cp.async,
                             two 32-cell segments ahead of use */
   FSLBM_LOADS_TMA = 2    /* the 19 rows of a segment by tensor-map (TMA) copies; needs nx a multiple
                             of 16 bytes of elements and nx >= 32 cells + two 16-byte halos, else
-                            plain loads */
+                            plain loads */,
+  FSLBM_LOADS_PAIRS = 3  /* two x-adjacent cells per lane: one 32-bit (FP16) or 64-bit (FP32) load
+                            per population without an x component and one store per population
+                            and pair, the collision of both cells in packed FP32x2 instructions
+                            (the fastest on GB300); needs nx even and 19 N < 2^32, else plain */
 };
 
 /* Field bits of fslbm_get_fields; out[] holds one pointer per set bit, in

@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "libfslbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fslbm_step.cu", "fslbm_conv.cu", "fslbm_state.cu", "fslbm_api.cu", "fslbm_adjoint.cu",
-           "fslbm_noalloc.cu", "fslbm_staged.cu", "fslbm_halo.cu", "fslbm_rate.cu"]
+           "fslbm_noalloc.cu", "fslbm_staged.cu", "fslbm_halo.cu", "fslbm_rate.cu", "fslbm_pairs.cu"]
 
 
 def nvcc() -> str:

@@ -103,7 +103,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   long long N = (long long)q.dims[0] * q.dims[1] * q.dims[2];
   if (N >= (1LL << 31)) return FSLBM_ERR_ARG;
   if (q.precision == FSLBM_F16 && q.compressible) return FSLBM_ERR_ARG;
-  if (q.bulk_loads < FSLBM_LOADS_PLAIN || q.bulk_loads > FSLBM_LOADS_TMA) return FSLBM_ERR_ARG;
+  if (q.bulk_loads < FSLBM_LOADS_PLAIN || q.bulk_loads > FSLBM_LOADS_PAIRS) return FSLBM_ERR_ARG;
   if (q.stress < 0 || q.stress > 2) return FSLBM_ERR_ARG;
   if (q.ub_extrap < 0 || q.ub_extrap > 1) return FSLBM_ERR_ARG;
   if (q.recon_nc < 0 || q.recon_nc > 1) return FSLBM_ERR_ARG;
@@ -217,6 +217,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   // loads of the bulk kernel: staged ones only for FP32/FP16 (FP64 is bound by its arithmetic)
   h->bulk_mode = BULK_PLAIN;
   if (h->prec != FSLBM_F64 && q.bulk_loads == FSLBM_LOADS_ASYNC) h->bulk_mode = BULK_ASYNC;
+  if (h->prec != FSLBM_F64 && q.bulk_loads == FSLBM_LOADS_PAIRS && pairs_shape_ok(p)) h->bulk_mode = BULK_PAIRS;
   if (h->prec != FSLBM_F64 && q.bulk_loads == FSLBM_LOADS_TMA && tma_shape_ok(p, h->prec)) {
     // tensor maps of both population buffers
     h->tmap = (CUtensorMap*)aligned_alloc(64, 2 * sizeof(CUtensorMap));
@@ -261,7 +262,10 @@ extern "C" int fslbm_tau_of_viscosity(double nu, double* tau) {
 
 extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
   if (!h) return FSLBM_ERR_ARG;
-  return h->bulk_mode == BULK_TMA ? FSLBM_LOADS_TMA : (h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC : FSLBM_LOADS_PLAIN);
+  return h->bulk_mode == BULK_TMA     ? FSLBM_LOADS_TMA
+         : h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC
+         : h->bulk_mode == BULK_PAIRS ? FSLBM_LOADS_PAIRS
+                                      : FSLBM_LOADS_PLAIN;
 }
 
 // the step's mass reduction runs inside the cooperative conversion kernel

@@ -40,7 +40,7 @@ inline int launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, siz
 int launch_reset(int* cnt, cudaStream_t st);
 
 // how the bulk kernel reaches its pulled values (fslbm_bulk_loads)
-enum BulkMode { BULK_PLAIN = 0, BULK_TMA = 1, BULK_ASYNC = 2 };
+enum BulkMode { BULK_PLAIN = 0, BULK_TMA = 1, BULK_ASYNC = 2, BULK_PAIRS = 3 };
 
 // bulk_mode: BulkMode (FP32/FP16 only for the staged modes); tmap: tensor map
 // of v.fin for BULK_TMA
@@ -57,6 +57,13 @@ int launch_bulk_tma(const Par& p, const View<P>& v, const CUtensorMap* map, cuda
                     const int* seglist, const int* segcount);
 template <int P>
 int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
+                      const int* segcount);
+
+// bulk kernel with two x-adjacent cells per lane (fslbm_pairs.cu): shape
+// test (nx even) and launcher (FP32/FP16)
+bool pairs_shape_ok(const Par& p);
+template <int P>
+int launch_bulk_pairs(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
                       const int* segcount);
 
 // records timing event k of the handle's current step (host side, fslbm_api.cu)

@@ -1,0 +1,402 @@
+// fslbm_pairs.cu -- bulk stream-collide with two x-adjacent cells per lane.
+//
+// k_bulk_pairs does the work of k_bulk (liquid cells of the fluid-segment
+// list, Eq. lbe1 pull with half-way bounce-back at non-periodic faces,
+// Eq. lbe2 collision, interface cells compacted into a list, per-warp FP64
+// partial sums of the liquid density) with the same arithmetic per cell, so
+// the populations, flags and lists it produces equal k_bulk's bit for bit.
+// It differs in how the pulled values reach the lanes: each half-warp takes
+// one 32-cell segment of the list, and lane l of it the cells x0 + 2l and
+// x0 + 2l + 1, whose values of one population sit in one aligned word of a
+// row (FP16: 32 bits, FP32: 64 bits).  The nine populations without an x
+// component are pulled one word per pair, the ten shifted along x one value
+// per cell, and the 19 results are stored one word per pair: 28 loads and 19
+// stores per two cells instead of 38 and 38.  The collisions of the two cells
+// run together in packed FP32x2 instructions (one instruction per operation
+// of both cells).  A source beyond a non-periodic face is replaced by the
+// cell's own slot of the opposite population (half-way bounce-back).
+// A segment holding a liquid cell that needs the general pull (next to a WALL
+// cell, on a periodic face, CLI link fractions or a moving wall on a face)
+// takes the general path of k_bulk for its liquid cells.  Lattices with odd
+// nx (rows not word-aligned) use k_bulk.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "fslbm_dev.cuh"
+#include "fslbm_kernels.h"
+#include "fslbm_pull.cuh"
+
+namespace fsl {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// resident blocks of 128 threads per SM (the register budget of a lane
+// holding two cells: 80 registers in FP16, 96 in FP32); the grid is one
+// resident wave
+#ifndef FSL_PAIRS_BLOCKS16
+#define FSL_PAIRS_BLOCKS16 6
+#endif
+#ifndef FSL_PAIRS_BLOCKS32
+#define FSL_PAIRS_BLOCKS32 5
+#endif
+template <int P>
+constexpr int pairs_blocks() { return P == P16 ? FSL_PAIRS_BLOCKS16 : FSL_PAIRS_BLOCKS32; }
+
+// A word holding the values of two x-adjacent cells (lo: the even cell).
+template <int P>
+struct PairWord;
+
+template <>
+struct PairWord<P16> {
+  using W = unsigned;
+  static __device__ __forceinline__ W load(const __half* base, unsigned k) {
+    return __ldg(reinterpret_cast<const unsigned*>(base + k));
+  }
+  // two single values into one word (lo: element ka, hi: element kb)
+  static __device__ __forceinline__ W load2(const __half* base, unsigned ka, unsigned kb) {
+    const unsigned a = __ldg(reinterpret_cast<const unsigned short*>(base + ka));
+    const unsigned b = __ldg(reinterpret_cast<const unsigned short*>(base + kb));
+    return a | (b << 16);
+  }
+  static __device__ __forceinline__ W zero() { return 0u; }
+  static __device__ __forceinline__ float2 unpack(W w) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
+  }
+  // rounded as the scalar store rounds each value
+  static __device__ __forceinline__ W pack(float2 v) {
+    const __half2 h = __floats2half2_rn(v.x, v.y);
+    W w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
+  static __device__ __forceinline__ void store(__half* base, unsigned k, W w) { *reinterpret_cast<unsigned*>(base + k) = w; }
+  static __device__ __forceinline__ void store_lo(__half* base, unsigned k, W w) {
+    *reinterpret_cast<unsigned short*>(base + k) = (unsigned short)(w & 0xffffu);
+  }
+  static __device__ __forceinline__ void store_hi(__half* base, unsigned k, W w) {
+    *reinterpret_cast<unsigned short*>(base + k + 1) = (unsigned short)(w >> 16);
+  }
+};
+
+template <>
+struct PairWord<P32> {
+  using W = float2;
+  static __device__ __forceinline__ W load(const float* base, unsigned k) {
+    return __ldg(reinterpret_cast<const float2*>(base + k));
+  }
+  static __device__ __forceinline__ W load2(const float* base, unsigned ka, unsigned kb) {
+    return make_float2(__ldg(base + ka), __ldg(base + kb));
+  }
+  static __device__ __forceinline__ W zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ float2 unpack(W w) { return w; }
+  static __device__ __forceinline__ W pack(float2 v) { return v; }
+  static __device__ __forceinline__ void store(float* base, unsigned k, W w) { *reinterpret_cast<float2*>(base + k) = w; }
+  static __device__ __forceinline__ void store_lo(float* base, unsigned k, W w) { base[k] = w.x; }
+  static __device__ __forceinline__ void store_hi(float* base, unsigned k, W w) { base[k + 1] = w.y; }
+};
+
+// ---------------------------------------------------------------------------
+// The TRT collision of k_bulk (collide<float, SH> of fslbm_dev.cuh) for two
+// cells at once, in the packed FP32 instructions of sm_100 and later
+// (add/mul/fma.rn.f32x2): every operation of the scalar collision, in the same
+// order and with the same rounding, on the pair (lo, hi), so each half equals
+// the scalar result bit for bit while the pair costs one instruction per
+// operation.  On return rho holds sum f (minus 1: the stored deviations).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <int q>
+__device__ __forceinline__ float2 cdot2(float2 ux, float2 uy, float2 uz) {
+  float2 s = bc2(0.f);
+  if (cx(q) == 1) s = add2(s, ux);
+  if (cx(q) == -1) s = sub2(s, ux);
+  if (cy(q) == 1) s = add2(s, uy);
+  if (cy(q) == -1) s = sub2(s, uy);
+  if (cz(q) == 1) s = add2(s, uz);
+  if (cz(q) == -1) s = sub2(s, uz);
+  return s;
+}
+
+template <bool SH>
+__device__ __forceinline__ void collide_x2(const Par& p, float2 (&f)[19], float2& rho) {
+  float2 r = f[0], jx = bc2(0.f), jy = bc2(0.f), jz = bc2(0.f);
+#pragma unroll
+  for (int q = 1; q < 19; ++q) r = add2(r, f[q]);
+#pragma unroll
+  for (int q = 1; q < 19; ++q) {
+    if (cx(q) == 1) jx = add2(jx, f[q]);
+    if (cx(q) == -1) jx = sub2(jx, f[q]);
+    if (cy(q) == 1) jy = add2(jy, f[q]);
+    if (cy(q) == -1) jy = sub2(jy, f[q]);
+    if (cz(q) == 1) jz = add2(jz, f[q]);
+    if (cz(q) == -1) jz = sub2(jz, f[q]);
+  }
+  const float2 r0 = p.compressible ? (SH ? add2(bc2(1.f), r) : r) : bc2(1.f);
+  const float2 ir0 = p.compressible ? make_float2(1.f / r0.x, 1.f / r0.y) : bc2(1.f);
+  const float2 Ux = mul2(jx, ir0), Uy = mul2(jy, ir0), Uz = mul2(jz, ir0);
+  const float gx = (float)p.g[0], gy = (float)p.g[1], gz = (float)p.g[2];
+  const float2 ux = fma2(bc2(0.5f), bc2(gx), Ux), uy = fma2(bc2(0.5f), bc2(gy), Uy),
+               uz = fma2(bc2(0.5f), bc2(gz), Uz);
+  const float ilm = (float)p.inv_lam_m;
+  const float2 vx = fma2(bc2(-gx), bc2(ilm), Ux), vy = fma2(bc2(-gy), bc2(ilm), Uy),
+               vz = fma2(bc2(-gz), bc2(ilm), Uz);
+  const float2 usq = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
+  const float2 lp = bc2((float)p.lam_p), lm = bc2((float)p.lam_m);
+  const float2 nl = bc2(p.linear_eq ? 0.f : 1.f);
+  const float2 k0 = mul2(mul2(bc2(1.5f * wq<float>(0)), r0), nl);
+  const float2 k1 = mul2(mul2(bc2(1.5f * wq<float>(1)), r0), nl);
+  const float2 k7 = mul2(mul2(bc2(1.5f * wq<float>(7)), r0), nl);
+  // the momentum-exact weights of e^- (as in collide)
+  constexpr float m7f = 1.f / 12.f;
+  constexpr float m1f = (1.f - 8.f * m7f) * 0.5f;
+  const float2 m1 = mul2(bc2(m1f), r0), m7 = mul2(bc2(m7f), r0);
+  float2 out[19];
+  {
+    const float2 ep = fma2(k0, neg2(usq), mul2(bc2(wq<float>(0)), r));
+    out[0] = fma2(lp, sub2(f[0], ep), f[0]);
+  }
+#define FSL_PAIR2(q)                                                                     \
+  {                                                                                      \
+    constexpr int qb = inv(q);                                                           \
+    const float2 kq = q <= 6 ? k1 : k7, mq = q <= 6 ? m1 : m7;                           \
+    const float2 cu = cdot2<q>(ux, uy, uz), cv = cdot2<q>(vx, vy, vz);                   \
+    const float2 ep = fma2(kq, fma2(mul2(bc2(3.f), cu), cu, neg2(usq)), mul2(bc2(wq<float>(q)), r)); \
+    const float2 em = mul2(mq, cv);                                                      \
+    const float2 np = fma2(bc2(0.5f), add2(f[q], f[qb]), neg2(ep));                      \
+    const float2 nm = fma2(bc2(0.5f), sub2(f[q], f[qb]), neg2(em));                      \
+    out[q] = fma2(lm, nm, fma2(lp, np, f[q]));                                           \
+    out[qb] = fma2(neg2(lm), nm, fma2(lp, np, f[qb]));                                   \
+  }
+  FSL_PAIR2(1) FSL_PAIR2(3) FSL_PAIR2(5) FSL_PAIR2(7) FSL_PAIR2(9)
+  FSL_PAIR2(11) FSL_PAIR2(13) FSL_PAIR2(15) FSL_PAIR2(17)
+#undef FSL_PAIR2
+#pragma unroll
+  for (int q = 0; q < 19; ++q) f[q] = out[q];
+  rho = r;
+}
+
+// Interface cells of the lanes' pairs into a list in x order (the even cell
+// before the odd one, the lanes in order), so that the interface kernels see
+// the cells as k_bulk lists them: back = false fills list[k] upward (count
+// *count), back = true list[cap - 1 - k].  All 32 lanes call it.
+__device__ __forceinline__ void append_pair(bool pa, bool pb, int ia, int* list, int* count, int cap, int* err,
+                                            bool back) {
+  const unsigned ba = __ballot_sync(FULL, pa), bb = __ballot_sync(FULL, pb);
+  if (!(ba | bb)) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(count, __popc(ba) + __popc(bb));
+  base = __shfl_sync(FULL, base, 0);
+  const int k = base + __popc(ba & lt) + __popc(bb & lt);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (!(c == 0 ? pa : pb)) continue;
+    const int kk = k + (c == 1 && pa ? 1 : 0);
+    if (kk < cap) list[back ? cap - 1 - kk : kk] = ia + c;
+    else atomicOr(err, ERRB_OVERFLOW);
+  }
+}
+
+// k_bulk's test for a liquid cell whose sources are plain offsets or lie
+// beyond a non-periodic face (bounce-back from its own slots)
+__device__ __forceinline__ bool fast_cell(const Par& p, uint8_t fl, int x, int y, int z) {
+  const bool ax = x == 0 || x == p.nx - 1, ay = y == 0 || y == p.ny - 1, az = z == 0 || z == p.nz - 1;
+  if ((fl & KIND) != LIQ) return false;
+  if (p.has_wd || p.has_uw) return !(fl & NEARB) && !ax && !ay && !az;
+  return !(fl & NEARW) && !(ax && p.px) && !(ay && p.py) && !(az && p.pz);
+}
+
+// the general pull of k_bulk for one liquid cell (walls, periodic faces, CLI)
+template <int P>
+__device__ __forceinline__ void general_cell(const Par& p, const View<P>& v, long long i, int x, int y, int z,
+                                             typename Form<P>::R (&f)[19]) {
+  using R = typename Form<P>::R;
+  const size_t N = (size_t)p.N;
+  unsigned wallm, gasm;
+  f[0] = ld<P, 0>(v.fin, (size_t)i);
+  pull_general<P>(p, v, x, y, z, f, wallm, gasm);
+  if (gasm) atomicOr(v.err, ERRB_STATE);  // liquid must not touch gas
+  wallm |= gasm;
+  if (wallm) {
+    R own[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) own[q] = ldq<P>(v.fin, (size_t)q * N + (size_t)i, q);
+    wall_links<P>(p, v, i, wallm, 0u, own, f);
+  }
+}
+
+// One liquid cell of a segment that needs the general pull, as k_bulk
+// treats it; returns its density for the mass balance (0 if not owned).
+template <int P>
+__device__ __noinline__ double slow_cell(const Par& p, const View<P>& v, long long i, int x, int y, int z,
+                                         uint8_t fl) {
+  using R = typename Form<P>::R;
+  constexpr bool SH = Form<P>::SH;
+  const size_t N = (size_t)p.N;
+  const long long sy = p.nx, sz = (long long)p.nx * p.ny;
+  R f[19];
+  if (fast_cell(p, fl, x, y, z)) {
+    // plain offsets, bounce-back beyond a non-periodic face
+    const bool ax0 = x == 0, ax1 = x == p.nx - 1, ay0 = y == 0, ay1 = y == p.ny - 1, az0 = z == 0,
+               az1 = z == p.nz - 1;
+    f[0] = ld<P, 0>(v.fin, (size_t)i);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      const bool bbq = (cx(q) == 1 && ax0) || (cx(q) == -1 && ax1) || (cy(q) == 1 && ay0) || (cy(q) == -1 && ay1) ||
+                       (cz(q) == 1 && az0) || (cz(q) == -1 && az1);
+      f[q] = bbq ? ldq<P>(v.fin, (size_t)inv(q) * N + (size_t)i, inv(q))
+                 : ldq<P>(v.fin, (size_t)q * N + (size_t)(i - (cx(q) + sy * cy(q) + sz * cz(q))), q);
+    }
+  } else {
+    general_cell<P>(p, v, i, x, y, z, f);
+  }
+  R rho, ux, uy, uz;
+  collide<R, SH>(p, f, rho, ux, uy, uz);
+  if (rho_bad<SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
+  return owned(p, x, y, z) ? rho_full<SH>(rho) : 0.0;
+}
+
+// The pulled values of population q for the pair (xa, xa + 1) of a row.  A
+// population without an x component is one aligned word of the source row
+// (or, beyond a y or z face, of the pair's own slots of the opposite
+// population); one with an x component is shifted by one cell against the
+// word grid and takes two single-value loads, each from the cell's own slot
+// of the opposite population where its source lies beyond a face.  All loads
+// are independent of one another.
+template <int P, int q>
+__device__ __forceinline__ typename PairWord<P>::W pull_pair(const Par& p, const typename Form<P>::S* fin, unsigned N,
+                                                            unsigned ia, unsigned sy, unsigned sz, int xa, int y,
+                                                            int z) {
+  using PW = PairWord<P>;
+  // the source row beyond a y or z face: bounce-back
+  const bool bb = (cy(q) == 1 && y == 0) || (cy(q) == -1 && y == p.ny - 1) || (cz(q) == 1 && z == 0) ||
+                  (cz(q) == -1 && z == p.nz - 1);
+  // 32-bit element indices (19 N < 2^32): the offsets wrap modulo 2^32 to the
+  // in-range result
+  const unsigned own_k = (unsigned)inv(q) * N + ia;
+  const unsigned src_k = (unsigned)q * N + ia - (unsigned)cx(q) - sy * (unsigned)cy(q) - sz * (unsigned)cz(q);
+  if constexpr (cx(q) == 0) {
+    return PW::load(fin, bb ? own_k : src_k);
+  } else {
+    const bool bba = bb || (cx(q) == 1 && xa == 0);           // the even cell's source beyond the x face
+    const bool bbb = bb || (cx(q) == -1 && xa + 2 == p.nx);   // the odd cell's
+    return PW::load2(fin, bba ? own_k : src_k, bbb ? own_k + 1 : src_k + 1);
+  }
+}
+
+// nparts: the mass-balance partial slots of the bulk kernels (one per warp of
+// k_bulk's grid); the slots beyond this grid's warps are zeroed
+template <int P>
+__global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, View<P> v,
+                                                                      const int* __restrict__ seglist,
+                                                                      const int* __restrict__ segcount, int nparts) {
+  pdl_begin();
+  using R = typename Form<P>::R;
+  using PW = PairWord<P>;
+  using W = typename PW::W;
+  constexpr bool SH = Form<P>::SH;
+  const int nseg = *((volatile const int*)segcount);
+  const int lane = threadIdx.x & 31, hl = lane & 15;
+  const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned Nu = (unsigned)p.N, syu = (unsigned)p.nx, szu = (unsigned)(p.nx * p.ny);
+  double msum = 0.0;
+  for (int base = 2 * gw; base < nseg; base += 2 * nw) {  // the same count of rounds on every lane
+    const int si = base + (lane >> 4);
+    const bool act = si < nseg;
+    const int4 sd = act ? reinterpret_cast<const int4*>(seglist)[si] : make_int4(0, 0, 0, 0);
+    const int x0 = sd.x, y = sd.y, z = sd.z;
+    const int len = act ? min(32, p.nx - x0) : 0;  // even (nx even, x0 a multiple of 32)
+    const bool in = 2 * hl < len;
+    const long long ia = (long long)sd.w + 2 * hl;  // the even cell of the pair
+    const int xa = x0 + 2 * hl;
+    const unsigned fl2 = in ? (unsigned)*reinterpret_cast<const unsigned short*>(v.flags + ia) : (GAS | (GAS << 8));
+    const uint8_t fla = (uint8_t)(fl2 & 0xffu), flb = (uint8_t)(fl2 >> 8);
+    const uint8_t ka = fla & KIND, kb = flb & KIND;
+    {  // interface cells: those whose stencil (every cell within 3) lies inside to the front
+      const bool yz3 = y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
+      const bool in3a = yz3 && xa >= 3 && xa < p.nx - 3, in3b = yz3 && xa + 1 >= 3 && xa + 1 < p.nx - 3;
+      const bool ia_ = ka == IFC, ib_ = kb == IFC;
+      append_pair(ia_ && in3a, ib_ && in3b, (int)ia, v.ilist, &v.cnt[0], v.cap, v.err, false);
+      append_pair(ia_ && !in3a, ib_ && !in3b, (int)ia, v.ilist, &v.cnt[6], v.cap, v.err, true);
+    }
+    const bool la = ka == LIQ, lb = kb == LIQ;
+    const bool slow = (la && !fast_cell(p, fla, xa, y, z)) || (lb && !fast_cell(p, flb, xa + 1, y, z));
+    const unsigned bslow = __ballot_sync(FULL, slow), bliq = __ballot_sync(FULL, la || lb);
+    const bool hslow = (bslow & hmask) != 0u;
+    const bool hwork = (bliq & hmask) != 0u && !hslow;  // the pair path serves this half
+    if (hwork && (la || lb)) {
+      const unsigned iau = (unsigned)ia;
+      W w[19];
+#define FSL_PP(q) w[q] = pull_pair<P, q>(p, v.fin, Nu, iau, syu, szu, xa, y, z);
+      FSL_PP(0) FSL_PP(1) FSL_PP(2) FSL_PP(3) FSL_PP(4) FSL_PP(5) FSL_PP(6) FSL_PP(7) FSL_PP(8)
+      FSL_PP(9) FSL_PP(10) FSL_PP(11) FSL_PP(12) FSL_PP(13) FSL_PP(14) FSL_PP(15) FSL_PP(16)
+      FSL_PP(17) FSL_PP(18)
+#undef FSL_PP
+      {
+        float2 f[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] = PW::unpack(w[q]);
+        float2 rho;
+        collide_x2<SH>(p, f, rho);
+        if ((la && rho_bad<SH>(rho.x)) || (lb && rho_bad<SH>(rho.y))) atomicOr(v.err, ERRB_UNSTABLE);
+        if (la && owned(p, xa, y, z)) msum += rho_full<SH>(rho.x);
+        if (lb && owned(p, xa + 1, y, z)) msum += rho_full<SH>(rho.y);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) w[q] = PW::pack(f[q]);
+        if (la && lb) {
+#pragma unroll
+          for (int q = 0; q < 19; ++q) PW::store(v.fout, (unsigned)q * Nu + iau, w[q]);
+        } else if (la) {
+#pragma unroll
+          for (int q = 0; q < 19; ++q) PW::store_lo(v.fout, (unsigned)q * Nu + iau, w[q]);
+        } else if (lb) {
+#pragma unroll
+          for (int q = 0; q < 19; ++q) PW::store_hi(v.fout, (unsigned)q * Nu + iau, w[q]);
+        }
+      }
+    }
+    if (hslow) {
+      // the general path of k_bulk, one cell after the other (out of line: rare)
+      if (la) msum += slow_cell<P>(p, v, ia, xa, y, z, fla);
+      if (lb) msum += slow_cell<P>(p, v, ia + 1, xa + 1, y, z, flb);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(FULL, msum, o);
+  if (lane == 0) v.partials[gw] = msum;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (nw + t < nparts) v.partials[nw + t] = 0.0;
+}
+
+// rows word-aligned (nx even) and the population arrays indexable in 32 bits
+bool pairs_shape_ok(const Par& p) { return (p.nx & 1) == 0 && 19LL * p.N < (1LL << 32); }
+
+template <int P>
+int launch_bulk_pairs(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
+                      const int* segcount) {
+  if constexpr (P == P64) {
+    return 1;
+  } else {
+    // bulk_blocks is 8 resident blocks per SM of k_bulk; one resident wave here
+    const int grid = bulk_blocks / 8 * pairs_blocks<P>();
+    return launch_k(k_bulk_pairs<P>, grid, 128, 0, st, p, v, seglist, segcount, bulk_blocks * 4);
+  }
+}
+
+template int launch_bulk_pairs<P64>(const Par&, const View<P64>&, cudaStream_t, int, const int*, const int*);
+template int launch_bulk_pairs<P32>(const Par&, const View<P32>&, cudaStream_t, int, const int*, const int*);
+template int launch_bulk_pairs<P16>(const Par&, const View<P16>&, cudaStream_t, int, const int*, const int*);
+
+}  // namespace fsl

@@ -475,6 +475,9 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
     } else if (bulk_mode == BULK_ASYNC) {
       if (launch_bulk_async<P>(p, v, st, bulk_blocks, seglist, segcount)) return 1;
       launched = true;
+    } else if (bulk_mode == BULK_PAIRS) {
+      if (launch_bulk_pairs<P>(p, v, st, bulk_blocks, seglist, segcount)) return 1;
+      launched = true;
     }
   }
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))

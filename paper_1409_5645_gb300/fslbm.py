@@ -22,7 +22,7 @@ F64, F32, F16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 FIELD_FLAGS, FIELD_F, FIELD_MASS, FIELD_PHI, FIELD_RHO, FIELD_U = 1, 2, 4, 8, 16, 32
 PRECISIONS = {"f64": F64, "f32": F32, "f16": F16}
-LOADS = {"plain": 0, "async": 1, "tma": 2}  # fslbm_loads
+LOADS = {"plain": 0, "async": 1, "tma": 2, "pairs": 3}  # fslbm_loads
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_STATE", -5: "ERR_UNSTABLE",
           -6: "ERR_OVERFLOW", -7: "ERR_TIMEOUT", -8: "ERR_TOO_LARGE"}
 

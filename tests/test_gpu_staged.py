@@ -1,7 +1,8 @@
-"""The staged bulk kernels of FP32 and FP16 storage (cp.async copies and TMA
-row copies into shared memory): identical results to the plain-load kernel,
-bit for bit, on lattices with a ragged last x segment, walls, periodic wraps
-and conversions; the rule that selects them."""
+"""The other bulk kernels of FP32 and FP16 storage (cp.async copies and TMA
+row copies into shared memory, two x-adjacent cells per lane): identical
+results to the plain-load kernel, bit for bit, on lattices with a ragged last
+x segment, walls, periodic wraps and conversions; the rule that selects
+them."""
 import numpy as np
 import pytest
 
@@ -27,7 +28,7 @@ def _pair(c, precision, steps, every, loads):
     return conv
 
 
-@pytest.mark.parametrize("loads", ["async", "tma"])
+@pytest.mark.parametrize("loads", ["async", "tma", "pairs"])
 @pytest.mark.parametrize("precision", ["f32", "f16"])
 def test_staged_equals_plain_dam_break(precision, loads):
     """72 x 40 x 48 dam break (last x segment 8 cells): walls on all faces,
@@ -37,7 +38,7 @@ def test_staged_equals_plain_dam_break(precision, loads):
     assert conv[0] > 0 and conv[2] > 0
 
 
-@pytest.mark.parametrize("loads", ["async", "tma"])
+@pytest.mark.parametrize("loads", ["async", "tma", "pairs"])
 @pytest.mark.parametrize("precision", ["f32", "f16"])
 def test_staged_equals_plain_periodic_blob(precision, loads):
     """48^3 periodic box with a liquid blob in uniform flow: the wraps take the
@@ -65,15 +66,40 @@ def test_async_odd_sizes_equal_plain(precision):
     _pair(c, precision, 120, 30, "async")
 
 
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_pairs_ragged_segment_all_faces(precision):
+    """Two cells per lane on a 70 x 12 x 20 dam break: rows of 32 + 32 + 6
+    cells, the column's front crossing segment ends, half-way bounce-back at
+    all six faces (the x faces on the end lanes' extra words, the y and z
+    faces on whole rows)."""
+    c = cases.dam_break(nx=70, ny=12, nz=20, col_x=33, col_z=15, tau=0.6, g=3e-4, rule=1)
+    conv = _pair(c, precision, 300, 60, "pairs")
+    assert conv[0] > 0 and conv[2] > 0
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("make", [lambda: cases.inclined_film(), lambda: cases.plate_flow(),
+                                  lambda: cases.standing_wave(n=64, depth=32.0)],
+                         ids=["inclined_film_cli", "plate_flow_moving_wall", "standing_wave_sigma"])
+def test_pairs_general_path_cases(precision, make):
+    """Segments whose liquid cells need the general pull (CLI link fractions
+    at WALL cells, the shifted x wrap, a moving wall, periodic faces) take
+    it; the rest of the lattice the pairs."""
+    _pair(make(), precision, 200, 50, "pairs")
+
+
 def test_selection_rule():
-    """Staged loads for FP32/FP16 storage only; TMA rows need nx a multiple of
-    16 bytes of elements and nx >= 32 cells + two 16-byte halos."""
+    """Staged loads and pairs for FP32/FP16 storage only; TMA rows need nx a
+    multiple of 16 bytes of elements and nx >= 32 cells + two 16-byte halos,
+    pairs an even nx."""
     p = cases.default_params(tau=0.6)
     for dims, prec, loads, want in [
             ((72, 8, 8), "f32", "tma", "tma"), ((40, 8, 8), "f32", "tma", "tma"), ((36, 8, 8), "f32", "tma", "plain"),
             ((70, 8, 8), "f32", "tma", "plain"), ((72, 8, 8), "f16", "tma", "tma"), ((44, 8, 8), "f16", "tma", "plain"),
             ((68, 8, 8), "f16", "tma", "plain"), ((64, 8, 8), "f64", "tma", "plain"), ((64, 8, 8), "f64", "async", "plain"),
-            ((37, 5, 3), "f32", "async", "async"), ((37, 5, 3), "f16", "async", "async")]:
+            ((37, 5, 3), "f32", "async", "async"), ((37, 5, 3), "f16", "async", "async"),
+            ((72, 8, 8), "f16", "pairs", "pairs"), ((38, 5, 3), "f32", "pairs", "pairs"),
+            ((37, 5, 3), "f16", "pairs", "plain"), ((64, 8, 8), "f64", "pairs", "plain")]:
         lat = fslbm.Lattice(dims, dict(p, bulk_loads=loads), precision=prec)
         assert lat.bulk_loads == want, (dims, prec, loads)
         lat.close()
