@@ -197,7 +197,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
             dalloc(h, &h->err, 8) && dalloc(h, &h->step_mass, 8) && dalloc(h, &h->total_out, 8);
   for (int k = 0; k < 6 && ok; ++k) ok = dalloc(h, &h->lists[k], Nn * sizeof(int));
   if (ok && q.keep_f0) ok = dalloc(h, &h->f0, 19 * Nn * 8);
-  if (ok) ok = dalloc(h, &h->seglist, (size_t)nseg * 4 * sizeof(int));  // int4 per segment
+  if (ok) ok = dalloc(h, &h->seglist, (size_t)nseg * 8 * sizeof(int));  // record and masks per segment
   if (!ok) {
     free_all(h);
     free(h);

@@ -26,7 +26,7 @@ struct fslbm {
   void* phiB;
   double* wd;
   int* lists[6];
-  int* seglist;  // 32-cell x segments holding fluid (rebuilt every step)
+  int* seglist;  // 32-cell x segments holding fluid: int4 records, then uint4 masks (rebuilt every step)
   int* cnt;
   double* share;
   void* geo;  // interface geometry scratch [5][cap] in the arithmetic type

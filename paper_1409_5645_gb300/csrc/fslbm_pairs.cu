@@ -307,35 +307,44 @@ __global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, Vi
   constexpr bool SH = Form<P>::SH;
   const int nseg = *((volatile const int*)segcount);
   const int lane = threadIdx.x & 31, hl = lane & 15;
-  const unsigned hmask = (lane < 16) ? 0x0000ffffu : 0xffff0000u;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const unsigned Nu = (unsigned)p.N, syu = (unsigned)p.nx, szu = (unsigned)(p.nx * p.ny);
   double msum = 0.0;
-  for (int base = 2 * gw; base < nseg; base += 2 * nw) {  // the same count of rounds on every lane
-    const int si = base + (lane >> 4);
+  // records and masks of the segment list (see k_segments); the next round's
+  // are loaded one round ahead, so a round's population loads depend on no
+  // load of its own
+  const int nsx = (p.nx + 31) >> 5;
+  const uint4* masks = reinterpret_cast<const uint4*>(seglist) + (long long)nsx * p.ny * p.nz;
+  int si = 2 * gw + (lane >> 4);
+  int4 sd_n = make_int4(0, 0, 0, 0);
+  uint4 sm_n = make_uint4(0u, 0u, 0u, 0u);
+  if (si < nseg) {
+    sd_n = reinterpret_cast<const int4*>(seglist)[si];
+    sm_n = masks[si];
+  }
+  for (int base = 2 * gw; base < nseg; base += 2 * nw, si += 2 * nw) {  // the same count of rounds on every lane
     const bool act = si < nseg;
-    const int4 sd = act ? reinterpret_cast<const int4*>(seglist)[si] : make_int4(0, 0, 0, 0);
+    const int4 sd = sd_n;
+    const uint4 sm = sm_n;  // liquid, interface, liquid needing the general pull
+    if (si + 2 * nw < nseg) {
+      sd_n = reinterpret_cast<const int4*>(seglist)[si + 2 * nw];
+      sm_n = masks[si + 2 * nw];
+    }
     const int x0 = sd.x, y = sd.y, z = sd.z;
-    const int len = act ? min(32, p.nx - x0) : 0;  // even (nx even, x0 a multiple of 32)
-    const bool in = 2 * hl < len;
     const long long ia = (long long)sd.w + 2 * hl;  // the even cell of the pair
     const int xa = x0 + 2 * hl;
-    const unsigned fl2 = in ? (unsigned)*reinterpret_cast<const unsigned short*>(v.flags + ia) : (GAS | (GAS << 8));
-    const uint8_t fla = (uint8_t)(fl2 & 0xffu), flb = (uint8_t)(fl2 >> 8);
-    const uint8_t ka = fla & KIND, kb = flb & KIND;
+    const unsigned bits = act ? (sm.x >> (2 * hl)) & 3u : 0u, ibits = act ? (sm.y >> (2 * hl)) & 3u : 0u;
     {  // interface cells: those whose stencil (every cell within 3) lies inside to the front
       const bool yz3 = y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
       const bool in3a = yz3 && xa >= 3 && xa < p.nx - 3, in3b = yz3 && xa + 1 >= 3 && xa + 1 < p.nx - 3;
-      const bool ia_ = ka == IFC, ib_ = kb == IFC;
+      const bool ia_ = ibits & 1u, ib_ = (ibits >> 1) & 1u;
       append_pair(ia_ && in3a, ib_ && in3b, (int)ia, v.ilist, &v.cnt[0], v.cap, v.err, false);
       append_pair(ia_ && !in3a, ib_ && !in3b, (int)ia, v.ilist, &v.cnt[6], v.cap, v.err, true);
     }
-    const bool la = ka == LIQ, lb = kb == LIQ;
-    const bool slow = (la && !fast_cell(p, fla, xa, y, z)) || (lb && !fast_cell(p, flb, xa + 1, y, z));
-    const unsigned bslow = __ballot_sync(FULL, slow), bliq = __ballot_sync(FULL, la || lb);
-    const bool hslow = (bslow & hmask) != 0u;
-    const bool hwork = (bliq & hmask) != 0u && !hslow;  // the pair path serves this half
+    const bool la = bits & 1u, lb = (bits >> 1) & 1u;
+    const bool hslow = act && sm.z != 0u;               // uniform over the half-warp
+    const bool hwork = act && sm.x != 0u && !hslow;     // the pair path serves this half
     if (hwork && (la || lb)) {
       const unsigned iau = (unsigned)ia;
       W w[19];
@@ -367,10 +376,11 @@ __global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, Vi
         }
       }
     }
-    if (hslow) {
+    if (hslow && (la || lb)) {
       // the general path of k_bulk, one cell after the other (out of line: rare)
-      if (la) msum += slow_cell<P>(p, v, ia, xa, y, z, fla);
-      if (lb) msum += slow_cell<P>(p, v, ia + 1, xa + 1, y, z, flb);
+      const unsigned fl2 = (unsigned)*reinterpret_cast<const unsigned short*>(v.flags + ia);
+      if (la) msum += slow_cell<P>(p, v, ia, xa, y, z, (uint8_t)(fl2 & 0xffu));
+      if (lb) msum += slow_cell<P>(p, v, ia + 1, xa + 1, y, z, (uint8_t)(fl2 >> 8));
     }
   }
 #pragma unroll

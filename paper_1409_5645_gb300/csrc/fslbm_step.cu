@@ -37,7 +37,18 @@ __device__ __forceinline__ double block_sum128(double v) {
 // ---------------------------------------------------------------------------
 // k_segments: compact list of the 32-cell x segments (one warp each) that
 // hold a liquid or interface cell; one thread per segment, one atomic per warp.
+// Besides the record (x0, y, z, first cell) of list entry k at seglist[4k],
+// it writes the segment's masks at seglist[4 (S + k)] (S: segments of the
+// lattice): bit j of each for cell x0 + j, liquid, interface, and liquid
+// needing the general pull (k_bulk's test of a fast cell, negated), so that a
+// bulk kernel reads no flag on its fast path.
 // ---------------------------------------------------------------------------
+// bit s of each byte of w, gathered into bits 0-3 (the four partial products
+// of the multiplier land on distinct bits, so no carries mix them)
+__device__ __forceinline__ unsigned byte_bits(unsigned w, int s) {
+  return ((((w >> s) & 0x01010101u) * 0x00204081u) >> 21) & 0xfu;
+}
+
 __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restrict__ flags, int* __restrict__ seglist,
                                                   int* __restrict__ count) {
   pdl_begin();
@@ -45,21 +56,35 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
   const long long nseg = (long long)nsx * p.ny * p.nz;
   const long long sgi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   bool act = false;
+  unsigned liq = 0u, ifc = 0u, nearb = 0u, nearw = 0u;
+  int len = 0;
   if (sgi < nseg) {
     const long long row = (long long)fdiv((unsigned)sgi, p.dnsx);
     const int x0 = (int)(sgi - row * nsx) << 5;
-    const int len = min(32, p.nx - x0);
+    len = min(32, p.nx - x0);
     const uint8_t* base = flags + row * p.nx + x0;
+    // kinds are one-hot (LIQ = bit 0, IFC = bit 1); NEARB = bit 4, NEARW = bit 5
     if (len == 32 && ((p.nx & 15) == 0)) {
       const uint4* v4 = reinterpret_cast<const uint4*>(base);
-      uint4 a = __ldg(v4), b = __ldg(v4 + 1);
-      unsigned acc = a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w;
-      act = (acc & 0x03030303u) != 0u;  // a byte with the liquid or interface bit
+      const uint4 a = __ldg(v4), b = __ldg(v4 + 1);
+      const unsigned w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        liq |= byte_bits(w[k], 0) << (4 * k);
+        ifc |= byte_bits(w[k], 1) << (4 * k);
+        nearb |= byte_bits(w[k], 4) << (4 * k);
+        nearw |= byte_bits(w[k], 5) << (4 * k);
+      }
     } else {
-      unsigned acc = 0u;
-      for (int k = 0; k < len; ++k) acc |= base[k];
-      act = (acc & 0x03u) != 0u;
+      for (int k = 0; k < len; ++k) {
+        const unsigned c = base[k];
+        liq |= (c & 1u) << k;
+        ifc |= ((c >> 1) & 1u) << k;
+        nearb |= ((c >> 4) & 1u) << k;
+        nearw |= ((c >> 5) & 1u) << k;
+      }
     }
+    act = (liq | ifc) != 0u;
   }
   // one global atomic per block: warp counts -> block offsets in shared memory
   __shared__ int wcount[8], wbase[8], bbase;
@@ -79,8 +104,17 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
     const unsigned row = fdiv((unsigned)sgi, p.dnsx);
     const unsigned zz = fdiv(row, p.dny);
     const int x0 = (int)((unsigned)sgi - row * (unsigned)nsx) << 5;
-    reinterpret_cast<int4*>(seglist)[bbase + wbase[w] + __popc(bal & ((1u << lane) - 1u))] =
-        make_int4(x0, (int)(row - zz * (unsigned)p.ny), (int)zz, (int)row * p.nx + x0);
+    const int y = (int)(row - zz * (unsigned)p.ny), z = (int)zz;
+    const int k = bbase + wbase[w] + __popc(bal & ((1u << lane) - 1u));
+    reinterpret_cast<int4*>(seglist)[k] = make_int4(x0, y, z, (int)row * p.nx + x0);
+    // liquid cells that need the general pull (fast_cell of the bulk kernels, negated)
+    const unsigned all = len == 32 ? 0xffffffffu : ((1u << len) - 1u);
+    const unsigned xf = (x0 == 0 ? 1u : 0u) | (x0 + len == p.nx ? 1u << (len - 1) : 0u);
+    const bool yf = y == 0 || y == p.ny - 1, zf = z == 0 || z == p.nz - 1;
+    unsigned slow;
+    if (p.has_wd || p.has_uw) slow = liq & (nearb | xf | ((yf || zf) ? all : 0u));
+    else slow = liq & (nearw | (p.px ? xf : 0u) | (((yf && p.py) || (zf && p.pz)) ? all : 0u));
+    reinterpret_cast<uint4*>(seglist)[nseg + k] = make_uint4(liq, ifc, slow, 0u);
   }
 }
 
