@@ -363,7 +363,7 @@ def adjoint_run(form, steps=4000, K=200):
     try:
         lat.adjoint_forward(steps, K)
         lat.adjoint_backward()
-    except fslbm.FslbmError as e:  # e.g. a conversion inside the window
+    except fslbm.FslbmError as e:
         lat.close()
         return {"steps": steps, "checkpoint_every": K, "error": str(e)}
     fwd, adj, peak = lat.adjoint_stats()
@@ -373,7 +373,7 @@ def adjoint_run(form, steps=4000, K=200):
             "peak_bytes": int(peak)}
 
 
-def adjoint_large(form, steps=400, K=40, dims=(256, 128, 128), peak=None):
+def adjoint_large(form, steps=400, K=40, dims=(256, 128, 128), peak=None, arith32=False):
     """Differentiation at scale: the dam break at 256 x 128 x 128 (4.2 M
     cells; cells fill, empty and appear inside the window, replayed by the
     adjoint), objective the mean x-velocity of the interface cells after
@@ -381,12 +381,13 @@ def adjoint_large(form, steps=400, K=40, dims=(256, 128, 128), peak=None):
     the fluid cells, and its bytes: per fluid cell k_adj_local reads the saved
     populations (19 s) and the incoming adjoint (19 x 8 B) and writes the
     outgoing adjoint and the pulled-population adjoints (2 x 19 x 8 B), and
-    k_adj_gather reads the latter and updates the former (3 x 19 x 8 B): 19 (s + 48) B."""
+    k_adj_gather reads the latter and updates the former (3 x 19 x 8 B): 19 (s + 48) B.
+    arith32: the reverse step of the FP32/FP16 form in FP32 arithmetic."""
     import numpy as np
     from paper_1409_5645_gb300 import cases, fslbm
     nx, ny, nz = dims
     c = cases.dam_break(nx=nx, ny=ny, nz=nz, col_x=nx // 4, col_z=nz * 3 // 4, tau=TAU, magic=MAGIC)
-    lat = fslbm.Lattice.from_case(c, precision=form)
+    lat = fslbm.Lattice.from_case(c, precision=form, adjoint_fp32=int(arith32))
     fl = c["flags"]
     nfluid = int(np.count_nonzero((fl == 1) | (fl == 2)))
     try:
@@ -399,7 +400,8 @@ def adjoint_large(form, steps=400, K=40, dims=(256, 128, 128), peak=None):
     lat.close()
     s = STORE_BYTES[form]
     gbs = nfluid * 19 * (s + 48) / (adj / 1e3) / 1e9
-    out = {"dims": list(dims), "steps": steps, "checkpoint_every": K, "fwd_ms_per_step": round(fwd, 5),
+    out = {"dims": list(dims), "steps": steps, "checkpoint_every": K,
+           "reverse_arithmetic": "fp32" if (arith32 and form != "f64") else "fp64", "fwd_ms_per_step": round(fwd, 5),
            "adj_ms_per_step": round(adj, 5), "adj_over_fwd": round(adj / fwd, 3) if fwd > 0 else None,
            "adj_mlups": round(c.N / (adj / 1e3) / 1e6, 1), "fluid_cells": nfluid,
            "adj_alg_gbs": round(gbs, 1), "peak_bytes": int(pk)}
@@ -589,15 +591,15 @@ def main():
                    "d2h_bytes_per_step": round(e2e["d2h_bytes_per_step"], 1), "steps": e2e_steps,
                    "includes": "initial state from pinned host memory, per-step mass read, final fields "
                                "(flags, rho, u, phi) read back"}
-    # differentiation: adjoint step cost per forward step (FP64 and FP32)
+    # differentiation: adjoint step cost per forward step (FP64 and FP32; the
+    # FP32 form's reverse step in FP64 and in FP32 arithmetic)
     if not args.no_adjoint:
-        # (FP32 rounding drifts the film's mass and fills a surface cell after
-        # about 4000 steps; a conversion ends a differentiated window, so the
-        # FP32 form is timed on the first 1000 steps)
         line["adjoint"] = {"workload": "film 8x4x64 depth 40, checkpoints with recompute",
                            "objective": "mean x-velocity of interface cells",
-                           "f64": adjoint_run("f64", 4000, 200), "f32": adjoint_run("f32", 1000, 100),
-                           "large": {f: adjoint_large(f, peak=peak) for f in ("f32", "f64")}}
+                           "f64": adjoint_run("f64", 4000, 200), "f32": adjoint_run("f32", 4000, 200),
+                           "large": {"f32": adjoint_large("f32", peak=peak),
+                                     "f32_arith32": adjoint_large("f32", peak=peak, arith32=True),
+                                     "f64": adjoint_large("f64", peak=peak)}}
     # the oracle on the host cores (rank 0, N = 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, st, el = oracle_rate((128, 64, 64), (32, 48), budget_s=12.0, tau=args.tau, magic=args.magic)

@@ -172,6 +172,11 @@ typedef struct {
                          (each through the cell's own fill) best reproduce the block's fill levels;
                          exact for planes.  The higher-order reconstruction the conclusion (Sec. 5)
                          asks of the interface position.  0 (default): Parker-Youngs */
+  int adjoint_fp32;   /* 1: the reverse step of an FP32/FP16 lattice computes in FP32, in the
+                         deviations f - w_q of the forward step (the adjoint variables stay FP64 in
+                         memory); 0 (default): in FP64.  An implementation choice: GB300 runs FP64
+                         at a small fraction of its FP32 rate, and the reverse step is bound by it.
+                         Ignored by FP64 lattices */
 } fslbm_params;
 
 /* Defaults: tau 0.8, magic 3/16, g 0, rho_G 1, sigma 0, FSL, rho_0 = 1,

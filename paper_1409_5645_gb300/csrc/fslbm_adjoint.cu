@@ -103,12 +103,26 @@ struct AdjView {
   const int* nfl;
 };
 
+// a population of the stored state in the arithmetic A of the reverse step:
+// f_q in FP64, or in the deviation mode (float A on FP32/FP16 storage) the
+// stored f_q - w_q itself
+template <int P, class A>
+__device__ __forceinline__ A ld_adj(const typename Form<P>::S* __restrict__ f, size_t k, int q) {
+  if constexpr (sizeof(A) == 4 && Form<P>::SH) {
+    if constexpr (P == P16) return __half2float(f[k]);
+    else return (A)f[k];
+  } else {
+    return (A)ldq_full<P>(f, k, q);
+  }
+}
+
 // warp-level sums of th added to out (one atomic per warp and component; all
 // 32 lanes call it)
-__device__ __forceinline__ void warp_add(double (&th)[5], double* out) {
+template <class A>
+__device__ __forceinline__ void warp_add(A (&th)[5], double* out) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double v = th[k];
+    double v = (double)th[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out + k, v);
@@ -116,83 +130,84 @@ __device__ __forceinline__ void warp_add(double (&th)[5], double* out) {
 }
 
 // d e_q^+ / d u for rho_0 = 1: w_q (9 (c.u) c - 3 u); zero for the linear equilibrium
-__device__ __forceinline__ void deplus_du(const Par& p, int q, double ux, double uy, double uz, double g,
-                                          double (&ub)[3]) {
+template <class A>
+__device__ __forceinline__ void deplus_du(const Par& p, int q, A ux, A uy, A uz, A g, A (&ub)[3]) {
   if (p.linear_eq) return;
-  double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-  double cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-  ub[0] += g * w * (9.0 * cu * cx(q) - 3.0 * ux);
-  ub[1] += g * w * (9.0 * cu * cy(q) - 3.0 * uy);
-  ub[2] += g * w * (9.0 * cu * cz(q) - 3.0 * uz);
+  A w = q == 0 ? A(1.0) / A(3.0) : (q <= 6 ? A(1.0) / A(18.0) : A(1.0) / A(36.0));
+  A cu = A(cx(q)) * ux + A(cy(q)) * uy + A(cz(q)) * uz;
+  ub[0] += g * w * (A(9.0) * cu * cx(q) - A(3.0) * ux);
+  ub[1] += g * w * (A(9.0) * cu * cy(q) - A(3.0) * uy);
+  ub[2] += g * w * (A(9.0) * cu * cz(q) - A(3.0) * uz);
 }
 
-__device__ __forceinline__ double eplus_d(const Par& p, int q, double rho, double ux, double uy, double uz) {
-  double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-  double e = w * rho;
+template <class A>
+__device__ __forceinline__ A eplus_d(const Par& p, int q, A rho, A ux, A uy, A uz) {
+  A w = q == 0 ? A(1.0) / A(3.0) : (q <= 6 ? A(1.0) / A(18.0) : A(1.0) / A(36.0));
+  A e = w * rho;
   if (!p.linear_eq) {
-    double cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-    e += w * 1.5 * (3.0 * cu * cu - (ux * ux + uy * uy + uz * uz));
+    A cu = A(cx(q)) * ux + A(cy(q)) * uy + A(cz(q)) * uz;
+    e += w * A(1.5) * (A(3.0) * cu * cu - (ux * ux + uy * uy + uz * uz));
   }
   return e;
 }
 
 // Reverse of the TRT collision (Eq. lbe2, rho_0 = 1) at pre-collision f with
 // output adjoint ab: adds to fb and to th (lambda_+, lambda_-, g).
-__device__ void collide_rev(const Par& p, const double (&f)[19], const double (&ab)[19], double (&fb)[19],
-                            double (&th)[5]) {
-  const double lp = p.lam_p, lm = p.lam_m;
-  const double g0 = p.g[0], g1 = p.g[1], g2 = p.g[2];
-  double r = 0, jx = 0, jy = 0, jz = 0;
+template <class A>
+__device__ void collide_rev(const Par& p, const A (&f)[19], const A (&ab)[19], A (&fb)[19], A (&th)[5]) {
+  const A lp = (A)p.lam_p, lm = (A)p.lam_m;
+  const A g0 = (A)p.g[0], g1 = (A)p.g[1], g2 = (A)p.g[2];
+  A r = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
   for (int q = 0; q < 19; ++q) {
     r += f[q];
-    jx += cx(q) * f[q];
-    jy += cy(q) * f[q];
-    jz += cz(q) * f[q];
+    jx += A(cx(q)) * f[q];
+    jy += A(cy(q)) * f[q];
+    jz += A(cz(q)) * f[q];
   }
-  const double ux = jx + 0.5 * g0, uy = jy + 0.5 * g1, uz = jz + 0.5 * g2;
-  const double vx = jx - g0 / lm, vy = jy - g1 / lm, vz = jz - g2 / lm;
-  double rb = 0, ub[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+  const A ux = jx + A(0.5) * g0, uy = jy + A(0.5) * g1, uz = jz + A(0.5) * g2;
+  const A vx = jx - g0 / lm, vy = jy - g1 / lm, vz = jz - g2 / lm;
+  A rb = 0, ub[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
 #pragma unroll
   for (int q = 0; q < 19; ++q) fb[q] += ab[q];
   {  // rest population: out0 = f0 + l+ (f0 - e0+)
-    double e0 = eplus_d(p, 0, r, ux, uy, uz);
-    double np = f[0] - e0;
-    double npb = lp * ab[0];
+    A e0 = eplus_d<A>(p, 0, r, ux, uy, uz);
+    A np = f[0] - e0;
+    A npb = lp * ab[0];
     th[0] += np * ab[0];
     fb[0] += npb;
-    rb += (1.0 / 3.0) * (-npb);
-    deplus_du(p, 0, ux, uy, uz, -npb, ub);
+    rb += (A(1.0) / A(3.0)) * (-npb);
+    deplus_du<A>(p, 0, ux, uy, uz, -npb, ub);
   }
 #pragma unroll
   for (int q = 1; q < 19; q += 2) {
     const int qb = q + 1;
-    double w = q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0;
-    double ep = eplus_d(p, q, r, ux, uy, uz);
-    double em = 3.0 * w * (cx(q) * vx + cy(q) * vy + cz(q) * vz);
-    double np = 0.5 * (f[q] + f[qb]) - ep;
-    double nm = 0.5 * (f[q] - f[qb]) - em;
-    double npb = lp * (ab[q] + ab[qb]);
-    double nmb = lm * (ab[q] - ab[qb]);
+    A w = q <= 6 ? A(1.0) / A(18.0) : A(1.0) / A(36.0);
+    A ep = eplus_d<A>(p, q, r, ux, uy, uz);
+    A em = A(3.0) * w * (A(cx(q)) * vx + A(cy(q)) * vy + A(cz(q)) * vz);
+    A np = A(0.5) * (f[q] + f[qb]) - ep;
+    A nm = A(0.5) * (f[q] - f[qb]) - em;
+    A npb = lp * (ab[q] + ab[qb]);
+    A nmb = lm * (ab[q] - ab[qb]);
     th[0] += np * (ab[q] + ab[qb]);
     th[1] += nm * (ab[q] - ab[qb]);
-    fb[q] += 0.5 * npb + 0.5 * nmb;
-    fb[qb] += 0.5 * npb - 0.5 * nmb;
+    fb[q] += A(0.5) * npb + A(0.5) * nmb;
+    fb[qb] += A(0.5) * npb - A(0.5) * nmb;
     // e^+: -npb;  e^-: -nmb
     rb += w * (-npb);
-    deplus_du(p, q, ux, uy, uz, -npb, ub);
-    vb[0] += 3.0 * w * cx(q) * (-nmb);
-    vb[1] += 3.0 * w * cy(q) * (-nmb);
-    vb[2] += 3.0 * w * cz(q) * (-nmb);
+    deplus_du<A>(p, q, ux, uy, uz, -npb, ub);
+    vb[0] += A(3.0) * w * A(cx(q)) * (-nmb);
+    vb[1] += A(3.0) * w * A(cy(q)) * (-nmb);
+    vb[2] += A(3.0) * w * A(cz(q)) * (-nmb);
   }
   // u = U + g/2, v = U - g/lambda_-, U = j
-  double Ub[3] = {ub[0] + vb[0], ub[1] + vb[1], ub[2] + vb[2]};
-  th[2] += 0.5 * ub[0] - vb[0] / lm;
-  th[3] += 0.5 * ub[1] - vb[1] / lm;
-  th[4] += 0.5 * ub[2] - vb[2] / lm;
+  A Ub[3] = {ub[0] + vb[0], ub[1] + vb[1], ub[2] + vb[2]};
+  th[2] += A(0.5) * ub[0] - vb[0] / lm;
+  th[3] += A(0.5) * ub[1] - vb[1] / lm;
+  th[4] += A(0.5) * ub[2] - vb[2] / lm;
   th[1] += (g0 * vb[0] + g1 * vb[1] + g2 * vb[2]) / (lm * lm);
 #pragma unroll
-  for (int q = 0; q < 19; ++q) fb[q] += rb + cx(q) * Ub[0] + cy(q) * Ub[1] + cz(q) * Ub[2];
+  for (int q = 0; q < 19; ++q) fb[q] += rb + A(cx(q)) * Ub[0] + A(cy(q)) * Ub[1] + A(cz(q)) * Ub[2];
 }
 
 __device__ __forceinline__ void block_add(double (&th)[5], double* out) {
@@ -357,20 +372,26 @@ __device__ __noinline__ double plane_fit_adjoint(const Par& p, const uint8_t* __
 // IFCP: the instance for interface cells (gas links, mass exchange,
 // geometry); the other runs the liquid cells, whose code is a small part of
 // this one (a liquid cell never touches gas).
-template <int P, bool IFCP>
+// A: the arithmetic of the reverse step (double; float for FP32/FP16 lattices
+// with adj32, which then works in the deviations f - w_q as the forward step
+// does: moments rho - 1, the gas density rho_G - 1 in the rebuilt links; every
+// closure is affine in the populations with weights summing to one per link
+// pair, so only the densities that divide (phi = m / rho) take the 1 back).
+template <int P, bool IFCP, class A>
 __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
   using R = typename Form<P>::R;
+  constexpr bool SH = sizeof(A) == 4 && Form<P>::SH;
   const size_t N = (size_t)p.N;
-  double th[5] = {0, 0, 0, 0, 0};
+  A th[5] = {0, 0, 0, 0, 0};
   const int nf = *a.nfl;
   for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < nf; li += gridDim.x * blockDim.x) {
     const long long i = a.flist[li];
     const uint8_t kc = IFCP ? (uint8_t)IFC : (uint8_t)LIQ;
     int x, y, z;
     coords(p, i, x, y, z);
-    double own[19], F[19], f[19];
+    A own[19], F[19], f[19];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) own[q] = ldq_full<P>(a.f, q * N + i, q);
+    for (int q = 0; q < 19; ++q) own[q] = ld_adj<P, A>(a.f, q * N + i, q);
     unsigned wallm = 0u, gasm = 0u;
     int src[19];
     F[0] = own[0];
@@ -380,15 +401,15 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
       long long s = nbr(p, x, y, z, -cx(q), -cy(q), -cz(q));
       src[q] = (int)s;
       uint8_t ks = kind_at(a.flags, s);
-      if (is_fluid(ks)) F[q] = ldq_full<P>(a.f, q * N + s, q);
-      else if (ks == WALL) { wallm |= 1u << q; F[q] = 0.0; }
-      else { gasm |= 1u << q; F[q] = 0.0; }
+      if (is_fluid(ks)) F[q] = ld_adj<P, A>(a.f, q * N + s, q);
+      else if (ks == WALL) { wallm |= 1u << q; F[q] = A(0.0); }
+      else { gasm |= 1u << q; F[q] = A(0.0); }
     }
     if constexpr (!IFCP) gasm = 0u;  // (liquid cells have no gas neighbour)
 #pragma unroll
     for (int q = 0; q < 19; ++q) f[q] = F[q];
     // own moments at t (rho_0 = 1): rho_t = sum f~, u_t = sum c f~ - g/2
-    double rt = 0, tx = 0, ty = 0, tz = 0;
+    A rt = 0, tx = 0, ty = 0, tz = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
       rt += own[q];
@@ -396,35 +417,35 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
       ty += cy(q) * own[q];
       tz += cz(q) * own[q];
     }
-    const double utx = tx - 0.5 * p.g[0], uty = ty - 0.5 * p.g[1], utz = tz - 0.5 * p.g[2];
+    const A utx = tx - A(0.5) * (A)p.g[0], uty = ty - A(0.5) * (A)p.g[1], utz = tz - A(0.5) * (A)p.g[2];
     const bool ifc = kc == IFC;
-    const double phic = ifc ? (double)a.phi[i] : 1.0;
+    const A phic = ifc ? (A)a.phi[i] : A(1);
     const bool dyn = ifc && !p.freeze;
     // mass exchange
-    double dm = 0.0;
+    A dm = A(0.0);
     if (dyn) {
 #pragma unroll
       for (int q = 1; q < 19; ++q) {
         if ((wallm | gasm) & (1u << q)) continue;
         uint8_t ks = a.flags[src[q]] & KIND;
-        double sw = (ks == LIQ) ? 1.0 : 0.5 * (phic + (double)a.phi[src[q]]);
+        A sw = (ks == LIQ) ? A(1.0) : A(0.5) * (phic + (A)a.phi[src[q]]);
         dm += sw * (F[q] - own[inv(q)]);
       }
     }
     // wall closures
-    double kw[19];
+    A kw[19];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) kw[q] = 0.0;
+    for (int q = 0; q < 19; ++q) kw[q] = A(0.0);
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
       if (!(wallm & (1u << q))) continue;
       const int pq = inv(q);
-      double val = own[pq];
+      A val = own[pq];
       if (p.has_wd) {
-        double dw = a.wd[(size_t)pq * N + i];
+        A dw = (A)a.wd[(size_t)pq * N + i];
         bool upf = !((wallm | gasm) & (1u << pq));
-        if (dw >= 0.0 && upf) {
-          kw[q] = (1.0 - 2.0 * dw) / (1.0 + 2.0 * dw);
+        if (dw >= A(0.0) && upf) {
+          kw[q] = (A(1.0) - A(2.0) * dw) / (A(1.0) + A(2.0) * dw);
           val += kw[q] * (F[pq] - own[q]);
         }
       }
@@ -432,9 +453,10 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
     }
     // free-surface closures (forward, keeping what the reverse needs)
     Geo<R> G;
-    double dl[19], npl[19], et[19];
+    A dl[19], npl[19], et[19];
     bool fsl[19];
-    const double lp = p.lam_p, inv1 = p.inv_1plp;
+    const A lp = (A)p.lam_p, inv1 = (A)p.inv_1plp, dmin = (A)p.delta_min;
+    const A rhoG = SH ? (A)(p.rho_G - 1.0) : (A)p.rho_G;  // (deviation of the gas density)
     if (gasm) {
       geometry<R>(p, a.flags, a.phi, x, y, z, (R)phic, G);
 #pragma unroll
@@ -442,65 +464,66 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
         fsl[q] = false;
         if (!(gasm & (1u << q))) continue;
         const int pq = inv(q);
-        double eb = eplus_d(p, pq, p.rho_G, utx, uty, utz);
+        A eb = eplus_d<A>(p, pq, rhoG, utx, uty, utz);
         bool upf = !((wallm | gasm) & (1u << pq));
         if (p.rule == 0 || !upf) {
-          f[q] = -own[pq] + 2.0 * eb;
+          f[q] = -own[pq] + A(2.0) * eb;
         } else {
-          double d_ = 0.5;
+          A d_ = A(0.5);
           if (G.ok) {
-            double cn = cx(pq) * (double)G.n[0] + cy(pq) * (double)G.n[1] + cz(pq) * (double)G.n[2];
-            if (cn > 0.0) {
-              d_ = (double)G.d / cn;
-              d_ = d_ < p.delta_min ? p.delta_min : (d_ > 1.0 ? 1.0 : d_);
+            A cn = A(cx(pq)) * (A)G.n[0] + A(cy(pq)) * (A)G.n[1] + A(cz(pq)) * (A)G.n[2];
+            if (cn > A(0.0)) {
+              d_ = (A)G.d / cn;
+              d_ = d_ < dmin ? dmin : (d_ > A(1) ? A(1) : d_);
             }
           }
           dl[q] = d_;
-          et[q] = eplus_d(p, pq, rt, utx, uty, utz);
-          npl[q] = (0.5 * (own[pq] + own[q]) - et[q]) * inv1;
-          double C = lp * (0.5 + d_) - 2.0 * lp;
-          f[q] = (0.5 - d_) * own[pq] + 0.5 * own[q] + (d_ - 1.0) * F[pq] + C * npl[q] + eb;
+          et[q] = eplus_d<A>(p, pq, rt, utx, uty, utz);
+          npl[q] = (A(0.5) * (own[pq] + own[q]) - et[q]) * inv1;
+          A C = lp * (A(0.5) + d_) - A(2.0) * lp;
+          f[q] = (A(0.5) - d_) * own[pq] + A(0.5) * own[q] + (d_ - A(1.0)) * F[pq] + C * npl[q] + eb;
           fsl[q] = true;
         }
       }
     }
-    double rho1 = 0.0;
+    A rho1 = 0;
 #pragma unroll
     for (int q = 0; q < 19; ++q) rho1 += f[q];
+    const A rho1f = SH ? A(1) + rho1 : rho1;  // the density after the step
 
     // ---------------- reverse ----------------
-    double ab[19], fb[19], ob[19], Fb[19];
+    A ab[19], fb[19], ob[19], Fb[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
-      ab[q] = a.abar_in[q * N + i];
-      fb[q] = 0.0; ob[q] = 0.0; Fb[q] = 0.0;
+      ab[q] = (A)a.abar_in[q * N + i];
+      fb[q] = A(0.0); ob[q] = A(0.0); Fb[q] = A(0.0);
     }
-    double phib_self = 0.0, mb1 = 0.0, rho1b = 0.0;
+    A phib_self = A(0.0), mb1 = A(0.0), rho1b = A(0.0);
     if (dyn) {
-      const double m1 = a.m[i] + dm;
-      const double pb = a.phibar_in[i];
-      mb1 = a.mbar_in[i] + pb / rho1;
-      rho1b = -pb * m1 / (rho1 * rho1);
+      const A m1 = (A)a.m[i] + dm;
+      const A pb = (A)a.phibar_in[i];
+      mb1 = (A)a.mbar_in[i] + pb / rho1f;
+      rho1b = -pb * m1 / (rho1f * rho1f);
     } else if (ifc) {
-      phib_self += a.phibar_in[i];  // frozen interface: phi(t+1) = phi(t)
+      phib_self += (A)a.phibar_in[i];  // frozen interface: phi(t+1) = phi(t)
     }
-    collide_rev(p, f, ab, fb, th);
+    collide_rev<A>(p, f, ab, fb, th);
 #pragma unroll
     for (int q = 0; q < 19; ++q) fb[q] += rho1b;
-    a.mbar_out[i] = dyn ? mb1 : 0.0;
+    a.mbar_out[i] = dyn ? (double)mb1 : 0.0;
     if (dyn) {
-      const double dmb = mb1;
+      const A dmb = mb1;
 #pragma unroll
       for (int q = 1; q < 19; ++q) {
         if ((wallm | gasm) & (1u << q)) continue;
         uint8_t ks = a.flags[src[q]] & KIND;
-        double sw = (ks == LIQ) ? 1.0 : 0.5 * (phic + (double)a.phi[src[q]]);
+        A sw = (ks == LIQ) ? A(1.0) : A(0.5) * (phic + (A)a.phi[src[q]]);
         Fb[q] += sw * dmb;
         ob[inv(q)] -= sw * dmb;
         if (ks == IFC) {
-          double c = 0.5 * dmb * (F[q] - own[inv(q)]);
+          A c = A(0.5) * dmb * (F[q] - own[inv(q)]);
           phib_self += c;
-          atomicAdd(a.phibar_out + src[q], c);
+          atomicAdd(a.phibar_out + src[q], (double)c);
         }
       }
     }
@@ -510,52 +533,52 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
       if (!(wallm & (1u << q))) continue;
       const int pq = inv(q);
       ob[pq] += fb[q];
-      if (kw[q] != 0.0) {
+      if (kw[q] != A(0.0)) {
         Fb[pq] += kw[q] * fb[q];
         ob[q] -= kw[q] * fb[q];
       }
     }
     // free-surface closures
-    double utb[3] = {0, 0, 0}, rtb = 0.0;
-    double Hbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    A utb[3] = {0, 0, 0}, rtb = A(0.0);
+    A Hbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool geo_used = false;
-    double dbar = 0.0, nbar[3] = {0.0, 0.0, 0.0};  // plane-fit cells: adjoints of the offset and unit normal
+    A dbar = A(0.0), nbar[3] = {A(0.0), A(0.0), A(0.0)};  // plane-fit cells: adjoints of the offset and unit normal
     bool plic_used = false;
     if (gasm) {
 #pragma unroll
       for (int q = 1; q < 19; ++q) {
         if (!(gasm & (1u << q))) continue;
         const int pq = inv(q);
-        const double fbq = fb[q];
+        const A fbq = fb[q];
         if (!fsl[q]) {  // FSK: f_q = -f~_p + 2 e_p^+(rho_b, u_t)
           ob[pq] -= fbq;
-          deplus_du(p, pq, utx, uty, utz, 2.0 * fbq, utb);
+          deplus_du<A>(p, pq, utx, uty, utz, A(2.0) * fbq, utb);
           continue;
         }
-        const double d_ = dl[q];
-        ob[pq] += (0.5 - d_) * fbq;
-        ob[q] += 0.5 * fbq;
-        Fb[pq] += (d_ - 1.0) * fbq;
-        const double C = lp * (0.5 + d_) - 2.0 * lp;
-        th[0] += fbq * (d_ - 1.5) * npl[q];
-        deplus_du(p, pq, utx, uty, utz, fbq, utb);  // e_p^+(rho_b, u_t)
-        const double nb = C * fbq;
-        ob[pq] += 0.5 * nb * inv1;
-        ob[q] += 0.5 * nb * inv1;
-        const double etb = -nb * inv1;
-        rtb += (pq <= 6 ? 1.0 / 18.0 : 1.0 / 36.0) * etb;
-        deplus_du(p, pq, utx, uty, utz, etb, utb);
-        th[0] += -nb * (0.5 * (own[pq] + own[q]) - et[q]) * inv1 * inv1;
+        const A d_ = dl[q];
+        ob[pq] += (A(0.5) - d_) * fbq;
+        ob[q] += A(0.5) * fbq;
+        Fb[pq] += (d_ - A(1.0)) * fbq;
+        const A C = lp * (A(0.5) + d_) - A(2.0) * lp;
+        th[0] += fbq * (d_ - A(1.5)) * npl[q];
+        deplus_du<A>(p, pq, utx, uty, utz, fbq, utb);  // e_p^+(rho_b, u_t)
+        const A nb = C * fbq;
+        ob[pq] += A(0.5) * nb * inv1;
+        ob[q] += A(0.5) * nb * inv1;
+        const A etb = -nb * inv1;
+        rtb += (pq <= 6 ? A(1.0) / A(18.0) : A(1.0) / A(36.0)) * etb;
+        deplus_du<A>(p, pq, utx, uty, utz, etb, utb);
+        th[0] += -nb * (A(0.5) * (own[pq] + own[q]) - et[q]) * inv1 * inv1;
         // delta -> heights (closed height columns) or -> plane offset and
         // normal (plane fit), unclamped delta only
-        const double db = fbq * (-own[pq] + F[pq] + lp * npl[q]);
-        if (G.ok && !G.closed && db != 0.0) {
-          const double cn = cx(pq) * (double)G.n[0] + cy(pq) * (double)G.n[1] + cz(pq) * (double)G.n[2];
-          if (cn > 0.0) {
-            const double raw = (double)G.d / cn;
-            if (raw > p.delta_min && raw < 1.0) {  // delta = d / (n.c_p)
+        const A db = fbq * (-own[pq] + F[pq] + lp * npl[q]);
+        if (G.ok && !G.closed && db != A(0.0)) {
+          const A cn = A(cx(pq)) * (A)G.n[0] + A(cy(pq)) * (A)G.n[1] + A(cz(pq)) * (A)G.n[2];
+          if (cn > A(0.0)) {
+            const A raw = (A)G.d / cn;
+            if (raw > dmin && raw < A(1.0)) {  // delta = d / (n.c_p)
               dbar += db / cn;
-              const double t = -db * raw / cn;
+              const A t = -db * raw / cn;
               nbar[0] += t * cx(pq);
               nbar[1] += t * cy(pq);
               nbar[2] += t * cz(pq);
@@ -563,23 +586,23 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
             }
           }
         }
-        if (G.ok && G.closed && db != 0.0) {
-          const int A = G.a, B = G.b, Cc = 3 - G.a - G.b;
-          const int ca = A == 0 ? cx(pq) : (A == 1 ? cy(pq) : cz(pq));
+        if (G.ok && G.closed && db != A(0.0)) {
+          const int Ax = G.a, B = G.b, Cc = 3 - G.a - G.b;
+          const int ca = Ax == 0 ? cx(pq) : (Ax == 1 ? cy(pq) : cz(pq));
           const int cb = B == 0 ? cx(pq) : (B == 1 ? cy(pq) : cz(pq));
           const int cc = Cc == 0 ? cx(pq) : (Cc == 1 ? cy(pq) : cz(pq));
-          const double Hb = 0.5 * ((double)G.H[7] - (double)G.H[1]);
-          const double Hc = 0.5 * ((double)G.H[5] - (double)G.H[3]);
-          const double vc = G.s * ca - Hb * cb - Hc * cc;
-          if (vc > 0.0) {
-            const double raw = ((double)G.H[4] - 3.5) / vc;
-            if (raw > p.delta_min && raw < 1.0) {
-              const double hb_ = db * d_ * cb / vc, hc_ = db * d_ * cc / vc;
+          const A Hb = A(0.5) * ((A)G.H[7] - (A)G.H[1]);
+          const A Hc = A(0.5) * ((A)G.H[5] - (A)G.H[3]);
+          const A vc = G.s * ca - Hb * cb - Hc * cc;
+          if (vc > A(0.0)) {
+            const A raw = ((A)G.H[4] - A(3.5)) / vc;
+            if (raw > dmin && raw < A(1.0)) {
+              const A hb_ = db * d_ * cb / vc, hc_ = db * d_ * cc / vc;
               Hbar[4] += db / vc;
-              Hbar[7] += 0.5 * hb_;
-              Hbar[1] -= 0.5 * hb_;
-              Hbar[5] += 0.5 * hc_;
-              Hbar[3] -= 0.5 * hc_;
+              Hbar[7] += A(0.5) * hb_;
+              Hbar[1] -= A(0.5) * hb_;
+              Hbar[5] += A(0.5) * hc_;
+              Hbar[3] -= A(0.5) * hc_;
               geo_used = true;
             }
           }
@@ -591,39 +614,41 @@ __global__ void __launch_bounds__(128) k_adj_local(Par p, AdjView<P> a) {
       if (!((wallm | gasm) & (1u << q))) Fb[q] += fb[q];
     ob[0] += fb[0];
     if (geo_used) {
-      const int A = G.a, B = G.b;
+      const int Ax = G.a, B = G.b;
       for (int ib = -1; ib <= 1; ++ib)
         for (int ic = -1; ic <= 1; ++ic) {
-          const double hb = Hbar[(ib + 1) * 3 + (ic + 1)];
-          if (hb == 0.0) continue;
+          const A hb = Hbar[(ib + 1) * 3 + (ic + 1)];
+          if (hb == A(0.0)) continue;
           for (int k = -3; k <= 3; ++k) {
-            int o0 = (A == 0) ? k : ((B == 0) ? ib : ic);
-            int o1 = (A == 1) ? k : ((B == 1) ? ib : ic);
-            int o2 = (A == 2) ? k : ((B == 2) ? ib : ic);
+            int o0 = (Ax == 0) ? k : ((B == 0) ? ib : ic);
+            int o1 = (Ax == 1) ? k : ((B == 1) ? ib : ic);
+            int o2 = (Ax == 2) ? k : ((B == 2) ? ib : ic);
             long long j = nbr(p, x, y, z, o0, o1, o2);
             uint8_t kj = kind_at(a.flags, j);
             if (kj == IFC || (kj == GAS && p.freeze)) {
               if (j == i) phib_self += hb;
-              else atomicAdd(a.phibar_out + j, hb);
+              else atomicAdd(a.phibar_out + j, (double)hb);
             }
           }
         }
     }
-    if (plic_used)
-      phib_self += plane_fit_adjoint(p, a.flags, a.phi, a.phibar_out, x, y, z, phic, (double)G.n[0],
-                                     (double)G.n[1], (double)G.n[2], (double)G.d, dbar, nbar);
+    if (plic_used) {
+      const double nbd[3] = {(double)nbar[0], (double)nbar[1], (double)nbar[2]};
+      phib_self += (A)plane_fit_adjoint(p, a.flags, a.phi, a.phibar_out, x, y, z, (double)phic, (double)G.n[0],
+                                        (double)G.n[1], (double)G.n[2], (double)G.d, (double)dbar, nbd);
+    }
     // own moments: rho_t = sum f~, u_t = sum c f~ - g/2
 #pragma unroll
     for (int q = 0; q < 19; ++q) ob[q] += rtb + cx(q) * utb[0] + cy(q) * utb[1] + cz(q) * utb[2];
-    th[2] -= 0.5 * utb[0];
-    th[3] -= 0.5 * utb[1];
-    th[4] -= 0.5 * utb[2];
+    th[2] -= A(0.5) * utb[0];
+    th[3] -= A(0.5) * utb[1];
+    th[4] -= A(0.5) * utb[2];
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
-      a.abar_out[q * N + i] = ob[q];
-      a.Pb[q * N + i] = Fb[q];
+      a.abar_out[q * N + i] = (double)ob[q];
+      a.Pb[q * N + i] = (double)Fb[q];
     }
-    if (phib_self != 0.0) atomicAdd(a.phibar_out + i, phib_self);
+    if (phib_self != A(0)) atomicAdd(a.phibar_out + i, (double)phib_self);
   }
   warp_add(th, a.theta);
 }
@@ -947,10 +972,24 @@ static void launch_local(const Par& p, AdjView<P> a, const CellLists& L0, cudaSt
   if (lb > 152 * 8) lb = 152 * 8;
   a.flist = L0.liq;
   a.nfl = L0.cnt;
-  k_adj_local<P, false><<<lb, 128, 0, st>>>(p, a);
-  a.flist = L0.ifc;
-  a.nfl = L0.cnt + 1;
-  k_adj_local<P, true><<<lb, 128, 0, st>>>(p, a);
+  if constexpr (P != P64) {
+    if (p.adj32) {
+      k_adj_local<P, false, float><<<lb, 128, 0, st>>>(p, a);
+      a.flist = L0.ifc;
+      a.nfl = L0.cnt + 1;
+      k_adj_local<P, true, float><<<lb, 128, 0, st>>>(p, a);
+    } else {
+      k_adj_local<P, false, double><<<lb, 128, 0, st>>>(p, a);
+      a.flist = L0.ifc;
+      a.nfl = L0.cnt + 1;
+      k_adj_local<P, true, double><<<lb, 128, 0, st>>>(p, a);
+    }
+  } else {
+    k_adj_local<P, false, double><<<lb, 128, 0, st>>>(p, a);
+    a.flist = L0.ifc;
+    a.nfl = L0.cnt + 1;
+    k_adj_local<P, true, double><<<lb, 128, 0, st>>>(p, a);
+  }
   int gb = (int)((p.N + 127) / 128);
   if (gb > 152 * 16) gb = 152 * 16;
   k_adj_gather<P><<<gb, 128, 0, st>>>(p, a.flags, a.Pb, a.abar_out, L0.liq, L0.ifc, L0.cnt);

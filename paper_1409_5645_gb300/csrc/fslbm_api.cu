@@ -109,6 +109,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   if (q.recon_nc < 0 || q.recon_nc > 1) return FSLBM_ERR_ARG;
   if (q.excess_split < 0 || q.excess_split > 1) return FSLBM_ERR_ARG;
   if (q.elvira < 0 || q.elvira > 1) return FSLBM_ERR_ARG;
+  if (q.adjoint_fp32 < 0 || q.adjoint_fp32 > 1) return FSLBM_ERR_ARG;
   if (q.compressible && (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0)) return FSLBM_ERR_ARG;
 
   fslbm* h = (fslbm*)calloc(1, sizeof(fslbm));
@@ -163,6 +164,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   }
   p.owned_all = 1;
   p.elvira = q.elvira;
+  p.adj32 = q.adjoint_fp32 && q.precision != FSLBM_F64;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;

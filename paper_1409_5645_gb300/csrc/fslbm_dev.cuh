@@ -156,6 +156,7 @@ struct Par {
   int own_lo[3], own_hi[3];
   int owned_all;
   int elvira;              // 1: ELVIRA normal where the height columns are open
+  int adj32;               // 1: the adjoint's reverse step in FP32 (FP32/FP16 lattices)
 };
 
 __device__ __forceinline__ bool owned(const Par& p, int x, int y, int z) {

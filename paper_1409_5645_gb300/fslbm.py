@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("stress", C.c_int), ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
                 ("ub_extrap", C.c_int), ("recon_nc", C.c_int), ("excess_split", C.c_int),
                 ("bulk_loads", C.c_int), ("precision", C.c_int),
-                ("stream", C.c_void_p), ("elvira", C.c_int)]
+                ("stream", C.c_void_p), ("elvira", C.c_int), ("adjoint_fp32", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -203,6 +203,7 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     P.stream = stream
     P.elvira = int(params.get("elvira", 0))
+    P.adjoint_fp32 = int(params.get("adjoint_fp32", 0))
     return P
 
 

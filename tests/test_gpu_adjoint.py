@@ -21,8 +21,8 @@ def _J_gpu(case, steps, precision="f64", **override):
     return g.adjoint_forward(steps, K=max(1, steps // 4))
 
 
-def _grad_gpu(case, steps, K, precision="f64", keep_f0=0):
-    g = fslbm.Lattice.from_case(case, precision=precision, keep_f0=keep_f0)
+def _grad_gpu(case, steps, K, precision="f64", keep_f0=0, **kw):
+    g = fslbm.Lattice.from_case(case, precision=precision, keep_f0=keep_f0, **kw)
     J = g.adjoint_forward(steps, K)
     dnu, dg, dphi = g.adjoint_backward()
     stats = g.adjoint_stats()
@@ -155,6 +155,51 @@ def test_adjoint_fp32_against_fp64():
     # the per-cell fill gradients rest on small differences of populations;
     # FP32 (storing f - w_q) carries them to a few percent of the largest
     assert e_phi < 0.1
+
+
+def test_adjoint_fp32_arithmetic():
+    """The reverse step in FP32 arithmetic (adjoint_fp32 = 1; it works in the
+    deviations f - w_q as the forward step does) on the FP32 trajectory of
+    the g = 1e-4 film: against the FP64 reverse step of the same trajectory
+    (what the arithmetic alone changes) and against the FP64 lattice.
+    dJ/dg and dJ/dphi0 keep 3e-6 and 2e-3; dJ/dnu loses about 1e-2 here: it
+    is 3 (dJ/dlambda_+ dlambda_+/dtau + dJ/dlambda_- dlambda_-/dtau), two
+    sums over every cell and step of non-equilibrium parts (differences of
+    populations of order |u|) times adjoints, which cancel to a small
+    remainder on this film, so their FP32 rounding shows in it (the default
+    FP64 reverse arithmetic keeps it to 7e-4 against the FP64 lattice)."""
+    c = cases.adjoint_film(nz=48, h=30.0, gx=1e-4)
+    _, d64, g64, p64, _ = _grad_gpu(c, 300, K=100, precision="f64", keep_f0=1)
+    _, d32, g32, p32, _ = _grad_gpu(c, 300, K=100, precision="f32", keep_f0=1)
+    _, da, ga, pa, _ = _grad_gpu(c, 300, K=100, precision="f32", keep_f0=1, adjoint_fp32=1)
+    ifc = c["flags"] == cases.INTERFACE
+    a_nu, a_g = abs(da - d32) / abs(d32), abs(ga[0] - g32[0]) / abs(g32[0])
+    a_phi = np.abs(pa[ifc] - p32[ifc]).max() / np.abs(p32[ifc]).max()
+    e_nu, e_g = abs(da - d64) / abs(d64), abs(ga[0] - g64[0]) / abs(g64[0])
+    e_phi = np.abs(pa[ifc] - p64[ifc]).max() / np.abs(p64[ifc]).max()
+    print(f"FP32 reverse arithmetic vs FP64 reverse (same FP32 trajectory): nu {a_nu:.2e}, g {a_g:.2e}, "
+          f"phi0 {a_phi:.2e}; vs the FP64 lattice: nu {e_nu:.2e}, g {e_g:.2e}, phi0 {e_phi:.2e}")
+    assert a_g < 3e-5 and a_nu < 5e-2 and a_phi < 2e-2
+    assert e_g < 3e-5 and e_nu < 5e-2 and e_phi < 0.1
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_adjoint_fp32_arithmetic_through_conversions(rule):
+    """FP32 reverse arithmetic on the dam-break miniature with conversions
+    (FP32 lattice, 200 steps, 800 conversions): against the FP64 reverse step
+    of the same trajectory, about 1e-6 in nu, g_z and the fill levels (under
+    FSK no population depends on a fill level, and both give dJ/dphi0 = 0)."""
+    c = _dam(rule)
+    _, d, g, ph, _ = _grad_gpu(c, 200, K=60, precision="f32")
+    _, da, ga, pa, _ = _grad_gpu(c, 200, K=60, precision="f32", adjoint_fp32=1)
+    ifc = c["flags"] == cases.INTERFACE
+    e_nu, e_g = abs(da - d) / abs(d), abs(ga[2] - g[2]) / abs(g[2])
+    scale = max(np.abs(ph[ifc]).max(), 1e-300)
+    e_phi = np.abs(pa[ifc] - ph[ifc]).max() / scale
+    print(f"rule {rule}: FP32 vs FP64 reverse arithmetic: nu {e_nu:.2e}, g_z {e_g:.2e}, phi0 {e_phi:.2e} "
+          f"(max |dJ/dphi0| {np.abs(ph[ifc]).max():.2e})")
+    assert e_nu < 1e-5 and e_g < 1e-5
+    assert np.abs(pa[ifc] - ph[ifc]).max() <= 1e-4 * scale
 
 
 def test_autograd_function_matches_c_interface():
