@@ -69,7 +69,8 @@ enum fslbm_status {
   FSLBM_ERR_OOM = -2,      /* device allocation failed */
   FSLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
   FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
-  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density */
+  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density, or a cell velocity above 0.4
+                              lattice units (the stability guard of the step) */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
   FSLBM_ERR_TIMEOUT = -7,  /* a bounded device-side wait expired (staged loads of the bulk kernel, the
                               grid barrier of the conversion kernel) */

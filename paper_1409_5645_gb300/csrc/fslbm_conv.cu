@@ -117,12 +117,13 @@ __device__ __forceinline__ void do_newg(const Par& p, const View<P>& v) {
     R rr = R(0), ux = R(0), uy = R(0), uz = R(0);
     if (lane >= 1 && lane < 19) {
       long long y2 = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      use = y2 >= 0 && is_fluid(v.flags[y2] & KIND);
-      if (use) {
+      if (y2 >= 0) {
+        // the populations are loaded beside the flag (a gas cell's are read and dropped)
         R g[19];
 #pragma unroll
         for (int r = 0; r < 19; ++r) g[r] = ldq<P>(v.fout, (size_t)r * N + (size_t)y2, r);
-        moments_post<R, Form<P>::SH>(p, g, rr, ux, uy, uz);
+        use = is_fluid(v.flags[y2] & KIND);
+        if (use) moments_post<R, Form<P>::SH>(p, g, rr, ux, uy, uz);
       }
     }
     R rs = R(0), s0 = R(0), s1 = R(0), s2 = R(0);
@@ -256,6 +257,12 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
     if (!isF && !(v.mark[i] & MK_EMPTY)) continue;  // warp-uniform
     int x, y, z;
     coords(p, i, x, y, z);
+    // lane 0: the cell's density and mass, loaded beside the neighbour tests
+    double rho = 0.0, mi = 0.0;
+    if (lane == 0) {
+      rho = rho_out<P>(p, v, i);
+      mi = v.m[i];
+    }
     bool recv = false;
     long long j = -1;
     if (q) {
@@ -276,8 +283,7 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
       for (int s = 1; s < 19; ++s) V += __shfl_sync(FULL, w, s);
     }
     if (lane == 0) {
-      const double rho = rho_out<P>(p, v, i);
-      const double ex = isF ? v.m[i] - rho : v.m[i];
+      const double ex = isF ? mi - rho : mi;
       const int nr = __popc(rm);
       if (nr == 0) {
         if (owned(p, x, y, z)) atomicAdd(v.lost, ex);  // (a ghost cell's owner books it)
@@ -327,6 +333,10 @@ __device__ __forceinline__ void do_recv(const Par& p, const View<P>& v) {
     int x, y, z;
     coords(p, yj, x, y, z);
     const bool in1 = x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1;
+    // the receiver's own mass and density first: their loads overlap the
+    // neighbours' marks and shares
+    const double m0 = v.m[yj];
+    const double rho = p.excess_split ? 1.0 : rho_out<P>(p, v, yj);
     double acc = 0.0;
 #pragma unroll
     for (int q = 1; q < 19; ++q) {
@@ -343,12 +353,12 @@ __device__ __forceinline__ void do_recv(const Par& p, const View<P>& v) {
         }
       }
     }
-    const double mm = v.m[yj] + acc;
+    const double mm = m0 + acc;
     v.m[yj] = mm;
     // (the weighted split reads the fill levels of interface cells here, so
     // its receivers take their new fill level in k_final)
     if (!p.excess_split) {
-      v.phout[yj] = (R)(mm / rho_out<P>(p, v, yj));
+      v.phout[yj] = (R)(mm / rho);
     }
   }
 }

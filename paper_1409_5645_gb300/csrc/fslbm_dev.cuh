@@ -43,7 +43,7 @@ __host__ __device__ constexpr R wq(int q) {
 // beyond a non-periodic face); NEARW a neighbour is a WALL cell of the lattice
 enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16, NEARW = 32, STATIC_BITS = 48 };
 enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_WSPLIT = 32 };
-enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8, ERRB_SYNC = 16 };
+enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8, ERRB_SYNC = 16, ERRB_SPEED = 32 };
 
 // ---------------------------------------------------------------------------
 // Precision forms
@@ -105,6 +105,13 @@ __device__ __forceinline__ double rho_full(R r) {
 template <bool SH, class R>
 __device__ __forceinline__ R rho_full_r(R r) {
   return SH ? R(1) + r : r;
+}
+// stability guard on a cell's velocity: |u| above 0.4 lattice units (the
+// equilibria are second order in u, and the lattice's speed of sound is
+// 1/sqrt(3) ~ 0.58)
+template <class R>
+__device__ __forceinline__ bool speed_bad(R ux, R uy, R uz) {
+  return ux * ux + uy * uy + uz * uz > R(0.16);
 }
 // instability test of a density given as a sum in the arithmetic type
 template <bool SH, class R>

@@ -103,7 +103,8 @@ struct PairWord<P32> {
 // (add/mul/fma.rn.f32x2): every operation of the scalar collision, in the same
 // order and with the same rounding, on the pair (lo, hi), so each half equals
 // the scalar result bit for bit while the pair costs one instruction per
-// operation.  On return rho holds sum f (minus 1: the stored deviations).
+// operation.  On return rho holds sum f (minus 1: the stored deviations) and
+// usq_out |u|^2 of the pre-collision state.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -125,7 +126,7 @@ __device__ __forceinline__ float2 cdot2(float2 ux, float2 uy, float2 uz) {
 }
 
 template <bool SH>
-__device__ __forceinline__ void collide_x2(const Par& p, float2 (&f)[19], float2& rho) {
+__device__ __forceinline__ void collide_x2(const Par& p, float2 (&f)[19], float2& rho, float2& usq_out) {
   float2 r = f[0], jx = bc2(0.f), jy = bc2(0.f), jz = bc2(0.f);
 #pragma unroll
   for (int q = 1; q < 19; ++q) r = add2(r, f[q]);
@@ -180,6 +181,7 @@ __device__ __forceinline__ void collide_x2(const Par& p, float2 (&f)[19], float2
 #pragma unroll
   for (int q = 0; q < 19; ++q) f[q] = out[q];
   rho = r;
+  usq_out = usq;
 }
 
 // Interface cells of the lanes' pairs into a list in x order (the even cell
@@ -261,6 +263,7 @@ __device__ __noinline__ double slow_cell(const Par& p, const View<P>& v, long lo
   R rho, ux, uy, uz;
   collide<R, SH>(p, f, rho, ux, uy, uz);
   if (rho_bad<SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
+  if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #pragma unroll
   for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
   return owned(p, x, y, z) ? rho_full<SH>(rho) : 0.0;
@@ -357,9 +360,10 @@ __global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, Vi
         float2 f[19];
 #pragma unroll
         for (int q = 0; q < 19; ++q) f[q] = PW::unpack(w[q]);
-        float2 rho;
-        collide_x2<SH>(p, f, rho);
+        float2 rho, usq;
+        collide_x2<SH>(p, f, rho, usq);
         if ((la && rho_bad<SH>(rho.x)) || (lb && rho_bad<SH>(rho.y))) atomicOr(v.err, ERRB_UNSTABLE);
+        if ((la && usq.x > 0.16f) || (lb && usq.y > 0.16f)) atomicOr(v.err, ERRB_SPEED);  // (speed_bad)
         if (la && owned(p, xa, y, z)) msum += rho_full<SH>(rho.x);
         if (lb && owned(p, xa + 1, y, z)) msum += rho_full<SH>(rho.y);
 #pragma unroll

@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     R rho, ux, uy, uz;
     collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
     if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
+    if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
     FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
       R rho, ux, uy, uz;
       collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
       if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
+      if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
       FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
       FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)

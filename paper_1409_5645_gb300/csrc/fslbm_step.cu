@@ -68,12 +68,15 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
       const uint4* v4 = reinterpret_cast<const uint4*>(base);
       const uint4 a = __ldg(v4), b = __ldg(v4 + 1);
       const unsigned w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      // the masks only for segments holding fluid (most of a lattice is gas)
+      if (((a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) & 0x03030303u) != 0u) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        liq |= byte_bits(w[k], 0) << (4 * k);
-        ifc |= byte_bits(w[k], 1) << (4 * k);
-        nearb |= byte_bits(w[k], 4) << (4 * k);
-        nearw |= byte_bits(w[k], 5) << (4 * k);
+        for (int k = 0; k < 8; ++k) {
+          liq |= byte_bits(w[k], 0) << (4 * k);
+          ifc |= byte_bits(w[k], 1) << (4 * k);
+          nearb |= byte_bits(w[k], 4) << (4 * k);
+          nearw |= byte_bits(w[k], 5) << (4 * k);
+        }
       }
     } else {
       for (int k = 0; k < len; ++k) {
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
     R rho, ux, uy, uz;
     collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
     if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
+    if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
     FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
@@ -376,6 +380,7 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
   R rho, ux, uy, uz;
   collide<R, SH>(p, f, rho, ux, uy, uz);
   if (rho_bad<SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
+  if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #pragma unroll
   for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
   double mm = v.m[i];
