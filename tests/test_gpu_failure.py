@@ -1,7 +1,8 @@
 """Failure detection by host-side injection (no GPU fault, no device trap): a
 state that breaks an invariant of the step, or the step's stability guard,
-makes the library return its error code; setting a valid state afterwards
-clears the error word and the same handle steps on."""
+makes the library return its error code at the next synchronising call (the
+step itself is asynchronous); setting a valid state afterwards clears the
+error word and the same handle steps on."""
 import numpy as np
 import pytest
 
@@ -30,14 +31,17 @@ def test_speed_guard(precision, loads):
     u[:, 0] = 0.35
     lat.init_equilibrium(flags, rho, u, phi)
     lat.step(3)
+    lat.sync()
     u[:, 0] = 0.45
     lat.init_equilibrium(flags, rho, u, phi)
     with pytest.raises(fslbm.FslbmError) as e:
         lat.step(1)
+        lat.sync()
     assert e.value.code == ERR_UNSTABLE and "velocity" in str(e.value)
     u[:] = 0.0
     lat.init_equilibrium(flags, rho, u, phi)
     lat.step(2)
+    lat.sync()
     lat.close()
 
 
@@ -50,30 +54,34 @@ def test_non_finite_density(precision):
     lat.init_equilibrium(flags, rho, u, phi)
     with pytest.raises(fslbm.FslbmError) as e:
         lat.step(1)
+        lat.sync()
     assert e.value.code == ERR_UNSTABLE and "density" in str(e.value)
     rho[123] = 1.0
     lat.init_equilibrium(flags, rho, u, phi)
     lat.step(1)
+    lat.sync()
     lat.close()
 
 
 def test_liquid_next_to_gas_and_bad_flag():
     """Setting a state with a liquid cell next to a gas cell, or a flag that
-    is no cell kind, returns ERR_STATE."""
+    is no cell kind, returns ERR_STATE (checked when the state is set, before
+    any step runs on it)."""
     dims, params, flags, rho, u, phi = _liquid_box()
     lat = fslbm.Lattice(dims, params)
     bad = flags.copy()
     bad[200] = cases.GAS
     with pytest.raises(fslbm.FslbmError) as e:
         lat.init_equilibrium(bad, rho, u, phi)
-        lat.step(1)
+        lat.sync()
     assert e.value.code == ERR_STATE
     bad = flags.copy()
     bad[7] = 3  # two kinds at once
     with pytest.raises(fslbm.FslbmError) as e:
         lat.init_equilibrium(bad, rho, u, phi)
-        lat.step(1)
+        lat.sync()
     assert e.value.code == ERR_STATE
     lat.init_equilibrium(flags, rho, u, phi)
     lat.step(1)
+    lat.sync()
     lat.close()
