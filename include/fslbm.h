@@ -69,8 +69,8 @@ enum fslbm_status {
   FSLBM_ERR_OOM = -2,      /* device allocation failed */
   FSLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
   FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
-  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density, or a cell velocity above 0.4
-                              lattice units (the stability guard of the step) */
+  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density, or a cell velocity above
+                              u_max (the stability guard of the step) */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
   FSLBM_ERR_TIMEOUT = -7,  /* a bounded device-side wait expired (staged loads of the bulk kernel, the
                               grid barrier of the conversion kernel) */
@@ -178,6 +178,9 @@ typedef struct {
                          memory); 0 (default): in FP64.  An implementation choice: GB300 runs FP64
                          at a small fraction of its FP32 rate, and the reverse step is bound by it.
                          Ignored by FP64 lattices */
+  double u_max;       /* stability guard: a step in which a cell's velocity exceeds u_max lattice
+                         units reports FSLBM_ERR_UNSTABLE (the equilibria are second order in u, and
+                         the lattice speed of sound is 1/sqrt(3)); default 0.4, 0 switches it off */
 } fslbm_params;
 
 /* Defaults: tau 0.8, magic 3/16, g 0, rho_G 1, sigma 0, FSL, rho_0 = 1,

@@ -58,6 +58,12 @@ static void drop_events(fslbm* h) {
 
 static void free_all(fslbm* h) {
   drop_events(h);
+  if (h->forked) {
+    cudaEventDestroy(h->fork.fork);
+    cudaEventDestroy(h->fork.join);
+    cudaStreamDestroy(h->fork.side);
+    h->forked = 0;
+  }
   void* ptrs[] = {h->flags, h->mark, h->fA, h->fB, h->m, h->phiA, h->phiB, h->wd, h->cnt, h->share, h->geo,
                   h->partials, h->red, h->lost, h->err, h->step_mass, h->total_out, h->f0, h->seglist};
   for (void* p : ptrs)
@@ -90,6 +96,7 @@ extern "C" void fslbm_default_params(fslbm_params* p) {
   p->cleanup = 3;
   p->keep_f0 = 0;
   p->precision = FSLBM_F64;
+  p->u_max = 0.4;
 }
 
 extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
@@ -110,6 +117,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   if (q.excess_split < 0 || q.excess_split > 1) return FSLBM_ERR_ARG;
   if (q.elvira < 0 || q.elvira > 1) return FSLBM_ERR_ARG;
   if (q.adjoint_fp32 < 0 || q.adjoint_fp32 > 1) return FSLBM_ERR_ARG;
+  if (!(q.u_max >= 0.0)) return FSLBM_ERR_ARG;
   if (q.compressible && (q.wall_u[0] != 0.0 || q.wall_u[1] != 0.0 || q.wall_u[2] != 0.0)) return FSLBM_ERR_ARG;
 
   fslbm* h = (fslbm*)calloc(1, sizeof(fslbm));
@@ -165,6 +173,7 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   p.owned_all = 1;
   p.elvira = q.elvira;
   p.adj32 = q.adjoint_fp32 && q.precision != FSLBM_F64;
+  p.umax2 = q.u_max * q.u_max;
 
   const size_t Nn = (size_t)N, N4 = (Nn + 3) & ~(size_t)3;
   h->cap = (int)N;
@@ -229,6 +238,14 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
       free(h->tmap);
       h->tmap = nullptr;
     }
+  }
+  // the side stream of the interface geometry (it runs beside the bulk kernel)
+  if (cudaStreamCreateWithFlags(&h->fork.side, cudaStreamNonBlocking) == cudaSuccess) {
+    if (cudaEventCreateWithFlags(&h->fork.fork, cudaEventDisableTiming) == cudaSuccess) {
+      if (cudaEventCreateWithFlags(&h->fork.join, cudaEventDisableTiming) == cudaSuccess) h->forked = 1;
+      else cudaEventDestroy(h->fork.fork);
+    }
+    if (!h->forked) cudaStreamDestroy(h->fork.side);
   }
   if (cudaStreamSynchronize(h->st) != cudaSuccess) {
     free_all(h);
@@ -339,7 +356,7 @@ static int read_err(fslbm* h) {
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   if (e & ERRB_STATE) return fail(h, FSLBM_ERR_STATE, "invariant violated: a liquid cell touches gas, or a bad flag");
   if (e & ERRB_UNSTABLE) return fail(h, FSLBM_ERR_UNSTABLE, "non-finite or non-positive density");
-  if (e & ERRB_SPEED) return fail(h, FSLBM_ERR_UNSTABLE, "a cell velocity above 0.4 lattice units");
+  if (e & ERRB_SPEED) return fail(h, FSLBM_ERR_UNSTABLE, "a cell velocity above u_max");
   if (e & ERRB_OVERFLOW) return fail(h, FSLBM_ERR_OVERFLOW, "conversion list overflow");
   if (e & ERRB_TMA) return fail(h, FSLBM_ERR_TIMEOUT, "staged loads of the bulk kernel failed (bounded wait expired)");
   if (e & ERRB_SYNC) return fail(h, FSLBM_ERR_TIMEOUT, "grid barrier of the conversion kernel expired");
@@ -470,7 +487,8 @@ static int step_t(fslbm* h) {
   View<P> v = make_view<P>(h);
   if (launch_reset(h->cnt, h->st)) return 1;
   if (launch_step_kernels<P>(h->par, v, h->st, h->bulk_blocks, h->iface_blocks, h->seglist, h->cnt + 9,
-                             h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr))
+                             h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr,
+                             h->forked ? &h->fork : nullptr))
     return 1;
   if (mark_event(h, 2)) return 1;
   // the mass reduction rides in the cooperative conversion kernel where that runs

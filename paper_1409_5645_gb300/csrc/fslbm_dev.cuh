@@ -106,13 +106,6 @@ template <bool SH, class R>
 __device__ __forceinline__ R rho_full_r(R r) {
   return SH ? R(1) + r : r;
 }
-// stability guard on a cell's velocity: |u| above 0.4 lattice units (the
-// equilibria are second order in u, and the lattice's speed of sound is
-// 1/sqrt(3) ~ 0.58)
-template <class R>
-__device__ __forceinline__ bool speed_bad(R ux, R uy, R uz) {
-  return ux * ux + uy * uy + uz * uz > R(0.16);
-}
 // instability test of a density given as a sum in the arithmetic type
 template <bool SH, class R>
 __device__ __forceinline__ bool rho_bad(R r) {
@@ -164,8 +157,16 @@ struct Par {
   int owned_all;
   int elvira;              // 1: ELVIRA normal where the height columns are open
   int adj32;               // 1: the adjoint's reverse step in FP32 (FP32/FP16 lattices)
+  double umax2;            // stability guard: |u|^2 above it is an error (0: off)
 };
 
+// stability guard on a cell's velocity: |u| above u_max (0.4 lattice units
+// by default: the equilibria are second order in u, and the lattice's speed
+// of sound is 1/sqrt(3) ~ 0.58); umax2 = u_max^2, 0 switches it off
+template <class R>
+__device__ __forceinline__ bool speed_bad(const Par& p, R ux, R uy, R uz) {
+  return p.umax2 > 0.0 && ux * ux + uy * uy + uz * uz > R(p.umax2);
+}
 __device__ __forceinline__ bool owned(const Par& p, int x, int y, int z) {
   return p.owned_all || ((unsigned)(x - p.own_lo[0]) < (unsigned)(p.own_hi[0] - p.own_lo[0]) &&
                          (unsigned)(y - p.own_lo[1]) < (unsigned)(p.own_hi[1] - p.own_lo[1]) &&

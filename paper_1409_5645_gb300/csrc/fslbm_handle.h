@@ -7,6 +7,7 @@
 
 #include "fslbm.h"
 #include "fslbm_dev.cuh"
+#include "fslbm_kernels.h"
 
 struct AdjointState;
 struct fslbm;
@@ -52,6 +53,8 @@ struct fslbm {
   int f0_valid;       // f0 holds the populations of the current initial state
   int bulk_mode;      // fsl::BulkMode of the bulk kernel
   CUtensorMap* tmap;  // [2] tensor maps of fA and fB for the TMA bulk kernel (64-byte aligned), or NULL
+  fsl::Fork fork;     // the side stream of the interface geometry and its two events
+  int forked;         // fork holds a stream and events
 };
 
 

@@ -42,11 +42,20 @@ int launch_reset(int* cnt, cudaStream_t st);
 // how the bulk kernel reaches its pulled values (fslbm_bulk_loads)
 enum BulkMode { BULK_PLAIN = 0, BULK_TMA = 1, BULK_ASYNC = 2, BULK_PAIRS = 3 };
 
+// a second stream of the handle and two events: the interface geometry runs
+// on it beside the bulk kernel (fork after the segment scan, join before the
+// interface kernel)
+struct Fork {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+
 // bulk_mode: BulkMode (FP32/FP16 only for the staged modes); tmap: tensor map
-// of v.fin for BULK_TMA
+// of v.fin for BULK_TMA; fork: NULL to run every kernel on st
 template <int P>
 int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
-                        int* seglist, int* segcount, void* timing_handle, int bulk_mode, const CUtensorMap* tmap);
+                        int* seglist, int* segcount, void* timing_handle, int bulk_mode, const CUtensorMap* tmap,
+                        const Fork* fork);
 
 // staged bulk kernels (fslbm_staged.cu): TMA shape test, tensor map of a
 // population buffer, launchers

@@ -2,9 +2,9 @@
 //
 // k_bulk_pairs does the work of k_bulk (liquid cells of the fluid-segment
 // list, Eq. lbe1 pull with half-way bounce-back at non-periodic faces,
-// Eq. lbe2 collision, interface cells compacted into a list, per-warp FP64
-// partial sums of the liquid density) with the same arithmetic per cell, so
-// the populations, flags and lists it produces equal k_bulk's bit for bit.
+// Eq. lbe2 collision, per-warp FP64 partial sums of the liquid density) with
+// the same arithmetic per cell, so the populations it produces equal
+// k_bulk's bit for bit.
 // It differs in how the pulled values reach the lanes: each half-warp takes
 // one 32-cell segment of the list, and lane l of it the cells x0 + 2l and
 // x0 + 2l + 1, whose values of one population sit in one aligned word of a
@@ -184,29 +184,6 @@ __device__ __forceinline__ void collide_x2(const Par& p, float2 (&f)[19], float2
   usq_out = usq;
 }
 
-// Interface cells of the lanes' pairs into a list in x order (the even cell
-// before the odd one, the lanes in order), so that the interface kernels see
-// the cells as k_bulk lists them: back = false fills list[k] upward (count
-// *count), back = true list[cap - 1 - k].  All 32 lanes call it.
-__device__ __forceinline__ void append_pair(bool pa, bool pb, int ia, int* list, int* count, int cap, int* err,
-                                            bool back) {
-  const unsigned ba = __ballot_sync(FULL, pa), bb = __ballot_sync(FULL, pb);
-  if (!(ba | bb)) return;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  int base = 0;
-  if (lane == 0) base = atomicAdd(count, __popc(ba) + __popc(bb));
-  base = __shfl_sync(FULL, base, 0);
-  const int k = base + __popc(ba & lt) + __popc(bb & lt);
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    if (!(c == 0 ? pa : pb)) continue;
-    const int kk = k + (c == 1 && pa ? 1 : 0);
-    if (kk < cap) list[back ? cap - 1 - kk : kk] = ia + c;
-    else atomicOr(err, ERRB_OVERFLOW);
-  }
-}
-
 // k_bulk's test for a liquid cell whose sources are plain offsets or lie
 // beyond a non-periodic face (bounce-back from its own slots)
 __device__ __forceinline__ bool fast_cell(const Par& p, uint8_t fl, int x, int y, int z) {
@@ -263,7 +240,7 @@ __device__ __noinline__ double slow_cell(const Par& p, const View<P>& v, long lo
   R rho, ux, uy, uz;
   collide<R, SH>(p, f, rho, ux, uy, uz);
   if (rho_bad<SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
-  if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
+  if (speed_bad(p, ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #pragma unroll
   for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
   return owned(p, x, y, z) ? rho_full<SH>(rho) : 0.0;
@@ -337,14 +314,7 @@ __global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, Vi
     const int x0 = sd.x, y = sd.y, z = sd.z;
     const long long ia = (long long)sd.w + 2 * hl;  // the even cell of the pair
     const int xa = x0 + 2 * hl;
-    const unsigned bits = act ? (sm.x >> (2 * hl)) & 3u : 0u, ibits = act ? (sm.y >> (2 * hl)) & 3u : 0u;
-    {  // interface cells: those whose stencil (every cell within 3) lies inside to the front
-      const bool yz3 = y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
-      const bool in3a = yz3 && xa >= 3 && xa < p.nx - 3, in3b = yz3 && xa + 1 >= 3 && xa + 1 < p.nx - 3;
-      const bool ia_ = ibits & 1u, ib_ = (ibits >> 1) & 1u;
-      append_pair(ia_ && in3a, ib_ && in3b, (int)ia, v.ilist, &v.cnt[0], v.cap, v.err, false);
-      append_pair(ia_ && !in3a, ib_ && !in3b, (int)ia, v.ilist, &v.cnt[6], v.cap, v.err, true);
-    }
+    const unsigned bits = act ? (sm.x >> (2 * hl)) & 3u : 0u;
     const bool la = bits & 1u, lb = (bits >> 1) & 1u;
     const bool hslow = act && sm.z != 0u;               // uniform over the half-warp
     const bool hwork = act && sm.x != 0u && !hslow;     // the pair path serves this half
@@ -363,7 +333,10 @@ __global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, Vi
         float2 rho, usq;
         collide_x2<SH>(p, f, rho, usq);
         if ((la && rho_bad<SH>(rho.x)) || (lb && rho_bad<SH>(rho.y))) atomicOr(v.err, ERRB_UNSTABLE);
-        if ((la && usq.x > 0.16f) || (lb && usq.y > 0.16f)) atomicOr(v.err, ERRB_SPEED);  // (speed_bad)
+        if (p.umax2 > 0.0) {  // (speed_bad)
+          const float um2 = (float)p.umax2;
+          if ((la && usq.x > um2) || (lb && usq.y > um2)) atomicOr(v.err, ERRB_SPEED);
+        }
         if (la && owned(p, xa, y, z)) msum += rho_full<SH>(rho.x);
         if (lb && owned(p, xa + 1, y, z)) msum += rho_full<SH>(rho.y);
 #pragma unroll

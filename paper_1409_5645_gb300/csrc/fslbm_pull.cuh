@@ -1,5 +1,5 @@
 // fslbm_pull.cuh -- device helpers of the stream step shared by the bulk
-// kernels: warp-aggregated list appends, the general pull next to walls,
+// kernels: the warp-aggregated list append, the general pull next to walls,
 // faces and gas, and the wall closures.
 #pragma once
 #include "fslbm_dev.cuh"
@@ -23,33 +23,6 @@ __device__ __forceinline__ void warp_append(bool pred, int value, int* list, int
     if (k < cap) list[k] = value;
     else atomicOr(err, ERRB_OVERFLOW);
   }
-}
-
-// the same, filling list[cap - 1 - k] (the list's back end)
-__device__ __forceinline__ void warp_append_back(bool pred, int value, int* list, int* count, int cap, int* err) {
-  unsigned bal = __ballot_sync(0xffffffffu, pred);
-  if (!bal) return;
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(bal) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(bal));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pred) {
-    int k = base + __popc(bal & ((1u << lane) - 1u));
-    if (k < cap) list[cap - 1 - k] = value;
-    else atomicOr(err, ERRB_OVERFLOW);
-  }
-}
-
-// Interface cells into the interface list: a cell whose stencil (every cell
-// within 3) lies inside the lattice from the front (count cnt[0]), the others
-// from the back (count cnt[6]), so that the interface kernels run the two
-// kinds in separate warps.  All 32 lanes call it.
-template <class V>
-__device__ __forceinline__ void append_iface(const Par& p, const V& v, bool ifc, int i, int x, int y, int z) {
-  const bool in3 = x >= 3 && x < p.nx - 3 && y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
-  warp_append(ifc && in3, i, v.ilist, &v.cnt[0], v.cap, v.err);
-  warp_append_back(ifc && !in3, i, v.ilist, &v.cnt[6], v.cap, v.err);
 }
 
 // ---------------------------------------------------------------------------

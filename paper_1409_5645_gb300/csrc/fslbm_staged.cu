@@ -3,8 +3,7 @@
 //
 // Both kernels do the work of k_bulk (liquid cells of the fluid-segment list,
 // one warp per 32-cell x segment, Eq. lbe1 pull, wall closures, Eq. lbe2
-// collision, interface cells compacted into a list, per-warp FP64 partial
-// sums) with the same arithmetic, so their results are identical to it; they
+// collision, per-warp FP64 partial sums) with the same arithmetic, so their results are identical to it; they
 // differ in how the 19 pulled values of a segment reach the warp.
 //
 // k_bulk_async  every lane copies the 19 values it will consume, f_q(x - c_q),
@@ -178,7 +177,6 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     const long long i = rowstart + x;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
-    append_iface(p, v, k == IFC, (int)i, x, y, z);
     R f[19];
     const bool fast = k == LIQ && !(fl & NEARB) && x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 &&
                       z < p.nz - 1;
@@ -214,7 +212,7 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     R rho, ux, uy, uz;
     collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
     if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
-    if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
+    if (speed_bad(p, ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
     FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
@@ -312,7 +310,6 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
     const long long i = rowstart + x;
     const uint8_t fl = in ? (uint8_t)(sl[19 * 32] >> (8 * (int)(i & 3))) : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
-    append_iface(p, v, k == IFC, (int)i, x, y, z);
     R f[19];
     const bool fast = k == LIQ && !(fl & NEARB) && x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 &&
                       z < p.nz - 1;
@@ -346,7 +343,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
       R rho, ux, uy, uz;
       collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
       if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
-      if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
+      if (speed_bad(p, ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
       FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
       FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)

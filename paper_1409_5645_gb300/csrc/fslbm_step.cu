@@ -1,12 +1,12 @@
 // fslbm_step.cu -- the stream-collide kernels of one FSLBM time step.
 //
 // k_segments  compact list of the 32-cell x segments holding fluid (so that
-//          gas-only stretches of the lattice cost one flag scan, not a warp).
-// k_bulk   every warp walks that list on its own, one lane per cell.  Liquid
-//          cells pull their 19 populations (Eq. lbe1), apply half-way
-//          bounce-back / CLI at walls, collide (Eq. lbe2) and store; interface
-//          cells are compacted into a list by warp ballot.  The liquid density
-//          is reduced per block for the mass balance.
+//          gas-only stretches of the lattice cost one flag scan, not a warp),
+//          their kind masks, and the list of the step's interface cells.
+// k_bulk   every warp walks the segment list on its own, one lane per cell.
+//          Liquid cells pull their 19 populations (Eq. lbe1), apply half-way
+//          bounce-back / CLI at walls, collide (Eq. lbe2) and store.  The
+//          liquid density is reduced per warp for the mass balance.
 // k_iface  one thread per interface cell (grid-stride over the list): pulls,
 //          rebuilds the populations arriving from gas cells by the FSK rule
 //          (Eq. koerner) or the FSL rule (Eq. closure, Table 1, D = 0) with the
@@ -41,7 +41,10 @@ __device__ __forceinline__ double block_sum128(double v) {
 // it writes the segment's masks at seglist[4 (S + k)] (S: segments of the
 // lattice): bit j of each for cell x0 + j, liquid, interface, and liquid
 // needing the general pull (k_bulk's test of a fast cell, negated), so that a
-// bulk kernel reads no flag on its fast path.
+// bulk kernel reads no flag on its fast path.  It also lists the step's
+// interface cells: a cell whose stencil (every cell within 3) lies inside the
+// lattice at the front of the interface list, the others at its back, each
+// segment's cells in x order, one atomic per warp and end.
 // ---------------------------------------------------------------------------
 // bit s of each byte of w, gathered into bits 0-3 (the four partial products
 // of the multiplier land on distinct bits, so no carries mix them)
@@ -49,8 +52,21 @@ __device__ __forceinline__ unsigned byte_bits(unsigned w, int s) {
   return ((((w >> s) & 0x01010101u) * 0x00204081u) >> 21) & 0xfu;
 }
 
+// the set bits of m (cells x0 + k of a segment) written in increasing k to
+// list positions k0, k0 + 1, ... (from the back of the list when back)
+__device__ __forceinline__ void put_cells(unsigned m, int first, int k0, int* list, int cap, bool back, int* err) {
+  while (m) {
+    const int k = __ffs(m) - 1;
+    m &= m - 1u;
+    if (k0 < cap) list[back ? cap - 1 - k0 : k0] = first + k;
+    else atomicOr(err, ERRB_OVERFLOW);
+    ++k0;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restrict__ flags, int* __restrict__ seglist,
-                                                  int* __restrict__ count) {
+                                                  int* __restrict__ count, int* __restrict__ ilist,
+                                                  int* __restrict__ icount, int cap, int* __restrict__ err) {
   pdl_begin();
   const int nsx = (p.nx + 31) >> 5;
   const long long nseg = (long long)nsx * p.ny * p.nz;
@@ -119,6 +135,50 @@ __global__ void __launch_bounds__(256) k_segments(Par p, const uint8_t* __restri
     else slow = liq & (nearw | (p.px ? xf : 0u) | (((yf && p.py) || (zf && p.pz)) ? all : 0u));
     reinterpret_cast<uint4*>(seglist)[nseg + k] = make_uint4(liq, ifc, slow, 0u);
   }
+  // interface cells: interior ones (every cell within 3 inside the lattice) to
+  // the front of the list (count icount[0]), the others to its back (icount[6])
+  unsigned fin = 0u, fed = 0u;
+  int first = 0;
+  if (ifc) {
+    const unsigned row = fdiv((unsigned)sgi, p.dnsx);
+    const unsigned zz = fdiv(row, p.dny);
+    const int x0 = (int)((unsigned)sgi - row * (unsigned)nsx) << 5;
+    const int y = (int)(row - zz * (unsigned)p.ny), z = (int)zz;
+    first = (int)row * p.nx + x0;
+    const int lo = max(0, 3 - x0), hi = min(len, p.nx - 3 - x0);  // cells with 3 <= x < nx - 3
+    const unsigned xin = hi > lo ? ((hi - lo == 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u) << lo) : 0u;
+    const bool yz3 = y >= 3 && y < p.ny - 3 && z >= 3 && z < p.nz - 3;
+    fin = yz3 ? (ifc & xin) : 0u;
+    fed = ifc & ~fin;
+  }
+  // prefix sums of the counts over the warp, then over the block's warps: one
+  // atomic per block and end (the two counters are shared by the whole grid)
+  int ni = __popc(fin), ne = __popc(fed);
+  const bool any = __ballot_sync(0xffffffffu, (fin | fed) != 0u) != 0u;
+  if (any) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(0xffffffffu, ni, o), b = __shfl_up_sync(0xffffffffu, ne, o);
+      if (lane >= o) { ni += a; ne += b; }
+    }
+  }
+  __shared__ int wi[8], we[8], bi0, be0;
+  if (lane == 31) { wi[w] = ni; we[w] = ne; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ti = 0, te = 0;
+    for (int k = 0; k < 8; ++k) {
+      const int a = wi[k], b = we[k];
+      wi[k] = ti; we[k] = te;
+      ti += a; te += b;
+    }
+    bi0 = ti ? atomicAdd(&icount[0], ti) : 0;
+    be0 = te ? atomicAdd(&icount[6], te) : 0;
+  }
+  __syncthreads();
+  const int bi = bi0 + wi[w], be = be0 + we[w];
+  if (fin) put_cells(fin, first, bi + ni - __popc(fin), ilist, cap, false, err);
+  if (fed) put_cells(fed, first, be + ne - __popc(fed), ilist, cap, true, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -142,7 +202,6 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
     const long long i = (long long)sd.w + lane;
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
-    append_iface(p, v, k == IFC, (int)i, x, y, z);
     const size_t N = (size_t)p.N;
     R f[19];
     // Fast path: every source is a fluid cell at a plain offset, or lies beyond
@@ -196,7 +255,7 @@ __global__ void __launch_bounds__(128, (P == P64 ? 4 : 8)) k_bulk(Par p, View<P>
     R rho, ux, uy, uz;
     collide<R, Form<P>::SH>(p, f, rho, ux, uy, uz);
     if (rho_bad<Form<P>::SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
-    if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
+    if (speed_bad(p, ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #define FSL_ST(q) st<P, q>(v.fout, (size_t)q * N + (size_t)i, f[q]);
     FSL_ST(0) FSL_ST(1) FSL_ST(2) FSL_ST(3) FSL_ST(4) FSL_ST(5) FSL_ST(6) FSL_ST(7) FSL_ST(8)
     FSL_ST(9) FSL_ST(10) FSL_ST(11) FSL_ST(12) FSL_ST(13) FSL_ST(14) FSL_ST(15) FSL_ST(16)
@@ -380,7 +439,7 @@ __device__ __forceinline__ double iface_cell(const Par& p, const View<P>& v, int
   R rho, ux, uy, uz;
   collide<R, SH>(p, f, rho, ux, uy, uz);
   if (rho_bad<SH>(rho)) atomicOr(v.err, ERRB_UNSTABLE);
-  if (speed_bad(ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
+  if (speed_bad(p, ux, uy, uz)) atomicOr(v.err, ERRB_SPEED);
 #pragma unroll
   for (int q = 0; q < 19; ++q) stq<P>(v.fout, (size_t)q * N + (size_t)i, q, f[q]);
   double mm = v.m[i];
@@ -499,12 +558,38 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ in, l
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// a launch without the programmatic-serialization attribute (after a wait
+// on another stream's event)
+template <typename... KArgs, typename... Args>
+inline int launch_plain(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  return (int)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <int P>
 int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, int iface_blocks,
                         int* seglist, int* segcount, void* timing_handle, int bulk_mode,
-                        const CUtensorMap* tmap) {
+                        const CUtensorMap* tmap, const Fork* fork) {
   const long long nseg = (long long)((p.nx + 31) / 32) * p.ny * p.nz;
-  if (launch_k(k_segments, (unsigned)((nseg + 255) / 256), 256, 0, st, p, v.flags, seglist, segcount)) return 1;
+  if (launch_k(k_segments, (unsigned)((nseg + 255) / 256), 256, 0, st, p, v.flags, seglist, segcount, v.ilist, v.cnt,
+               v.cap, v.err))
+    return 1;
+  // the interface geometry reads phi(t), the flags and the interface list of
+  // the segment scan, and writes only its scratch: it runs on the side stream
+  // beside the bulk kernel
+  const bool geo = p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc;
+  auto kgeo = p.elvira ? (p.sigma != 0.0 ? k_geom<P, true, true> : k_geom<P, false, true>)
+                       : (p.sigma != 0.0 ? k_geom<P, true, false> : k_geom<P, false, false>);
+  const bool side = geo && fork;
+  if (side) {
+    if (cudaEventRecord(fork->fork, st) != cudaSuccess) return 1;
+    if (cudaStreamWaitEvent(fork->side, fork->fork, 0) != cudaSuccess) return 1;
+    if (launch_plain(kgeo, iface_blocks, 128, fork->side, p, v)) return 1;
+    if (cudaEventRecord(fork->join, fork->side) != cudaSuccess) return 1;
+  }
   if (timing_handle && fslbm_mark(timing_handle, 0)) return 1;  // the bulk group times the bulk kernel alone
   bool launched = false;
   if constexpr (P != P64) {
@@ -522,15 +607,15 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
     return 1;
   if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
-  if ((p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc) &&
-      launch_k(p.elvira ? (p.sigma != 0.0 ? k_geom<P, true, true> : k_geom<P, false, true>)
-                        : (p.sigma != 0.0 ? k_geom<P, true, false> : k_geom<P, false, false>),
-               iface_blocks, 128, 0, st, p, v))
-    return 1;
+  if (geo && !side && launch_k(kgeo, iface_blocks, 128, 0, st, p, v)) return 1;
   // the interface partials follow the bulk warps' ones
-  if (launch_k((p.stress || p.ub_extrap || p.recon_nc) ? k_iface<P, true> : k_iface<P, false>, iface_blocks, 128, 0, st, p, v,
-               bulk_blocks * 4))
+  auto kif = (p.stress || p.ub_extrap || p.recon_nc) ? k_iface<P, true> : k_iface<P, false>;
+  if (side) {
+    if (cudaStreamWaitEvent(st, fork->join, 0) != cudaSuccess) return 1;
+    if (launch_plain(kif, iface_blocks, 128, st, p, v, bulk_blocks * 4)) return 1;
+  } else if (launch_k(kif, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) {
     return 1;
+  }
   return (int)cudaGetLastError();
 }
 
@@ -554,10 +639,10 @@ int launch_reduce(const double* in, long long n, double* tmp, int tmp_blocks, co
 }
 
 template int launch_step_kernels<P64>(const Par&, const View<P64>&, cudaStream_t, int, int, int*, int*, void*,
-                                      int, const CUtensorMap*);
+                                      int, const CUtensorMap*, const Fork*);
 template int launch_step_kernels<P32>(const Par&, const View<P32>&, cudaStream_t, int, int, int*, int*, void*,
-                                      int, const CUtensorMap*);
+                                      int, const CUtensorMap*, const Fork*);
 template int launch_step_kernels<P16>(const Par&, const View<P16>&, cudaStream_t, int, int, int*, int*, void*,
-                                      int, const CUtensorMap*);
+                                      int, const CUtensorMap*, const Fork*);
 
 }  // namespace fsl

@@ -41,7 +41,8 @@ class Params(C.Structure):
                 ("stress", C.c_int), ("shear_b", C.c_double * 6), ("wall_u", C.c_double * 3),
                 ("ub_extrap", C.c_int), ("recon_nc", C.c_int), ("excess_split", C.c_int),
                 ("bulk_loads", C.c_int), ("precision", C.c_int),
-                ("stream", C.c_void_p), ("elvira", C.c_int), ("adjoint_fp32", C.c_int)]
+                ("stream", C.c_void_p), ("elvira", C.c_int), ("adjoint_fp32", C.c_int),
+                ("u_max", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -204,6 +205,7 @@ def params_struct(dims, params: dict, precision=F64, stream=None) -> Params:
     P.stream = stream
     P.elvira = int(params.get("elvira", 0))
     P.adjoint_fp32 = int(params.get("adjoint_fp32", 0))
+    P.u_max = float(params.get("u_max", 0.4))
     return P
 
 
