@@ -384,6 +384,17 @@ long long fslbm_time(const fslbm_t *h);
  * NULL).  An implementation property with no counterpart in the paper. */
 int fslbm_bulk_loads(const fslbm_t *h);
 
+/* Scheduling of the interface kernels (an implementation choice with no
+ * counterpart in the paper; the results are the same either way, bit for
+ * bit).  on = 1 (default): after the segment scan the interface geometry,
+ * and beside the two-cells-per-lane bulk kernel the interface kernel too,
+ * run on a second stream of the handle while the bulk kernel runs on its
+ * stream; the pair kernel's grid then leaves room for them on every SM, and
+ * the streams join before the conversions.  on = 0: every kernel in order on
+ * the handle's stream, the bulk kernel on a full resident wave (to time the
+ * kernels alone).  FSLBM_ERR_ARG for other values. */
+int fslbm_set_overlap(fslbm_t *h, int on);
+
 /* Kernel launches one fslbm_step time step makes on this handle (the
  * per-step reset, segment list, bulk, interface geometry where the rule,
  * surface tension, the shear term or the normal links need it, interface,

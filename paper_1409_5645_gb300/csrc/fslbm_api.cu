@@ -239,7 +239,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
       h->tmap = nullptr;
     }
   }
-  // the side stream of the interface geometry (it runs beside the bulk kernel)
+  // the side stream of the interface kernels (they run beside the bulk kernel)
+  h->overlap = 1;
   if (cudaStreamCreateWithFlags(&h->fork.side, cudaStreamNonBlocking) == cudaSuccess) {
     if (cudaEventCreateWithFlags(&h->fork.fork, cudaEventDisableTiming) == cudaSuccess) {
       if (cudaEventCreateWithFlags(&h->fork.join, cudaEventDisableTiming) == cudaSuccess) h->forked = 1;
@@ -285,6 +286,12 @@ extern "C" int fslbm_bulk_loads(const fslbm_t* h) {
          : h->bulk_mode == BULK_ASYNC ? FSLBM_LOADS_ASYNC
          : h->bulk_mode == BULK_PAIRS ? FSLBM_LOADS_PAIRS
                                       : FSLBM_LOADS_PLAIN;
+}
+
+extern "C" int fslbm_set_overlap(fslbm_t* h, int on) {
+  if (!h || (on != 0 && on != 1)) return FSLBM_ERR_ARG;
+  h->overlap = on;
+  return FSLBM_OK;
 }
 
 // the step's mass reduction runs inside the cooperative conversion kernel
@@ -488,7 +495,7 @@ static int step_t(fslbm* h) {
   if (launch_reset(h->cnt, h->st)) return 1;
   if (launch_step_kernels<P>(h->par, v, h->st, h->bulk_blocks, h->iface_blocks, h->seglist, h->cnt + 9,
                              h->timing ? h : nullptr, h->bulk_mode, h->tmap ? &h->tmap[h->cur] : nullptr,
-                             h->forked ? &h->fork : nullptr))
+                             (h->forked && h->overlap) ? &h->fork : nullptr))
     return 1;
   if (mark_event(h, 2)) return 1;
   // the mass reduction rides in the cooperative conversion kernel where that runs

@@ -53,8 +53,9 @@ struct fslbm {
   int f0_valid;       // f0 holds the populations of the current initial state
   int bulk_mode;      // fsl::BulkMode of the bulk kernel
   CUtensorMap* tmap;  // [2] tensor maps of fA and fB for the TMA bulk kernel (64-byte aligned), or NULL
-  fsl::Fork fork;     // the side stream of the interface geometry and its two events
+  fsl::Fork fork;     // the side stream of the interface kernels and its two events
   int forked;         // fork holds a stream and events
+  int overlap;        // 1: the interface kernels run on the side stream beside the bulk kernel
 };
 
 

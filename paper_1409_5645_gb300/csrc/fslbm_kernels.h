@@ -42,9 +42,10 @@ int launch_reset(int* cnt, cudaStream_t st);
 // how the bulk kernel reaches its pulled values (fslbm_bulk_loads)
 enum BulkMode { BULK_PLAIN = 0, BULK_TMA = 1, BULK_ASYNC = 2, BULK_PAIRS = 3 };
 
-// a second stream of the handle and two events: the interface geometry runs
-// on it beside the bulk kernel (fork after the segment scan, join before the
-// interface kernel)
+// a second stream of the handle and two events: the interface geometry (and,
+// beside the pair kernel, the interface kernel) runs on it beside the bulk
+// kernel (fork after the segment scan, join before the interface kernel or
+// the conversions)
 struct Fork {
   cudaStream_t side;
   cudaEvent_t fork, join;
@@ -73,7 +74,7 @@ int launch_bulk_async(const Par& p, const View<P>& v, cudaStream_t st, int bulk_
 bool pairs_shape_ok(const Par& p);
 template <int P>
 int launch_bulk_pairs(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
-                      const int* segcount);
+                      const int* segcount, bool shared);
 
 // records timing event k of the handle's current step (host side, fslbm_api.cu)
 int fslbm_mark(void* handle, int k);

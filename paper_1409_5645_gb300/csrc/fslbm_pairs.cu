@@ -41,6 +41,18 @@ constexpr unsigned FULL = 0xffffffffu;
 #endif
 template <int P>
 constexpr int pairs_blocks() { return P == P16 ? FSL_PAIRS_BLOCKS16 : FSL_PAIRS_BLOCKS32; }
+// blocks per SM in the launch when the interface kernels run beside it on
+// the side stream: fewer than resident, so that their blocks find room
+// (measured on the 512x256x256 dam break: FP32 at 3 of 5 and FP16 at 4 of 6
+// gave the shortest step)
+#ifndef FSL_PAIRS_GRID16
+#define FSL_PAIRS_GRID16 4
+#endif
+#ifndef FSL_PAIRS_GRID32
+#define FSL_PAIRS_GRID32 3
+#endif
+template <int P>
+constexpr int pairs_grid() { return P == P16 ? FSL_PAIRS_GRID16 : FSL_PAIRS_GRID32; }
 
 // A word holding the values of two x-adjacent cells (lo: the even cell).
 template <int P>
@@ -372,18 +384,19 @@ bool pairs_shape_ok(const Par& p) { return (p.nx & 1) == 0 && 19LL * p.N < (1LL 
 
 template <int P>
 int launch_bulk_pairs(const Par& p, const View<P>& v, cudaStream_t st, int bulk_blocks, const int* seglist,
-                      const int* segcount) {
+                      const int* segcount, bool shared) {
   if constexpr (P == P64) {
     return 1;
   } else {
-    // bulk_blocks is 8 resident blocks per SM of k_bulk; one resident wave here
-    const int grid = bulk_blocks / 8 * pairs_blocks<P>();
+    // bulk_blocks is 8 resident blocks per SM of k_bulk; one resident wave
+    // here, or fewer blocks beside the interface kernels (shared)
+    const int grid = bulk_blocks / 8 * (shared ? pairs_grid<P>() : pairs_blocks<P>());
     return launch_k(k_bulk_pairs<P>, grid, 128, 0, st, p, v, seglist, segcount, bulk_blocks * 4);
   }
 }
 
-template int launch_bulk_pairs<P64>(const Par&, const View<P64>&, cudaStream_t, int, const int*, const int*);
-template int launch_bulk_pairs<P32>(const Par&, const View<P32>&, cudaStream_t, int, const int*, const int*);
-template int launch_bulk_pairs<P16>(const Par&, const View<P16>&, cudaStream_t, int, const int*, const int*);
+template int launch_bulk_pairs<P64>(const Par&, const View<P64>&, cudaStream_t, int, const int*, const int*, bool);
+template int launch_bulk_pairs<P32>(const Par&, const View<P32>&, cudaStream_t, int, const int*, const int*, bool);
+template int launch_bulk_pairs<P16>(const Par&, const View<P16>&, cudaStream_t, int, const int*, const int*, bool);
 
 }  // namespace fsl

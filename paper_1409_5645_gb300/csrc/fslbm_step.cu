@@ -579,15 +579,23 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
     return 1;
   // the interface geometry reads phi(t), the flags and the interface list of
   // the segment scan, and writes only its scratch: it runs on the side stream
-  // beside the bulk kernel
+  // beside the bulk kernel.  Beside the pair kernel (whose grid then leaves
+  // room on every SM) the interface kernel follows it there: it reads f~(t),
+  // phi(t), m and the flags, and writes the interface cells' populations, m,
+  // phi(t+1), marks and lists, none of which the bulk kernel touches
   const bool geo = p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc;
   auto kgeo = p.elvira ? (p.sigma != 0.0 ? k_geom<P, true, true> : k_geom<P, false, true>)
                        : (p.sigma != 0.0 ? k_geom<P, true, false> : k_geom<P, false, false>);
-  const bool side = geo && fork;
-  if (side) {
+  auto kif = (p.stress || p.ub_extrap || p.recon_nc) ? k_iface<P, true> : k_iface<P, false>;
+  const bool pairs = P != P64 && bulk_mode == BULK_PAIRS;
+  const bool side_geo = geo && fork;
+  const bool side_if = pairs && fork;
+  if (side_geo || side_if) {
     if (cudaEventRecord(fork->fork, st) != cudaSuccess) return 1;
     if (cudaStreamWaitEvent(fork->side, fork->fork, 0) != cudaSuccess) return 1;
-    if (launch_plain(kgeo, iface_blocks, 128, fork->side, p, v)) return 1;
+    if (side_geo && launch_plain(kgeo, iface_blocks, 128, fork->side, p, v)) return 1;
+    // the interface partials follow the bulk warps' ones
+    if (side_if && launch_plain(kif, iface_blocks, 128, fork->side, p, v, bulk_blocks * 4)) return 1;
     if (cudaEventRecord(fork->join, fork->side) != cudaSuccess) return 1;
   }
   if (timing_handle && fslbm_mark(timing_handle, 0)) return 1;  // the bulk group times the bulk kernel alone
@@ -600,21 +608,21 @@ int launch_step_kernels(const Par& p, const View<P>& v, cudaStream_t st, int bul
       if (launch_bulk_async<P>(p, v, st, bulk_blocks, seglist, segcount)) return 1;
       launched = true;
     } else if (bulk_mode == BULK_PAIRS) {
-      if (launch_bulk_pairs<P>(p, v, st, bulk_blocks, seglist, segcount)) return 1;
+      if (launch_bulk_pairs<P>(p, v, st, bulk_blocks, seglist, segcount, side_if)) return 1;
       launched = true;
     }
   }
   if (!launched && launch_k(k_bulk<P>, bulk_blocks, 128, 0, st, p, v, (const int*)seglist, (const int*)segcount))
     return 1;
   if (timing_handle && fslbm_mark(timing_handle, 1)) return 1;
-  if (geo && !side && launch_k(kgeo, iface_blocks, 128, 0, st, p, v)) return 1;
-  // the interface partials follow the bulk warps' ones
-  auto kif = (p.stress || p.ub_extrap || p.recon_nc) ? k_iface<P, true> : k_iface<P, false>;
-  if (side) {
+  if (geo && !side_geo && launch_k(kgeo, iface_blocks, 128, 0, st, p, v)) return 1;
+  if (side_geo || side_if) {
     if (cudaStreamWaitEvent(st, fork->join, 0) != cudaSuccess) return 1;
-    if (launch_plain(kif, iface_blocks, 128, st, p, v, bulk_blocks * 4)) return 1;
-  } else if (launch_k(kif, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4)) {
-    return 1;
+  }
+  if (!side_if) {
+    if (side_geo ? launch_plain(kif, iface_blocks, 128, st, p, v, bulk_blocks * 4)
+                 : launch_k(kif, iface_blocks, 128, 0, st, p, v, bulk_blocks * 4))
+      return 1;
   }
   return (int)cudaGetLastError();
 }

@@ -89,6 +89,8 @@ def lib():
             L.fslbm_time.restype = C.c_longlong
             L.fslbm_bulk_loads.argtypes = [vp]
             L.fslbm_bulk_loads.restype = C.c_int
+            L.fslbm_set_overlap.argtypes = [vp, C.c_int]
+            L.fslbm_set_overlap.restype = C.c_int
             L.fslbm_launches_per_step.argtypes = [vp]
             L.fslbm_launches_per_step.restype = C.c_int
             L.fslbm_check_grid_barrier.argtypes = [ip, vp]
@@ -399,8 +401,14 @@ class Lattice:
     @property
     def bulk_loads(self) -> str:
         """How the bulk kernel reaches its pulled values: 'async' (cp.async into
-        shared memory), 'plain' (global loads) or 'tma' (tensor-map row copies)."""
+        shared memory), 'plain' (global loads), 'tma' (tensor-map row copies)
+        or 'pairs' (two cells per lane)."""
         return {v: k for k, v in LOADS.items()}[self.L.fslbm_bulk_loads(self.h)]
+
+    def set_overlap(self, on: bool):
+        """Interface kernels on a second stream beside the bulk kernel (True,
+        the default) or every kernel in order on the handle's stream."""
+        self._check(self.L.fslbm_set_overlap(self.h, int(bool(on))), "set_overlap")
 
     @property
     def launches_per_step(self) -> int:
