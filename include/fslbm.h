@@ -399,7 +399,7 @@ int fslbm_set_overlap(fslbm_t *h, int on);
  * per-step reset, segment list, bulk, interface geometry where the rule,
  * surface tension, the shear term or the normal links need it, interface,
  * the two-level mass reduction, and the conversions: one cooperative launch
- * where the device allows it, else five; none with frozen flags), or
+ * where the device allows it, else four; none with frozen flags), or
  * FSLBM_ERR_ARG for NULL.  An implementation property with no counterpart in
  * the paper. */
 int fslbm_launches_per_step(const fslbm_t *h);

@@ -183,8 +183,8 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
   h->iface_blocks = 152 * 16;  // one thread per interface cell up to 311 296 cells per round
   h->list_blocks = 152 * 8;  // 8 warps each: one warp per listed cell, 9728 cells per round
   {
-    // the five conversion stages as one cooperative launch, two resident
-    // blocks per SM, where the device allows it; else five launches
+    // the four conversion stages as one cooperative launch, two resident
+    // blocks per SM, where the device allows it; else four launches
     int dev = 0, coop = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -323,7 +323,7 @@ extern "C" int fslbm_launches_per_step(const fslbm_t* h) {
   if (!h) return FSLBM_ERR_ARG;
   const Par& p = h->par;
   const int geom = (p.rule != 0 || p.sigma != 0.0 || p.stress || p.recon_nc) ? 1 : 0;
-  const int conv = p.freeze ? 0 : (h->coop_blocks > 0 ? 1 : 5);
+  const int conv = p.freeze ? 0 : (h->coop_blocks > 0 ? 1 : 4);
   const int reduce = fold_reduce(h) ? 0 : 2;
   return 4 + geom + reduce + conv;  // reset, segments, bulk, interface
 }
@@ -518,7 +518,7 @@ static int step_t(fslbm* h) {
     int rc = launch_conversions<P>(h->par, v, h->st, h->list_blocks, h->coop_blocks, mr);
     if (rc == (int)cudaErrorCooperativeLaunchTooLarge && h->coop_blocks > 0) {
       // the device cannot hold the cooperative grid now (e.g. shared with
-      // other work): five launches and the stand-alone reduction from here on
+      // other work): four launches and the stand-alone reduction from here on
       cudaGetLastError();
       h->coop_blocks = 0;
       if (mr.nb > 0 && launch_reduce(h->partials, nparts, h->red, h->red_blocks, h->lost, h->step_mass, h->st))

@@ -6,21 +6,24 @@
 // Then, all as list kernels (grid-stride; counts read on the device, no host
 // synchronisation):
 //   fill     gas neighbours of F become new interface (NEWG, listed once by an
-//            atomic byte-OR); an E cell next to F leaves E
+//            atomic byte-OR)
+//   empty    an E cell with an F neighbour leaves E (it stays interface);
+//            liquid neighbours of the remaining E become interface (NEWL)
 //   newg     NEWG cells get f = f^eq(mean rho, mean u) over their liquid /
 //            interface neighbours (q order), collided, m = 0
-//   empty    liquid neighbours of the remaining E become interface (NEWL)
 //   newl     NEWL cells get m = rho
 //   share    excess (F: m - rho, E: m) / number of receivers (interface after
 //            the steps above, not converting); no receiver -> lost ledger
 //   recv     each receiver gathers the shares of its converting neighbours in q
 //            order (deterministic, no floating-point atomics)
 //   final    F -> liquid, E -> gas, new cells -> interface, marks cleared
-// newg and empty run together, newl and share together (each pair is
-// independent).  The five stages run as one cooperative launch (k_convert,
-// two resident blocks per SM, grid barriers between the stages) where the
-// device allows it, else as five launches.  The result does not depend on
-// list order.
+// fill and empty run together (each E cell tests its own neighbours for F
+// marks, which the step kernel set), and so do newg, newl and share (share
+// reads only the marks and claims of the first stage and the converting
+// cells' own state).  The four stages run as one cooperative launch
+// (k_convert, two resident blocks per SM, grid barriers between the stages)
+// where the device allows it, else as four launches.  The result does not
+// depend on list order.
 #include "fslbm_dev.cuh"
 #include "fslbm_kernels.h"
 
@@ -84,17 +87,18 @@ __device__ __forceinline__ void do_fill(const Par& p, const View<P>& v) {
       if (kj == GAS) {
         const uint8_t old = or_u8(v.mark, j, MK_NEWG);
         won = !(old & MK_NEWG);  // the first claimant lists the new cell
-      } else if (kj == IFC) {
-        if (((volatile uint8_t*)v.mark)[j] & MK_EMPTY) clear_u8(v.mark, j, MK_EMPTY);
       }
     }
     push(won, v.nglist, &v.cnt[3], v.cap, (int)j, v.err);
   }
 }
 template <int P>
-__global__ void __launch_bounds__(256) k_fill(Par p, View<P> v) {
+__device__ __forceinline__ void do_empty(const Par& p, const View<P>& v);
+template <int P>
+__global__ void __launch_bounds__(256) k_fill_empty(Par p, View<P> v) {
   pdl_begin();
   do_fill<P>(p, v);
+  do_empty<P>(p, v);
 }
 
 // one warp per new cell: lane l (1..18) reads neighbour l's populations; the
@@ -185,14 +189,24 @@ __device__ __forceinline__ void do_empty(const Par& p, const View<P>& v) {
     if (!(v.mark[i] & MK_EMPTY)) continue;  // warp-uniform
     int x, y, z;
     coords(p, i, x, y, z);
-    bool won = false;
     long long j = -1;
+    uint8_t kj = WALL, mj = 0;
     if (q) {
       j = nbr(p, x, y, z, cx(q), cy(q), cz(q));
-      if (j >= 0 && (v.flags[j] & KIND) == LIQ) {
-        const uint8_t old = or_u8(v.mark, j, MK_NEWL);
-        won = !(old & MK_NEWL);  // the first claimant lists it; k_newl sets m = rho
+      if (j >= 0) {
+        kj = v.flags[j] & KIND;
+        mj = v.mark[j];
       }
+    }
+    // an emptied cell next to a filled one stays interface
+    if (__any_sync(0xffffffffu, (mj & MK_FILL) != 0)) {
+      if (lane == 0) clear_u8(v.mark, i, MK_EMPTY);
+      continue;  // (warp-uniform)
+    }
+    bool won = false;
+    if (kj == LIQ) {
+      const uint8_t old = or_u8(v.mark, j, MK_NEWL);
+      won = !(old & MK_NEWL);  // the first claimant lists it; newl sets m = rho
     }
     push(won, v.nllist, &v.cnt[4], v.cap, (int)j, v.err);
   }
@@ -305,18 +319,13 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
   }
 }
 
-// new cells from gas and the empty list are independent once the fill list is
-// processed, and so are new cells from liquid and the excess shares once the
-// empty list is: two launches instead of four
+// new cells from gas, new cells from liquid and the excess shares are
+// independent once the first stage has claimed the new cells and settled the
+// empty list
 template <int P>
-__global__ void __launch_bounds__(256) k_newg_empty(Par p, View<P> v) {
+__global__ void __launch_bounds__(256) k_new_share(Par p, View<P> v) {
   pdl_begin();
   do_newg<P>(p, v);
-  do_empty<P>(p, v);
-}
-template <int P>
-__global__ void __launch_bounds__(256) k_newl_share(Par p, View<P> v) {
-  pdl_begin();
   do_newl<P>(p, v);
   do_share<P>(p, v);
 }
@@ -458,33 +467,34 @@ __device__ __forceinline__ void grid_sync(unsigned* ctr, unsigned target, int* e
   __syncthreads();
 }
 
-// the five conversion stages in one launch, separated by grid barriers; the
+// the four conversion stages in one launch, separated by grid barriers; the
 // step's two-level mass reduction rides along in the first two stages (the
-// same chunks and order as the stand-alone reduction, before any excess
-// reaches the lost ledger)
+// same chunks and order as the stand-alone reduction), with the lost ledger
+// read before any excess of this step reaches it
 template <int P>
 __global__ void __launch_bounds__(256) k_convert(Par p, View<P> v, MassReduce mr) {
   pdl_begin();
   unsigned* ctr = (unsigned*)&v.cnt[10];
   const unsigned nb = gridDim.x;
+  double lost0 = 0.0;
+  if (mr.nb > 0 && blockIdx.x == 0 && threadIdx.x == 0) lost0 = *mr.add;
   if ((int)blockIdx.x < mr.nb) {
     const double t = block_chunk_sum(mr.in, mr.n, mr.chunk, blockIdx.x);
     if (threadIdx.x == 0) mr.tmp[blockIdx.x] = t;
   }
   do_fill<P>(p, v);
+  do_empty<P>(p, v);
   grid_sync(ctr, nb, v.err);
   if (mr.nb > 0 && blockIdx.x == 0) {
     const double t = block_chunk_sum(mr.tmp, mr.nb, mr.nb, 0);
-    if (threadIdx.x == 0) *mr.out = t + *mr.add;
+    if (threadIdx.x == 0) *mr.out = t + lost0;
   }
   do_newg<P>(p, v);
-  do_empty<P>(p, v);
-  grid_sync(ctr, 2 * nb, v.err);
   do_newl<P>(p, v);
   do_share<P>(p, v);
-  grid_sync(ctr, 3 * nb, v.err);
+  grid_sync(ctr, 2 * nb, v.err);
   do_recv<P>(p, v);
-  grid_sync(ctr, 4 * nb, v.err);
+  grid_sync(ctr, 3 * nb, v.err);
   do_final<P>(p, v);
 }
 
@@ -516,7 +526,7 @@ int convert_blocks_per_sm() {
 }
 
 // coop_blocks > 0: the fused cooperative kernel on that many blocks (all
-// resident); else five launches of list_blocks
+// resident); else four launches of list_blocks
 template <int P>
 int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list_blocks, int coop_blocks,
                        const MassReduce& mr) {
@@ -533,7 +543,7 @@ int launch_conversions(const Par& p, const View<P>& v, cudaStream_t st, int list
     if (mr.nb > coop_blocks) return (int)cudaErrorInvalidValue;
     return (int)cudaLaunchKernelEx(&cfg, k_convert<P>, p, v, mr);
   }
-  void (*ks[5])(Par, View<P>) = {k_fill<P>, k_newg_empty<P>, k_newl_share<P>, k_recv<P>, k_final<P>};
+  void (*ks[4])(Par, View<P>) = {k_fill_empty<P>, k_new_share<P>, k_recv<P>, k_final<P>};
   for (auto k : ks)
     if (launch_k(k, list_blocks, 256, 0, st, p, v)) return 1;
   return 0;

@@ -34,7 +34,7 @@ struct fslbm {
   double* partials;
   long long nparts;
   int bulk_blocks, iface_blocks, list_blocks, red_blocks;
-  int coop_blocks;  // blocks of the fused cooperative conversion kernel (0: five launches)
+  int coop_blocks;  // blocks of the fused cooperative conversion kernel (0: four launches)
   double* red;
   double* lost;
   int* err;
