@@ -237,7 +237,8 @@ def hbm_peak():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("fslbm_step.cu", "fslbm_staged.cu", "fslbm_pairs.cu", "fslbm_pull.cuh", "fslbm_dev.cuh"):
+    for f in ("fslbm_step.cu", "fslbm_step.cuh", "fslbm_staged.cu", "fslbm_pairs.cu", "fslbm_pull.cuh",
+              "fslbm_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -68,7 +68,8 @@ enum fslbm_status {
   FSLBM_ERR_ARG = -1,      /* bad argument or parameter */
   FSLBM_ERR_OOM = -2,      /* device allocation failed */
   FSLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
-  FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag */
+  FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag; in the
+                              bounds-checked library also an index outside its array */
   FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density, or a cell velocity above
                               u_max (the stability guard of the step) */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
@@ -423,6 +424,17 @@ int fslbm_check_grid_barrier(int expire, void *stream);
  * on GB300.  Synchronises the stream.  An implementation property with no
  * counterpart in the paper. */
 int fslbm_fp64_rate(double *tflops, void *stream);
+
+/* Build properties of the loaded library: bit 0 set in the bounds-checked
+ * library (compiled with FSLBM_CHECKED).  There every cell index a kernel
+ * reads from a segment record or a cell list, and every source cell that a
+ * fast path forms by offset arithmetic, is tested against the lattice before
+ * the access (as is a fast path's precondition, a cell handled as interior
+ * lying 3 or more cells inside every face); a failed test skips to cell 0
+ * and makes the next synchronising call return FSLBM_ERR_STATE.  Results are
+ * otherwise those of the normal library.  An implementation property with
+ * no counterpart in the paper. */
+int fslbm_build_info(void);
 
 /* Bytes of device memory held by the handle. */
 size_t fslbm_device_bytes(const fslbm_t *h);

@@ -214,6 +214,9 @@ extern "C" int fslbm_create_ex(const fslbm_params* prm, fslbm_t** out) {
     free(h);
     return FSLBM_ERR_OOM;
   }
+#ifdef FSLBM_CHECKED
+  p.err = h->err;
+#endif
   cudaMemsetAsync(h->flags, GAS, N4, h->st);
   cudaMemsetAsync(h->mark, 0, N4, h->st);
   cudaMemsetAsync(h->fA, 0, 19 * Nn * store_bytes(h->prec), h->st);
@@ -367,6 +370,7 @@ static int read_err(fslbm* h) {
   if (e & ERRB_OVERFLOW) return fail(h, FSLBM_ERR_OVERFLOW, "conversion list overflow");
   if (e & ERRB_TMA) return fail(h, FSLBM_ERR_TIMEOUT, "staged loads of the bulk kernel failed (bounded wait expired)");
   if (e & ERRB_SYNC) return fail(h, FSLBM_ERR_TIMEOUT, "grid barrier of the conversion kernel expired");
+  if (e & ERRB_BOUNDS) return fail(h, FSLBM_ERR_STATE, "an index outside its array (bounds-checked build)");
   return FSLBM_OK;
 }
 
@@ -669,5 +673,13 @@ extern "C" int fslbm_counters(fslbm_t* h, long long out[5]) {
 }
 
 extern "C" long long fslbm_time(const fslbm_t* h) { return h ? h->t : -1; }
+extern "C" int fslbm_build_info(void) {
+#ifdef FSLBM_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 extern "C" size_t fslbm_device_bytes(const fslbm_t* h) { return h ? h->bytes : 0; }
 extern "C" const char* fslbm_last_error(const fslbm_t* h) { return h ? h->msg : "NULL handle"; }

@@ -76,7 +76,7 @@ __device__ __forceinline__ void do_fill(const Par& p, const View<P>& v) {
   const int nf = min(load_count(&v.cnt[1]), v.cap);
   const int q = (lane >= 1 && lane < 19) ? lane : 0;
   for (int k = gw; k < nf; k += nw) {
-    const long long i = v.flist[k];
+    const long long i = FSL_CK(p, v.flist[k], p.N);
     int x, y, z;
     coords(p, i, x, y, z);
     bool won = false;
@@ -114,7 +114,7 @@ __device__ __forceinline__ void do_newg(const Par& p, const View<P>& v) {
   const int nn = min(load_count(&v.cnt[3]), v.cap);
   const int q = lane < 19 ? lane : 0;
   for (int k = gw; k < nn; k += nw) {
-    const long long j = v.nglist[k];
+    const long long j = FSL_CK(p, v.nglist[k], p.N);
     int x, y, z;
     coords(p, j, x, y, z);
     bool use = false;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void do_empty(const Par& p, const View<P>& v) {
   const int ne = min(load_count(&v.cnt[2]), v.cap);
   const int q = (lane >= 1 && lane < 19) ? lane : 0;
   for (int k = gw; k < ne; k += nw) {
-    const long long i = v.elist[k];
+    const long long i = FSL_CK(p, v.elist[k], p.N);
     if (!(v.mark[i] & MK_EMPTY)) continue;  // warp-uniform
     int x, y, z;
     coords(p, i, x, y, z);
@@ -218,7 +218,7 @@ __device__ __forceinline__ void do_newl(const Par& p, const View<P>& v) {
   using R = typename Form<P>::R;
   int nl = min(load_count(&v.cnt[4]), v.cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x) {
-    long long j = v.nllist[k];
+    long long j = FSL_CK(p, v.nllist[k], p.N);
     const double r = rho_out<P>(p, v, j);
     v.m[j] = r;
     v.phout[j] = (R)(r / r);
@@ -267,7 +267,7 @@ __device__ __forceinline__ void do_share(const Par& p, const View<P>& v) {
   const int q = (lane >= 1 && lane < 19) ? lane : 0;
   for (int k = gw; k < nf + ne; k += nw) {
     const bool isF = k < nf;
-    const long long i = isF ? v.flist[k] : v.elist[k - nf];
+    const long long i = FSL_CK(p, isF ? v.flist[k] : v.elist[k - nf], p.N);
     if (!isF && !(v.mark[i] & MK_EMPTY)) continue;  // warp-uniform
     int x, y, z;
     coords(p, i, x, y, z);
@@ -338,7 +338,7 @@ __device__ __forceinline__ void do_recv(const Par& p, const View<P>& v) {
   const int nr = min(load_count(&v.cnt[5]), v.cap);
   const long long sy = p.nx, sz = (long long)p.nx * p.ny;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nr; k += gridDim.x * blockDim.x) {
-    const long long yj = v.rlist[k];
+    const long long yj = FSL_CK(p, v.rlist[k], p.N);
     int x, y, z;
     coords(p, yj, x, y, z);
     const bool in1 = x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1;
@@ -391,14 +391,14 @@ __device__ __forceinline__ void do_final(const Par& p, const View<P>& v) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
     int kk = k;
     if (kk < nf) {
-      long long i = v.flist[kk];
+      long long i = FSL_CK(p, v.flist[kk], p.N);
       v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | LIQ);
       v.mark[i] = 0;
       continue;
     }
     kk -= nf;
     if (kk < ne) {
-      long long i = v.elist[kk];
+      long long i = FSL_CK(p, v.elist[kk], p.N);
       if (v.mark[i] & MK_EMPTY) {
         v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | GAS);
         v.phout[i] = R(0);
@@ -409,20 +409,20 @@ __device__ __forceinline__ void do_final(const Par& p, const View<P>& v) {
     }
     kk -= ne;
     if (kk < ng) {
-      long long i = v.nglist[kk];
+      long long i = FSL_CK(p, v.nglist[kk], p.N);
       v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | IFC);
       v.mark[i] = 0;
       continue;
     }
     kk -= ng;
     if (kk < nl) {
-      long long i = v.nllist[kk];
+      long long i = FSL_CK(p, v.nllist[kk], p.N);
       v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | IFC);
       v.mark[i] = 0;
       continue;
     }
     kk -= nl;
-    const long long r = v.rlist[kk];
+    const long long r = FSL_CK(p, v.rlist[kk], p.N);
     v.mark[r] = 0;
     if (p.excess_split) v.phout[r] = (R)(v.m[r] / rho_out<P>(p, v, r));
   }

@@ -43,7 +43,8 @@ __host__ __device__ constexpr R wq(int q) {
 // beyond a non-periodic face); NEARW a neighbour is a WALL cell of the lattice
 enum : uint8_t { LIQ = 1, IFC = 2, GAS = 4, WALL = 8, KIND = 15, NEARB = 16, NEARW = 32, STATIC_BITS = 48 };
 enum : uint8_t { MK_FILL = 1, MK_EMPTY = 2, MK_NEWG = 4, MK_NEWL = 8, MK_RECV = 16, MK_WSPLIT = 32 };
-enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8, ERRB_SYNC = 16, ERRB_SPEED = 32 };
+enum : int { ERRB_STATE = 1, ERRB_UNSTABLE = 2, ERRB_OVERFLOW = 4, ERRB_TMA = 8, ERRB_SYNC = 16, ERRB_SPEED = 32,
+             ERRB_BOUNDS = 64 };
 
 // ---------------------------------------------------------------------------
 // Precision forms
@@ -158,7 +159,64 @@ struct Par {
   int elvira;              // 1: ELVIRA normal where the height columns are open
   int adj32;               // 1: the adjoint's reverse step in FP32 (FP32/FP16 lattices)
   double umax2;            // stability guard: |u|^2 above it is an error (0: off)
+#ifdef FSLBM_CHECKED
+  int* err;                // the handle's error word (bounds-checked build)
+#endif
 };
+
+// ---------------------------------------------------------------------------
+// Bounds-checked build (compiled with FSLBM_CHECKED, a library of its own).
+// Every cell index a kernel reads from memory (a segment record, a cell list)
+// and every source cell a fast path forms by offset arithmetic is tested
+// against the lattice before the access, and so is a fast path's
+// precondition (a cell handled as interior lies 3 or more cells inside every
+// face).  A failed test sets ERRB_BOUNDS in the error word, reported at the
+// next synchronising call, and the access goes to cell 0 instead (where a
+// precondition failed, the cell is skipped); nothing traps.  Indices from nbr() (an in-range cell or -1) and from bounded loop
+// counters need no test.  In the normal build each macro is the bare
+// expression.
+// ---------------------------------------------------------------------------
+#ifdef FSLBM_CHECKED
+__device__ __forceinline__ long long chk_index(long long k, long long n, int* err) {
+  if ((unsigned long long)k < (unsigned long long)n) return k;
+  atomicOr(err, ERRB_BOUNDS);
+  return 0;
+}
+// element k of an array of n from base
+__device__ __forceinline__ long long chk_cell(long long k, long long base, long long n, int* err) {
+  if ((unsigned long long)(k - base) < (unsigned long long)n) return k;
+  atomicOr(err, ERRB_BOUNDS);
+  return 0;
+}
+// element k of a word of two (k even, k + 1 in the same array of n from base)
+__device__ __forceinline__ long long chk_word(long long k, long long base, long long n, int* err) {
+  if ((k & 1) == 0 && (unsigned long long)(k - base) < (unsigned long long)(n - 1)) return k;
+  atomicOr(err, ERRB_BOUNDS);
+  return 0;
+}
+__device__ __forceinline__ bool chk_ok(bool ok, int* err) {
+  if (!ok) atomicOr(err, ERRB_BOUNDS);
+  return ok;
+}
+// k in [0, n), else 0
+#define FSL_CK(p, k, n) fsl::chk_index((long long)(k), (long long)(n), (p).err)
+// the same where c holds (k is not used otherwise)
+#define FSL_CK_IF(p, c, k, n) ((c) ? fsl::chk_index((long long)(k), (long long)(n), (p).err) : (long long)(k))
+// k - base in [0, n) (an element of population plane base / N), else 0
+#define FSL_CK_CELL(p, k, base, n) fsl::chk_cell((long long)(k), (long long)(base), (long long)(n), (p).err)
+// the first element of a two-element word (see chk_word), else 0
+#define FSL_CK_WORD(p, k, base, n) fsl::chk_word((long long)(k), (long long)(base), (long long)(n), (p).err)
+#define FSL_CK_WORD_IF(p, c, k, n) ((c) ? fsl::chk_word((long long)(k), 0LL, (long long)(n), (p).err) : (long long)(k))
+// a precondition: c, a failure recorded (the caller then skips the cell)
+#define FSL_OK(p, c) fsl::chk_ok((c), (p).err)
+#else
+#define FSL_CK(p, k, n) (k)
+#define FSL_CK_IF(p, c, k, n) (k)
+#define FSL_CK_CELL(p, k, base, n) (k)
+#define FSL_CK_WORD(p, k, base, n) (k)
+#define FSL_CK_WORD_IF(p, c, k, n) (k)
+#define FSL_OK(p, c) true
+#endif
 
 // stability guard on a cell's velocity: |u| above u_max (0.4 lattice units
 // by default: the equilibria are second order in u, and the lattice's speed

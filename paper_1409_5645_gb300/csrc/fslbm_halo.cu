@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_box(Par p, View<P> v, int x0, int y0, i
     const int x = x0 + (int)(k - row * bx);
     const int y = y0 + (int)(row % by);
     const int z = z0 + (int)(row / by);
-    const size_t i = (size_t)x + (size_t)p.nx * ((size_t)y + (size_t)p.ny * (size_t)z);
+    const size_t i = (size_t)FSL_CK(p, (size_t)x + (size_t)p.nx * ((size_t)y + (size_t)p.ny * (size_t)z), p.N);
     if (UNPACK) {
       v.flags[i] = (uint8_t)((v.flags[i] & STATIC_BITS) | (bk[k] & KIND));
       v.m[i] = bm[k];

@@ -35,6 +35,11 @@ inline int launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, siz
   return (int)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// the segment scan (fslbm_step.cu): the list of the 32-cell x segments that
+// hold fluid, with their kind masks, and the step's interface cells
+int launch_segments(const Par& p, const uint8_t* flags, int* seglist, int* segcount, int* ilist, int* cnt, int cap,
+                    int* err, cudaStream_t st);
+
 // zero the per-step counters cnt[0..7] and cnt[9] (one small kernel, so that
 // the whole step is a chain of kernels)
 int launch_reset(int* cnt, cudaStream_t st);

@@ -244,7 +244,7 @@ __device__ __noinline__ double slow_cell(const Par& p, const View<P>& v, long lo
       const bool bbq = (cx(q) == 1 && ax0) || (cx(q) == -1 && ax1) || (cy(q) == 1 && ay0) || (cy(q) == -1 && ay1) ||
                        (cz(q) == 1 && az0) || (cz(q) == -1 && az1);
       f[q] = bbq ? ldq<P>(v.fin, (size_t)inv(q) * N + (size_t)i, inv(q))
-                 : ldq<P>(v.fin, (size_t)q * N + (size_t)(i - (cx(q) + sy * cy(q) + sz * cz(q))), q);
+                 : ldq<P>(v.fin, (size_t)q * N + (size_t)FSL_CK(p, i - (cx(q) + sy * cy(q) + sz * cz(q)), p.N), q);
     }
   } else {
     general_cell<P>(p, v, i, x, y, z, f);
@@ -278,11 +278,12 @@ __device__ __forceinline__ typename PairWord<P>::W pull_pair(const Par& p, const
   const unsigned own_k = (unsigned)inv(q) * N + ia;
   const unsigned src_k = (unsigned)q * N + ia - (unsigned)cx(q) - sy * (unsigned)cy(q) - sz * (unsigned)cz(q);
   if constexpr (cx(q) == 0) {
-    return PW::load(fin, bb ? own_k : src_k);
+    return PW::load(fin, (unsigned)FSL_CK_WORD(p, bb ? own_k : src_k, (unsigned)(bb ? inv(q) : q) * N, N));
   } else {
     const bool bba = bb || (cx(q) == 1 && xa == 0);           // the even cell's source beyond the x face
     const bool bbb = bb || (cx(q) == -1 && xa + 2 == p.nx);   // the odd cell's
-    return PW::load2(fin, bba ? own_k : src_k, bbb ? own_k + 1 : src_k + 1);
+    return PW::load2(fin, (unsigned)FSL_CK_CELL(p, bba ? own_k : src_k, (unsigned)(bba ? inv(q) : q) * N, N),
+                     (unsigned)FSL_CK_CELL(p, bbb ? own_k + 1 : src_k + 1, (unsigned)(bbb ? inv(q) : q) * N, N));
   }
 }
 
@@ -324,9 +325,9 @@ __global__ void __launch_bounds__(128, pairs_blocks<P>()) k_bulk_pairs(Par p, Vi
       sm_n = masks[si + 2 * nw];
     }
     const int x0 = sd.x, y = sd.y, z = sd.z;
-    const long long ia = (long long)sd.w + 2 * hl;  // the even cell of the pair
     const int xa = x0 + 2 * hl;
     const unsigned bits = act ? (sm.x >> (2 * hl)) & 3u : 0u;
+    const long long ia = FSL_CK_WORD_IF(p, bits != 0u, (long long)sd.w + 2 * hl, p.N);  // the even cell of the pair
     const bool la = bits & 1u, lb = (bits >> 1) & 1u;
     const bool hslow = act && sm.z != 0u;               // uniform over the half-warp
     const bool hwork = act && sm.x != 0u && !hslow;     // the pair path serves this half

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(128, TmaGeom<P>::BLOCKS) k_bulk_tma(Par p, Vie
     const int x = sd.x + lane, y = sd.y, z = sd.z;
     const long long rowstart = (long long)sd.w - sd.x;  // index of x = 0 in this row
     const bool in = x < p.nx;
-    const long long i = rowstart + x;
+    const long long i = FSL_CK_IF(p, in, rowstart + x, p.N);
     const uint8_t fl = in ? v.flags[i] : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
     R f[19];
@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
       const int4 sd = reinterpret_cast<const int4*>(seglist)[si];
       const int x = sd.x + lane, y = sd.y, z = sd.z;
       const long long rowstart = (long long)sd.w - sd.x;  // index of x = 0 in this row
-      const long long i = rowstart + x;
       const bool in = x < p.nx;
+      const long long i = FSL_CK_IF(p, in, rowstart + x, p.N);
       const bool xm = x >= 1, xp = x < p.nx - 1, ym = y >= 1, yp = y < p.ny - 1, zm = z >= 1, zp = z < p.nz - 1;
       const unsigned dst = base + (unsigned)(stg * 20 * 128);
       // the flag word (the flag array is padded to a multiple of 4 bytes)
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
         if (ccy == -1) ok = ok && yp;
         if (ccz == 1) ok = ok && zm;
         if (ccz == -1) ok = ok && zp;
-        const long long e = (long long)q * (long long)N + (ok ? i - (ccx + sy * ccy + sz * ccz) : 0LL);
+        const long long e = (long long)q * (long long)N + (ok ? FSL_CK(p, i - (ccx + sy * ccy + sz * ccz), p.N) : 0LL);
         if constexpr (P == P16) {
           cp_async4(dst + q * 128, reinterpret_cast<const uint32_t*>(v.fin) + (e >> 1), ok);
         } else {
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(128, 8) k_bulk_async(Par p, View<P> v, const i
     const int x = sd.x + lane, y = sd.y, z = sd.z;
     const long long rowstart = (long long)sd.w - sd.x;  // index of x = 0 in this row
     const bool in = x < p.nx;
-    const long long i = rowstart + x;
+    const long long i = FSL_CK_IF(p, in, rowstart + x, p.N);
     const uint8_t fl = in ? (uint8_t)(sl[19 * 32] >> (8 * (int)(i & 3))) : (uint8_t)GAS;
     const uint8_t k = fl & KIND;
     R f[19];

@@ -15,7 +15,9 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libfslbm.so")
+# FSLBM_CHECKED=1: the bounds-checked variant of the library (build.build(checked=True))
+LIB_PATH = os.path.join(_PKG, "_build", *(["checked"] if os.environ.get("FSLBM_CHECKED") == "1" else []),
+                        "libfslbm.so")
 
 FSK, FSL = 0, 1
 F64, F32, F16 = 0, 1, 2
@@ -95,6 +97,8 @@ def lib():
             L.fslbm_launches_per_step.restype = C.c_int
             L.fslbm_check_grid_barrier.argtypes = [ip, vp]
             L.fslbm_check_grid_barrier.restype = C.c_int
+            L.fslbm_build_info.argtypes = []
+            L.fslbm_build_info.restype = C.c_int
             L.fslbm_device_bytes.argtypes = [vp]
             L.fslbm_device_bytes.restype = C.c_size_t
             L.fslbm_last_error.argtypes = [vp]

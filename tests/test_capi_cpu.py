@@ -78,10 +78,26 @@ def test_default_params_and_argument_checks(built_lib):
     assert L.fslbm_check_grid_barrier(2, None) == -1          # expire must be 0 or 1
     L.fslbm_launches_per_step.argtypes = [ctypes.c_void_p]
     assert L.fslbm_launches_per_step(None) == -1
+    assert L.fslbm_build_info() == 0                        # the normal library, not the bounds-checked one
     assert L.fslbm_step(None, 1) == -1
     L.fslbm_last_error.restype = ctypes.c_char_p
     assert L.fslbm_last_error(None) == b"NULL handle"
     L.fslbm_destroy(None)
+
+
+def test_checked_variant_is_a_separate_build():
+    """build(checked=True) compiles the same sources with FSLBM_CHECKED into
+    a library of its own, which the binding loads only when FSLBM_CHECKED=1."""
+    from paper_1409_5645_gb300 import build, fslbm
+    assert build.CHECKED_LIB != build.LIB and os.path.dirname(build.CHECKED_LIB) != os.path.dirname(build.LIB)
+    if os.environ.get("FSLBM_CHECKED") != "1":
+        assert fslbm.LIB_PATH == build.LIB
+    src = open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", "fslbm_dev.cuh")).read()
+    # in the normal build every check macro is the bare expression
+    normal = src.split("#ifdef FSLBM_CHECKED\n__device__")[1].split("#else")[1].split("#endif")[0]
+    for line in normal.strip().splitlines():
+        name, body = re.match(r"#define (FSL_[A-Z_]+)\((.*?)\) (.*)", line).group(1, 3)
+        assert body in ("(k)", "true"), line
 
 
 def test_binding_refuses_without_library(monkeypatch, tmp_path):
