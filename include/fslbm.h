@@ -70,8 +70,8 @@ enum fslbm_status {
   FSLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
   FSLBM_ERR_STATE = -4,    /* invariant violated: a liquid cell next to gas, bad flag; in the
                               bounds-checked library also an index outside its array */
-  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density, or a cell velocity above
-                              u_max (the stability guard of the step) */
+  FSLBM_ERR_UNSTABLE = -5, /* non-finite or non-positive density, or a liquid cell's velocity
+                              above u_max (the stability guard of the step) */
   FSLBM_ERR_OVERFLOW = -6, /* a conversion list exceeded its capacity */
   FSLBM_ERR_TIMEOUT = -7,  /* a bounded device-side wait expired (staged loads of the bulk kernel, the
                               grid barrier of the conversion kernel) */
@@ -179,9 +179,13 @@ typedef struct {
                          memory); 0 (default): in FP64.  An implementation choice: GB300 runs FP64
                          at a small fraction of its FP32 rate, and the reverse step is bound by it.
                          Ignored by FP64 lattices */
-  double u_max;       /* stability guard: a step in which a cell's velocity exceeds u_max lattice
-                         units reports FSLBM_ERR_UNSTABLE (the equilibria are second order in u, and
-                         the lattice speed of sound is 1/sqrt(3)); default 0.4, 0 switches it off */
+  double u_max;       /* stability guard: a step in which a liquid cell's velocity exceeds u_max
+                         lattice units reports FSLBM_ERR_UNSTABLE (the equilibria are second order in
+                         u, and the lattice speed of sound is 1/sqrt(3)); default 0.4, 0 switches it
+                         off.  Interface cells are not guarded: isolated ones in spray, with a few
+                         fluid neighbours, reach 0.4 in stable flows (dam break 512x256x256,
+                         tau 0.53, steps 5000-15500: interface cells up to 0.4 and above, liquid
+                         cells below 0.14) */
 } fslbm_params;
 
 /* Defaults: tau 0.8, magic 3/16, g 0, rho_G 1, sigma 0, FSL, rho_0 = 1,

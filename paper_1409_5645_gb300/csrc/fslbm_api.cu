@@ -366,7 +366,7 @@ static int read_err(fslbm* h) {
   CK(cudaStreamSynchronize(h->st), "stream synchronize");
   if (e & ERRB_STATE) return fail(h, FSLBM_ERR_STATE, "invariant violated: a liquid cell touches gas, or a bad flag");
   if (e & ERRB_UNSTABLE) return fail(h, FSLBM_ERR_UNSTABLE, "non-finite or non-positive density");
-  if (e & ERRB_SPEED) return fail(h, FSLBM_ERR_UNSTABLE, "a cell velocity above u_max");
+  if (e & ERRB_SPEED) return fail(h, FSLBM_ERR_UNSTABLE, "a liquid cell velocity above u_max");
   if (e & ERRB_OVERFLOW) return fail(h, FSLBM_ERR_OVERFLOW, "conversion list overflow");
   if (e & ERRB_TMA) return fail(h, FSLBM_ERR_TIMEOUT, "staged loads of the bulk kernel failed (bounded wait expired)");
   if (e & ERRB_SYNC) return fail(h, FSLBM_ERR_TIMEOUT, "grid barrier of the conversion kernel expired");

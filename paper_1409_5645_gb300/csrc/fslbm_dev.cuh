@@ -218,9 +218,11 @@ __device__ __forceinline__ bool chk_ok(bool ok, int* err) {
 #define FSL_OK(p, c) true
 #endif
 
-// stability guard on a cell's velocity: |u| above u_max (0.4 lattice units
-// by default: the equilibria are second order in u, and the lattice's speed
-// of sound is 1/sqrt(3) ~ 0.58); umax2 = u_max^2, 0 switches it off
+// stability guard on a liquid cell's velocity: |u| above u_max (0.4 lattice
+// units by default: the equilibria are second order in u, and the lattice's
+// speed of sound is 1/sqrt(3) ~ 0.58); umax2 = u_max^2, 0 switches it off.
+// Interface cells are left out: isolated ones in spray (a few fluid
+// neighbours) reach such speeds in a stable flow.
 template <class R>
 __device__ __forceinline__ bool speed_bad(const Par& p, R ux, R uy, R uz) {
   return p.umax2 > 0.0 && ux * ux + uy * uy + uz * uz > R(p.umax2);
