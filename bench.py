@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--spinup", type=int, default=5000,
                     help="untimed steps from the initial column before the warm-up, so that the timed window "
-                         "sits in the middle of the 10000-step run (its interface and conversions), not at its "
-                         "start")
+                         "(steps spinup + warmup + 1 to spinup + warmup + steps) covers the front, the splash "
+                         "and the spray of the dam break (its interface and conversions), not its start")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="f32,f64,f16", help="precision forms; the first is the headline")
     ap.add_argument("--form-steps", type=int, default=2000, help="timed steps of the non-headline forms")
@@ -532,7 +532,8 @@ def main():
                    "precision": forms[0], "parallelism": "one lattice, one GPU",
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (N * 2 * 19 * s / 1e9),
                    "start": ("saved state " + args.load_state) if args.load_state else
-                   ("after %d untimed steps from the initial column (middle of the 10000-step run)" % args.spinup
+                   ("after %d untimed and %d warm-up steps from the initial column: timed steps %d to %d"
+                    % (args.spinup, args.warmup, args.spinup + args.warmup + 1, args.spinup + args.warmup + args.steps)
                     if args.spinup else "initial column")},
         "mflups_active": round(ws * (head["n_liquid"] + head["n_interface"]) * args.steps
                                / (ms_max / 1e3) / 1e6, 2),
