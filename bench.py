@@ -236,10 +236,15 @@ def hbm_peak():
 
 
 def kernel_source_sha():
+    """Hash of the bulk and interface kernels' code (comments and blank lines
+    left out, so that a change of wording does not orphan a profile)."""
     h = hashlib.sha256()
     for f in ("fslbm_step.cu", "fslbm_step.cuh", "fslbm_staged.cu", "fslbm_pairs.cu", "fslbm_pull.cuh",
               "fslbm_dev.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1409_5645_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        code = [ln.split("//")[0].rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in code if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

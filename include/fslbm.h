@@ -432,12 +432,12 @@ int fslbm_fp64_rate(double *tflops, void *stream);
 /* Build properties of the loaded library: bit 0 set in the bounds-checked
  * library (compiled with FSLBM_CHECKED).  There every cell index a kernel
  * reads from a segment record or a cell list, and every source cell that a
- * fast path forms by offset arithmetic, is tested against the lattice before
- * the access (as is a fast path's precondition, a cell handled as interior
- * lying 3 or more cells inside every face); a failed test skips to cell 0
- * and makes the next synchronising call return FSLBM_ERR_STATE.  Results are
- * otherwise those of the normal library.  An implementation property with
- * no counterpart in the paper. */
+ * bulk kernel's fast path forms by offset arithmetic, is tested against the
+ * lattice before the access (as is the interface kernels' precondition for
+ * a cell handled as interior: 3 or more cells inside every face); a failed
+ * test skips to cell 0 and makes the next synchronising call return
+ * FSLBM_ERR_STATE.  Results are otherwise those of the normal library.  An
+ * implementation property with no counterpart in the paper. */
 int fslbm_build_info(void);
 
 /* Bytes of device memory held by the handle. */

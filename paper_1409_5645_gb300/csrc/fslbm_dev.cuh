@@ -167,14 +167,16 @@ struct Par {
 // ---------------------------------------------------------------------------
 // Bounds-checked build (compiled with FSLBM_CHECKED, a library of its own).
 // Every cell index a kernel reads from memory (a segment record, a cell list)
-// and every source cell a fast path forms by offset arithmetic is tested
-// against the lattice before the access, and so is a fast path's
-// precondition (a cell handled as interior lies 3 or more cells inside every
-// face).  A failed test sets ERRB_BOUNDS in the error word, reported at the
-// next synchronising call, and the access goes to cell 0 instead (where a
-// precondition failed, the cell is skipped); nothing traps.  Indices from nbr() (an in-range cell or -1) and from bounded loop
-// counters need no test.  In the normal build each macro is the bare
-// expression.
+// and every source cell a bulk kernel's fast path forms by offset arithmetic
+// (whose range rests on the segment masks) is tested against the lattice
+// before the access, and so is the precondition of the interface kernels'
+// interior instances (the cell lies 3 or more cells inside every face).  A
+// failed test sets ERRB_BOUNDS in the error word, reported at the next
+// synchronising call, and the access goes to cell 0 instead (where the
+// precondition failed, the cell is skipped); nothing traps.  Indices from
+// nbr() (an in-range cell or -1), from bounded loop counters and from
+// offsets next to a test of the cell's coordinates need no test.  In the
+// normal build each macro is the bare expression.
 // ---------------------------------------------------------------------------
 #ifdef FSLBM_CHECKED
 __device__ __forceinline__ long long chk_index(long long k, long long n, int* err) {
