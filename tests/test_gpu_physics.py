@@ -155,3 +155,54 @@ def test_droplet_parity_and_laplace_jump():
         print(f"droplet R=6 {prec}: Laplace jump / theory = {ratio:.4f}")
         assert abs(ratio - 1.0) < 0.06
         g.close()
+
+
+def _golden_dam_break_128():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dam_break_128x64x64_oracle.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        out[key] = [float(v) for v in vals] if len(vals) > 1 else float(vals[0])
+    return out
+
+
+def test_dam_break_miniature_mass_against_the_oracle():
+    """The throughput workload scaled by 1/4 (128x64x64, column x < 32,
+    z < 48, tau 0.53) over 10 000 steps in the three forms, beside the FP64
+    oracle's own run of it (tests/golden/dam_break_128x64x64_oracle.txt,
+    written by the oracle alone): the same initial mass (to the round-off of
+    a 0.5 M-term sum taken in another order); FP64 conserves mass
+    plus ledger to round-off as the oracle does; FP32 and FP16 storage drift
+    by rounding only (bounds stated, values printed).  The FP64 cell counts
+    at the end equal the oracle's: 10 000 steps of a splash at 1e-12 per-step
+    parity flip no cell (measured: 91 776 liquid, 13 912 interface on both
+    sides); the reduced forms' counts are printed beside them."""
+    gold = _golden_dam_break_128()
+    steps = int(gold["steps"])
+    c = cases.dam_break(nx=128, ny=64, nz=64, col_x=32, col_z=48, tau=0.53, magic=0.005, rule=1,
+                        bulk_loads="pairs")
+    drift, counts = {}, {}
+    for prec in ("f64", "f32", "f16"):
+        g = fslbm.Lattice.from_case(c, precision=prec)
+        M0, _ = g.total_mass()
+        if prec == "f64":
+            # the same populations summed in another order (the library sums
+            # its stored post-collision values with a fixed reduction tree)
+            assert M0 == pytest.approx(gold["mass0"], rel=1e-12)
+        g.step(steps)
+        M1, lost = g.total_mass()
+        fl = g.get(fslbm.FIELD_FLAGS)["flags"]
+        drift[prec] = (M1 - M0) / M0
+        counts[prec] = (int((fl == cases.LIQUID).sum()), int((fl == cases.INTERFACE).sum()), lost)
+        g.close()
+    print("mass drift over %d steps: oracle %.2e, FP64 %.2e, FP32 %.2e, FP16 storage %.2e"
+          % (steps, gold["drift_rel"], drift["f64"], drift["f32"], drift["f16"]))
+    print("liquid / interface cells at the end: oracle %d / %d, FP64 %d / %d, FP32 %d / %d, FP16 %d / %d"
+          % (gold["liquid1"], gold["interface1"], *counts["f64"][:2], *counts["f32"][:2], *counts["f16"][:2]))
+    assert abs(gold["drift_rel"]) < 1e-11 and abs(drift["f64"]) < 1e-11
+    assert counts["f64"][:2] == (int(gold["liquid1"]), int(gold["interface1"]))
+    assert abs(drift["f32"]) < 1e-4
+    assert abs(drift["f16"]) < 1e-2
